@@ -1,0 +1,256 @@
+"""Python side of the MQCT oracle (plain FP64 CPU reference of the trajectory method).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and by
+the CPU-baseline leg of ``bench.py``.  The CUDA library never imports it.
+
+The arithmetic lives in ``mqct_oracle.c`` (built with gcc into ``oracle/_build``);
+this module only marshals numpy arrays through ctypes.  Every quantity is in
+atomic units (hartree, bohr, electron masses, atomic units of time).
+
+Paper passages followed (arXiv 2312.02322): Eq. 4-10 (equations of motion), Eq. 12
+(factorised PES), Eq. 15 (Gaunt integral), Sec. III (cubic spline of the coupling),
+Sec. II (cross sections from final populations).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mqct_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ST_MAX_STEPS = 1
+ST_TABLE_RANGE = 2
+ST_NONFINITE = 4
+
+F_NO_STOP = 1
+F_PRESCRIBED = 2
+F_FLIP_JY = 4
+F_PLANT_TORQUE = 8      # planted mistake: torque sign reversed alone
+F_PLANT_CORIOLIS = 16   # planted mistake: Coriolis factor 1/2 dropped
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, OpenMP over trajectories)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int), ("n_terms", C.c_int), ("n_grid", C.c_int),
+        ("mu", C.c_double), ("r_min", C.c_double), ("r_max", C.c_double),
+        ("energy", C.c_void_p), ("level", C.c_void_p), ("jq", C.c_void_p), ("mq", C.c_void_p),
+        ("G", C.c_void_p), ("v", C.c_void_p), ("dv_ends", C.c_void_p),
+        ("n_params", C.c_int), ("dvp", C.c_void_p), ("dvp_ends", C.c_void_p),
+    ]
+
+
+class _Traj(C.Structure):
+    _fields_ = [("e_coll", C.c_double), ("b", C.c_double), ("r0", C.c_double), ("r_end", C.c_double),
+                ("dt", C.c_double), ("init_state", C.c_int), ("max_steps", C.c_int)]
+
+
+class _Res(C.Structure):
+    _fields_ = [("steps", C.c_int), ("status", C.c_int), ("norm_dev", C.c_double), ("energy_dev", C.c_double),
+                ("angmom_dev", C.c_double), ("t_final", C.c_double), ("R", C.c_double), ("PR", C.c_double),
+                ("Phi", C.c_double), ("PPhi", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.ora_cg.restype = C.c_double
+            L.ora_cg.argtypes = [C.c_int] * 6
+            L.ora_diatom_n.restype = C.c_int
+            L.ora_spline.restype = C.c_int
+            L.ora_propagate.restype = C.c_int
+            L.ora_tangent.restype = C.c_int
+            L.ora_num_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def cg(j1, m1, j2, m2, J, M) -> float:
+    """Clebsch-Gordan coefficient <j1 m1 j2 m2 | J M> (Racah formula)."""
+    return lib().ora_cg(j1, m1, j2, m2, J, M)
+
+
+def num_threads() -> int:
+    return lib().ora_num_threads()
+
+
+class System:
+    """Atom + rigid-rotor system in the oracle's own representation (atomic units).
+
+    energy[n], level[n], jq[n], mq[n] label the states (jq < 0 disables the Coriolis
+    term for that state); G[L][n][n] are the angular coupling matrices of Eq. 12;
+    v[L][n_grid] and dv_ends[L][2] define the clamped splines of v_lambda(R).
+    """
+
+    def __init__(self, energy, level, jq, mq, G, v, dv_ends, mu, r_min, r_max, dvp=None, dvp_ends=None):
+        self.energy = np.ascontiguousarray(energy, np.float64)
+        self.level = np.ascontiguousarray(level, np.int32)
+        self.jq = np.ascontiguousarray(jq, np.int32)
+        self.mq = np.ascontiguousarray(mq, np.int32)
+        self.G = np.ascontiguousarray(G, np.float64)
+        self.v = np.ascontiguousarray(v, np.float64)
+        self.dv_ends = np.ascontiguousarray(dv_ends, np.float64)
+        self.mu, self.r_min, self.r_max = float(mu), float(r_min), float(r_max)
+        self.n = self.energy.shape[0]
+        self.L = self.G.shape[0]
+        self.n_grid = self.v.shape[1]
+        self.n_levels = int(self.level.max()) + 1
+        self.dvp = None if dvp is None else np.ascontiguousarray(dvp, np.float64)
+        self.dvp_ends = None if dvp_ends is None else np.ascontiguousarray(dvp_ends, np.float64)
+        assert self.G.shape == (self.L, self.n, self.n)
+        assert self.v.shape == (self.L, self.n_grid) and self.dv_ends.shape == (self.L, 2)
+
+    def _desc(self):
+        d = _Desc()
+        d.n, d.n_terms, d.n_grid = self.n, self.L, self.n_grid
+        d.mu, d.r_min, d.r_max = self.mu, self.r_min, self.r_max
+        d.energy, d.level, d.jq, d.mq = _p(self.energy), _p(self.level), _p(self.jq), _p(self.mq)
+        d.G, d.v, d.dv_ends = _p(self.G), _p(self.v), _p(self.dv_ends)
+        if self.dvp is not None:
+            d.n_params = self.dvp.shape[0]
+            d.dvp, d.dvp_ends = _p(self.dvp), _p(self.dvp_ends)
+        return d
+
+
+def diatom_basis(jmax: int, bconst: float):
+    n = lib().ora_diatom_n(jmax)
+    e = np.zeros(n)
+    lev, jq, mq = (np.zeros(n, np.int32) for _ in range(3))
+    lib().ora_diatom_basis(C.c_int(jmax), C.c_double(bconst), _p(e), _p(lev), _p(jq), _p(mq))
+    return e, lev, jq, mq
+
+
+def diatom_G(jmax: int, lam: int) -> np.ndarray:
+    """<j'' m | P_lambda | j' m> in j-major state order (Eq. 15)."""
+    n = lib().ora_diatom_n(jmax)
+    G = np.zeros((n, n))
+    lib().ora_diatom_G(C.c_int(jmax), C.c_int(lam), _p(G))
+    return G
+
+
+def diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params=False):
+    A = np.ascontiguousarray(A, np.float64)
+    beta = np.ascontiguousarray(beta, np.float64)
+    L = A.shape[0]
+    v = np.zeros((L, n_grid))
+    ends = np.zeros((L, 2))
+    dvp = np.zeros((2 * L, L, n_grid)) if with_params else None
+    dvpe = np.zeros((2 * L, L, 2)) if with_params else None
+    lib().ora_diatom_pes(C.c_int(L), _p(A), _p(beta), C.c_double(c6), C.c_double(rd), C.c_int(n_grid),
+                         C.c_double(r_min), C.c_double(r_max), _p(v), _p(ends),
+                         _p(dvp) if with_params else None, _p(dvpe) if with_params else None)
+    return v, ends, dvp, dvpe
+
+
+def diatom_system(jmax, bconst, mu, A, beta, c6, rd, n_grid, r_min, r_max, with_params=False) -> System:
+    """Atom + linear rotor (Eq. 2 basis, Eq. 15 coupling, PES of the form used in the tests)."""
+    e, lev, jq, mq = diatom_basis(jmax, bconst)
+    L = len(A)
+    G = np.stack([diatom_G(jmax, l) for l in range(L)])
+    v, ends, dvp, dvpe = diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params)
+    return System(e, lev, jq, mq, G, v, ends, mu, r_min, r_max, dvp, dvpe)
+
+
+def spline(y, h, d0, dn) -> np.ndarray:
+    y = np.ascontiguousarray(y, np.float64)
+    coef = np.zeros((y.shape[0] - 1, 4))
+    rc = lib().ora_spline(C.c_int(y.shape[0]), C.c_double(h), _p(y), C.c_double(d0), C.c_double(dn), _p(coef))
+    if rc:
+        raise ValueError("ora_spline failed")
+    return coef
+
+
+def spline_eval(coef, n_grid, r_min, r_max, R):
+    R = np.ascontiguousarray(R, np.float64)
+    f, df, d2f = (np.zeros_like(R) for _ in range(3))
+    lib().ora_spline_eval(_p(np.ascontiguousarray(coef)), C.c_int(n_grid), C.c_double(r_min), C.c_double(r_max),
+                          C.c_int(R.shape[0]), _p(R), _p(f), _p(df), _p(d2f))
+    return f, df, d2f
+
+
+def _trajs(e_coll, b, r0, r_end, dt, init_state, max_steps):
+    n = len(e_coll)
+    arr = (_Traj * n)()
+    for i in range(n):
+        arr[i].e_coll = float(e_coll[i])
+        arr[i].b = float(b[i])
+        arr[i].r0 = float(np.broadcast_to(r0, (n,))[i])
+        arr[i].r_end = float(np.broadcast_to(r_end, (n,))[i])
+        arr[i].dt = float(np.broadcast_to(dt, (n,))[i])
+        arr[i].init_state = int(init_state[i])
+        arr[i].max_steps = int(np.broadcast_to(max_steps, (n,))[i])
+    return arr
+
+
+def _results(res, n):
+    out = {k: np.array([getattr(res[i], k) for i in range(n)]) for k, _ in _Res._fields_}
+    out["steps"] = out["steps"].astype(np.int64)
+    out["status"] = out["status"].astype(np.int64)
+    return out
+
+
+def propagate(sys: System, e_coll, b, init_state, r0=30.0, r_end=30.0, dt=5.0, max_steps=1_000_000,
+              flags=0, line_speed=None, n_threads=0):
+    """Run the RK4 MQCT trajectories; returns (final amplitudes [n_traj][n] complex, result dict)."""
+    n_traj = len(e_coll)
+    tr = _trajs(e_coll, b, r0, r_end, dt, init_state, max_steps)
+    amp = np.zeros((n_traj, sys.n, 2))
+    res = (_Res * n_traj)()
+    ls = None if line_speed is None else np.ascontiguousarray(line_speed, np.float64)
+    d = sys._desc()
+    rc = lib().ora_propagate(C.byref(d), tr, C.c_int(n_traj), C.c_int(flags), _p(ls) if ls is not None else None,
+                             C.c_int(n_threads), _p(amp), res)
+    if rc:
+        raise RuntimeError(f"ora_propagate failed ({rc})")
+    return amp[..., 0] + 1j * amp[..., 1], _results(res, n_traj)
+
+
+def tangent(sys: System, e_coll, b, init_state, r0=30.0, r_end=30.0, dt=5.0, max_steps=1_000_000, n_threads=0):
+    """Forward-mode derivative of the final populations: returns (amp, dpop [n_traj][P][n], results)."""
+    if sys.dvp is None:
+        raise ValueError("system has no parameter-derivative tables")
+    n_traj = len(e_coll)
+    P = sys.dvp.shape[0]
+    tr = _trajs(e_coll, b, r0, r_end, dt, init_state, max_steps)
+    amp = np.zeros((n_traj, sys.n, 2))
+    dpop = np.zeros((n_traj, P, sys.n))
+    res = (_Res * n_traj)()
+    d = sys._desc()
+    rc = lib().ora_tangent(C.byref(d), tr, C.c_int(n_traj), C.c_int(n_threads), _p(amp), _p(dpop), res)
+    if rc:
+        raise RuntimeError(f"ora_tangent failed ({rc})")
+    return amp[..., 0] + 1j * amp[..., 1], dpop, _results(res, n_traj)
+
+
+def cross_sections(sys: System, pop, weight, group, n_groups) -> np.ndarray:
+    """sigma[g][level''] = sum_{t in g} weight_t * sum_{s in level''} pop_t[s]."""
+    pop = np.ascontiguousarray(pop, np.float64)
+    weight = np.ascontiguousarray(weight, np.float64)
+    group = np.ascontiguousarray(group, np.int32)
+    sig = np.zeros((n_groups, sys.n_levels))
+    lib().ora_cross_sections(C.c_int(sys.n), _p(sys.level), C.c_int(sys.n_levels), C.c_int(pop.shape[0]), _p(pop),
+                             _p(weight), _p(group), C.c_int(n_groups), _p(sig))
+    return sig

@@ -1,0 +1,861 @@
+/*
+ * MQCT oracle -- a plain, slow, FP64 CPU implementation of the mixed
+ * quantum/classical (Ehrenfest mean-field) trajectory method of
+ * Joy, Mandal, Bostan, Dubernet & Babikov (arXiv 2312.02322).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py load this file.  It shares no code, header,
+ * table or helper with the CUDA library; the two are compared on the same
+ * seeded inputs.
+ *
+ * What it follows (paper sections / equations):
+ *   Eq. 4       amplitudes a_n in the interaction picture; c_n = exp(-i E_n t) a_n
+ *   Eq. 5       quantum equations of motion: potential coupling summed over the
+ *               states of the same m, plus the Coriolis m +- 1 term driven by dPhi/dt
+ *   Eq. 6       M(R) = <Psi_n'' m | V | Psi_n' m>: real, symmetric, diagonal in m
+ *   Eqs. 7-10   classical R, Phi, P_R, P_Phi in the collision plane (Theta = pi/2)
+ *   Eq. 12      V = sum_lambda v_lambda(R) tau_lambda, hence M(R) = sum_lambda v_lambda(R) G^lambda
+ *   Eq. 15      integral of three spherical harmonics (G^lambda of a linear rotor)
+ *   Sec. III    cubic-spline interpolation of the coupling along R
+ *   Sec. II     final |a|^2 summed over final and averaged over initial degenerate states
+ *
+ * Readings where the printed text is garbled or silent (each is listed in the
+ * design notes of the repository):
+ *   - Eq. 5 Coriolis term: written as the anti-Hermitian generator
+ *       (K a)_{j m} = (dPhi/dt / 2) [ A-_{jm} a_{j,m-1} - A+_{jm} a_{j,m+1} ],
+ *     A+-_{jm} = sqrt(j(j+1) - m(m+-1)), i.e. H_q = H_rot + V - dPhi/dt J_y.
+ *   - Eq. 10 torque: dP_Phi/dt = i <[J_y, V]> = Re( c^dag D M c ),  D = J+ - J-,
+ *     the unique form that conserves E_tot and P_Phi + <J_y> with the above.
+ *   - Initial conditions: a = e_s0, R = R0, Phi = 0, P_Phi = b sqrt(2 mu E),
+ *     P_R = -sqrt(2 mu (E - M_s0s0(R0)) - P_Phi^2 / R0^2).
+ *   - Spline: clamped cubic on a uniform grid with given end slopes; outside the
+ *     grid the first / last cubic is extrapolated.  Interval k = floor((R-r_min)/h)
+ *     clamped to [0, n_grid-2], x = R - (r_min + k h).
+ *   - Time stepping: classical 4-stage RK4 with fixed dt, stage times
+ *     n dt, n dt + dt/2, n dt + dt/2, (n+1) dt.  A trajectory stops after the
+ *     first step that ends with R >= r_end and P_R > 0, or after max_steps.
+ *
+ * Everything is FP64, written for clarity: per-state complex exponentials,
+ * per-element M_rc = sum_lambda v_lambda G^lambda_rc, sums in state order.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORA_OK 0
+#define ORA_EINVAL 1
+#define ORA_ENOMEM 2
+
+/* trajectory status bits */
+#define ORA_ST_MAX_STEPS 1
+#define ORA_ST_TABLE_RANGE 2
+#define ORA_ST_NONFINITE 4
+
+/* propagation flags */
+#define ORA_F_NO_STOP 1     /* only max_steps ends a trajectory                   */
+#define ORA_F_PRESCRIBED 2  /* classical motion fixed to a straight line (test)   */
+#define ORA_F_FLIP_JY 4     /* J_y -> -J_y in the Coriolis term and in the torque */
+/* planted mistakes, used only by the tests that show the conservation pins catch them */
+#define ORA_F_PLANT_TORQUE 8     /* reverse the sign of the torque alone          */
+#define ORA_F_PLANT_CORIOLIS 16  /* drop the factor 1/2 of the Coriolis term      */
+
+/* ------------------------------------------------------------------ */
+/* Clebsch-Gordan coefficients: Racah's closed formula, long double.  */
+/* ------------------------------------------------------------------ */
+static long double lfac(int n) { return lgammal((long double)n + 1.0L); }
+
+double ora_cg(int j1, int m1, int j2, int m2, int J, int M)
+{
+    if (m1 + m2 != M) return 0.0;
+    if (j1 < 0 || j2 < 0 || J < 0) return 0.0;
+    if (abs(m1) > j1 || abs(m2) > j2 || abs(M) > J) return 0.0;
+    if (J < abs(j1 - j2) || J > j1 + j2) return 0.0;
+    if (m1 == 0 && m2 == 0 && ((j1 + j2 + J) & 1)) return 0.0; /* parity: vanishes exactly */
+    long double pre = 0.5L * (logl(2.0L * J + 1.0L) + lfac(J + j1 - j2) + lfac(J - j1 + j2) +
+                              lfac(j1 + j2 - J) - lfac(j1 + j2 + J + 1) + lfac(J + M) + lfac(J - M) +
+                              lfac(j1 - m1) + lfac(j1 + m1) + lfac(j2 - m2) + lfac(j2 + m2));
+    int kmin = 0;
+    if (j2 - J - m1 > kmin) kmin = j2 - J - m1;
+    if (j1 + m2 - J > kmin) kmin = j1 + m2 - J;
+    int kmax = j1 + j2 - J;
+    if (j1 - m1 < kmax) kmax = j1 - m1;
+    if (j2 + m2 < kmax) kmax = j2 + m2;
+    long double s = 0.0L;
+    for (int k = kmin; k <= kmax; ++k) {
+        long double den = lfac(k) + lfac(j1 + j2 - J - k) + lfac(j1 - m1 - k) + lfac(j2 + m2 - k) +
+                          lfac(J - j2 + m1 + k) + lfac(J - j1 - m2 + k);
+        long double t = expl(pre - den);
+        s += (k & 1) ? -t : t;
+    }
+    return (double)s;
+}
+
+/* ------------------------------------------------------------------ */
+/* Linear rotor basis and G^lambda (Eq. 2, Eq. 15)                     */
+/* ------------------------------------------------------------------ */
+/* States in j-major order: s = j*j + (m + j), j = 0..jmax, m = -j..j.  */
+int ora_diatom_n(int jmax) { return (jmax + 1) * (jmax + 1); }
+
+void ora_diatom_basis(int jmax, double bconst, double *energy, int *level, int *jq, int *mq)
+{
+    for (int j = 0; j <= jmax; ++j)
+        for (int m = -j; m <= j; ++m) {
+            int s = j * j + (m + j);
+            energy[s] = bconst * j * (j + 1);
+            level[s] = j;
+            jq[s] = j;
+            mq[s] = m;
+        }
+}
+
+/* <j'' m | P_lambda(cos theta) | j' m>: Eq. 15 with P_lambda = sqrt(4 pi/(2 lambda+1)) Y_lambda0:
+ *   sqrt((2j'+1)/(2j''+1)) C^{j'' 0}_{j' 0 lambda 0} C^{j'' m}_{j' m lambda 0};  zero unless m'' = m'. */
+void ora_diatom_G(int jmax, int lam, double *G)
+{
+    int n = ora_diatom_n(jmax);
+    memset(G, 0, sizeof(double) * (size_t)n * n);
+    for (int j2 = 0; j2 <= jmax; ++j2)        /* j''  (row)    */
+        for (int j1 = 0; j1 <= jmax; ++j1) {  /* j'   (column) */
+            double c0 = ora_cg(j1, 0, lam, 0, j2, 0);
+            if (c0 == 0.0) continue;
+            double f = sqrt((2.0 * j1 + 1.0) / (2.0 * j2 + 1.0)) * c0;
+            int mm = j1 < j2 ? j1 : j2;
+            for (int m = -mm; m <= mm; ++m) {
+                int r = j2 * j2 + (m + j2), c = j1 * j1 + (m + j1);
+                G[(size_t)r * n + c] = f * ora_cg(j1, m, lam, 0, j2, m);
+            }
+        }
+}
+
+/* Synthetic atom + diatom PES of the form
+ *   V(R, theta) = sum_{lambda=0}^{4} A_l exp(-beta_l R) P_l(cos theta)
+ *                 - C6 R^-6 (1 - exp(-(R/Rd)^6))          (isotropic, lambda = 0)
+ * evaluated on a uniform grid; all quantities in atomic units.
+ * Outputs v[L][n_grid], dv_ends[L][2] (analytic dv/dR at both ends) and, if
+ * dvp != NULL, the derivatives with respect to theta = (A_0..A_{L-1}, beta_0..beta_{L-1}):
+ * dvp[2L][L][n_grid], dvp_ends[2L][L][2]. */
+void ora_diatom_pes(int L, const double *A, const double *beta, double c6, double rd, int n_grid,
+                    double r_min, double r_max, double *v, double *dv_ends, double *dvp, double *dvp_ends)
+{
+    double h = (r_max - r_min) / (n_grid - 1);
+    for (int l = 0; l < L; ++l) {
+        for (int k = 0; k < n_grid; ++k) {
+            double R = r_min + k * h;
+            double val = A[l] * exp(-beta[l] * R);
+            if (l == 0) val -= c6 * pow(R, -6.0) * (1.0 - exp(-pow(R / rd, 6.0)));
+            v[l * n_grid + k] = val;
+        }
+        for (int e = 0; e < 2; ++e) {
+            double R = e ? r_max : r_min;
+            double d = -beta[l] * A[l] * exp(-beta[l] * R);
+            if (l == 0) {
+                double u = pow(R / rd, 6.0);
+                d += 6.0 * c6 * pow(R, -7.0) * (1.0 - exp(-u)) - c6 * pow(R, -6.0) * exp(-u) * 6.0 * u / R;
+            }
+            dv_ends[l * 2 + e] = d;
+        }
+    }
+    if (!dvp) return;
+    memset(dvp, 0, sizeof(double) * (size_t)2 * L * L * n_grid);
+    memset(dvp_ends, 0, sizeof(double) * (size_t)2 * L * L * 2);
+    for (int l = 0; l < L; ++l) {
+        double *pa = dvp + ((size_t)l * L + l) * n_grid;        /* d v_l / d A_l    */
+        double *pb = dvp + ((size_t)(L + l) * L + l) * n_grid;  /* d v_l / d beta_l */
+        for (int k = 0; k < n_grid; ++k) {
+            double R = r_min + k * h;
+            pa[k] = exp(-beta[l] * R);
+            pb[k] = -R * A[l] * exp(-beta[l] * R);
+        }
+        for (int e = 0; e < 2; ++e) {
+            double R = e ? r_max : r_min;
+            double ex = exp(-beta[l] * R);
+            dvp_ends[((size_t)l * L + l) * 2 + e] = -beta[l] * ex;
+            dvp_ends[((size_t)(L + l) * L + l) * 2 + e] = -A[l] * ex + beta[l] * R * A[l] * ex;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Clamped cubic spline on a uniform grid (second-derivative form).   */
+/* ------------------------------------------------------------------ */
+/* coef[i][0..3]: y(R) = c0 + c1 x + c2 x^2 + c3 x^3 on [R_i, R_{i+1}], x = R - R_i. */
+int ora_spline(int n, double h, const double *y, double d0, double dn, double *coef)
+{
+    if (n < 2 || !(h > 0)) return ORA_EINVAL;
+    double *a = malloc(sizeof(double) * n), *b = malloc(sizeof(double) * n), *c = malloc(sizeof(double) * n),
+           *r = malloc(sizeof(double) * n), *s = malloc(sizeof(double) * n);
+    if (!a || !b || !c || !r || !s) {
+        free(a); free(b); free(c); free(r); free(s);
+        return ORA_ENOMEM;
+    }
+    /* tridiagonal system for the second derivatives s_i */
+    a[0] = 0.0; b[0] = 2.0; c[0] = 1.0;
+    r[0] = 6.0 / h * ((y[1] - y[0]) / h - d0);
+    for (int i = 1; i < n - 1; ++i) {
+        a[i] = 1.0; b[i] = 4.0; c[i] = 1.0;
+        r[i] = 6.0 / (h * h) * (y[i + 1] - 2.0 * y[i] + y[i - 1]);
+    }
+    a[n - 1] = 1.0; b[n - 1] = 2.0; c[n - 1] = 0.0;
+    r[n - 1] = 6.0 / h * (dn - (y[n - 1] - y[n - 2]) / h);
+    /* Thomas algorithm */
+    for (int i = 1; i < n; ++i) {
+        double w = a[i] / b[i - 1];
+        b[i] -= w * c[i - 1];
+        r[i] -= w * r[i - 1];
+    }
+    s[n - 1] = r[n - 1] / b[n - 1];
+    for (int i = n - 2; i >= 0; --i) s[i] = (r[i] - c[i] * s[i + 1]) / b[i];
+    for (int i = 0; i < n - 1; ++i) {
+        double *q = coef + 4 * (size_t)i;
+        q[0] = y[i];
+        q[1] = (y[i + 1] - y[i]) / h - h * (2.0 * s[i] + s[i + 1]) / 6.0;
+        q[2] = 0.5 * s[i];
+        q[3] = (s[i + 1] - s[i]) / (6.0 * h);
+    }
+    free(a); free(b); free(c); free(r); free(s);
+    return ORA_OK;
+}
+
+/* value, first and second derivative of a spline built by ora_spline */
+static void spline_at(const double *coef, int n_int, double r_min, double h, double R, double *f, double *df,
+                      double *d2f)
+{
+    int k = (int)floor((R - r_min) / h);
+    if (k < 0) k = 0;
+    if (k > n_int - 1) k = n_int - 1;
+    double x = R - (r_min + k * h);
+    const double *q = coef + 4 * (size_t)k;
+    *f = q[0] + x * (q[1] + x * (q[2] + x * q[3]));
+    *df = q[1] + x * (2.0 * q[2] + 3.0 * x * q[3]);
+    *d2f = 2.0 * q[2] + 6.0 * x * q[3];
+}
+
+void ora_spline_eval(const double *coef, int n_grid, double r_min, double r_max, int npts, const double *R,
+                     double *f, double *df, double *d2f)
+{
+    double h = (r_max - r_min) / (n_grid - 1);
+    for (int i = 0; i < npts; ++i) spline_at(coef, n_grid - 1, r_min, h, R[i], f + i, df + i, d2f + i);
+}
+
+/* ------------------------------------------------------------------ */
+/* System: states, coupling terms, spline of v_lambda.                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int n, n_terms, n_grid;
+    double mu, r_min, r_max;
+    const double *energy;  /* [n]            */
+    const int *level;      /* [n]            */
+    const int *jq, *mq;    /* [n]; jq < 0 switches the Coriolis term off for the state */
+    const double *G;       /* [L][n][n]      */
+    const double *v;       /* [L][n_grid]    */
+    const double *dv_ends; /* [L][2]         */
+    int n_params;          /* derivative tables for ora_tangent (0 if unused) */
+    const double *dvp;     /* [P][L][n_grid] */
+    const double *dvp_ends;/* [P][L][2]      */
+} ora_system_desc;
+
+typedef struct {
+    double e_coll, b, r0, r_end, dt;
+    int init_state, max_steps;
+} ora_traj;
+
+typedef struct {
+    int steps, status;
+    double norm_dev, energy_dev, angmom_dev, t_final;
+    double R, PR, Phi, PPhi;
+} ora_result;
+
+typedef struct {
+    int n, L, n_int, P;
+    double mu, r_min, h;
+    const double *E;
+    int n_blk;
+    int *blk_start, *blk_size, *members; /* members grouped by block (same m) */
+    double *Gb;                          /* per block: [L][nb][nb]            */
+    size_t *blk_goff;
+    int *up, *dn;                        /* Coriolis partners (-1: none)      */
+    double *aup, *adn;                   /* A+ and A- ladder factors          */
+    double *coef;                        /* [L][n_int][4]                     */
+    double *dcoef;                       /* [P][L][n_int][4]                  */
+} ora_sys;
+
+static void sys_free(ora_sys *S)
+{
+    free(S->blk_start); free(S->blk_size); free(S->members); free(S->Gb); free(S->blk_goff);
+    free(S->up); free(S->dn); free(S->aup); free(S->adn); free(S->coef); free(S->dcoef);
+    memset(S, 0, sizeof(*S));
+}
+
+static int sys_build(const ora_system_desc *d, ora_sys *S)
+{
+    memset(S, 0, sizeof(*S));
+    int n = d->n, L = d->n_terms;
+    if (n < 1 || L < 1 || d->n_grid < 2 || !(d->mu > 0) || !(d->r_max > d->r_min)) return ORA_EINVAL;
+    S->n = n; S->L = L; S->n_int = d->n_grid - 1; S->P = d->n_params;
+    S->mu = d->mu; S->r_min = d->r_min; S->h = (d->r_max - d->r_min) / (d->n_grid - 1);
+    S->E = d->energy;
+    /* blocks of equal m (Eq. 5 couples states only within each m) */
+    int *blk_of = malloc(sizeof(int) * n);
+    S->blk_start = malloc(sizeof(int) * (n + 1));
+    S->blk_size = malloc(sizeof(int) * n);
+    S->members = malloc(sizeof(int) * n);
+    S->up = malloc(sizeof(int) * n); S->dn = malloc(sizeof(int) * n);
+    S->aup = malloc(sizeof(double) * n); S->adn = malloc(sizeof(double) * n);
+    int *mvals = malloc(sizeof(int) * n);
+    if (!blk_of || !S->blk_start || !S->blk_size || !S->members || !S->up || !S->dn || !S->aup || !S->adn || !mvals) {
+        free(blk_of); free(mvals); sys_free(S);
+        return ORA_ENOMEM;
+    }
+    int nb = 0;
+    for (int s = 0; s < n; ++s) {
+        int b = -1;
+        for (int q = 0; q < nb; ++q)
+            if (mvals[q] == d->mq[s]) b = q;
+        if (b < 0) { b = nb; mvals[nb++] = d->mq[s]; }
+        blk_of[s] = b;
+    }
+    S->n_blk = nb;
+    int pos = 0;
+    for (int b = 0; b < nb; ++b) {
+        S->blk_start[b] = pos;
+        for (int s = 0; s < n; ++s)
+            if (blk_of[s] == b) S->members[pos++] = s;
+        S->blk_size[b] = pos - S->blk_start[b];
+    }
+    S->blk_start[nb] = pos;
+    /* coupling must vanish between different m (Eq. 6) */
+    for (int l = 0; l < L; ++l)
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c)
+                if (blk_of[r] != blk_of[c] && d->G[((size_t)l * n + r) * n + c] != 0.0) {
+                    free(blk_of); free(mvals); sys_free(S);
+                    return ORA_EINVAL;
+                }
+    S->blk_goff = malloc(sizeof(size_t) * (nb + 1));
+    size_t tot = 0;
+    for (int b = 0; b < nb; ++b) { S->blk_goff[b] = tot; tot += (size_t)L * S->blk_size[b] * S->blk_size[b]; }
+    S->blk_goff[nb] = tot;
+    S->Gb = malloc(sizeof(double) * (tot ? tot : 1));
+    for (int b = 0; b < nb; ++b) {
+        int sz = S->blk_size[b];
+        const int *mem = S->members + S->blk_start[b];
+        for (int l = 0; l < L; ++l)
+            for (int r = 0; r < sz; ++r)
+                for (int c = 0; c < sz; ++c)
+                    S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + c] = d->G[((size_t)l * n + mem[r]) * n + mem[c]];
+    }
+    /* Coriolis partners: same level and j, m +- 1 */
+    for (int s = 0; s < n; ++s) {
+        S->up[s] = S->dn[s] = -1;
+        S->aup[s] = S->adn[s] = 0.0;
+        int j = d->jq[s], m = d->mq[s];
+        if (j < 0) continue;
+        for (int q = 0; q < n; ++q) {
+            if (d->jq[q] != j || d->level[q] != d->level[s]) continue;
+            if (d->mq[q] == m + 1) S->up[s] = q;
+            if (d->mq[q] == m - 1) S->dn[s] = q;
+        }
+        double jj = (double)j * (j + 1);
+        if (S->up[s] >= 0) S->aup[s] = sqrt(jj - (double)m * (m + 1));
+        if (S->dn[s] >= 0) S->adn[s] = sqrt(jj - (double)m * (m - 1));
+    }
+    free(blk_of); free(mvals);
+    /* splines of the expansion coefficients (and of their parameter derivatives) */
+    S->coef = malloc(sizeof(double) * (size_t)L * S->n_int * 4);
+    for (int l = 0; l < L; ++l) {
+        int e = ora_spline(d->n_grid, S->h, d->v + (size_t)l * d->n_grid, d->dv_ends[2 * l], d->dv_ends[2 * l + 1],
+                           S->coef + (size_t)l * S->n_int * 4);
+        if (e) { sys_free(S); return e; }
+    }
+    if (S->P > 0) {
+        S->dcoef = malloc(sizeof(double) * (size_t)S->P * L * S->n_int * 4);
+        for (int p = 0; p < S->P; ++p)
+            for (int l = 0; l < L; ++l) {
+                size_t o = (size_t)p * L + l;
+                int e = ora_spline(d->n_grid, S->h, d->dvp + o * d->n_grid, d->dvp_ends[2 * o], d->dvp_ends[2 * o + 1],
+                                   S->dcoef + o * S->n_int * 4);
+                if (e) { sys_free(S); return e; }
+            }
+    }
+    return ORA_OK;
+}
+
+/* v_lambda and its first two R-derivatives; table_range set if R < r_min */
+static void eval_terms(const ora_sys *S, const double *coef, double R, double *v, double *dv, double *d2v)
+{
+    for (int l = 0; l < S->L; ++l)
+        spline_at(coef + (size_t)l * S->n_int * 4, S->n_int, S->r_min, S->h, R, v + l, dv + l, d2v + l);
+}
+
+/* y = sum over the m-blocks of (sum_lambda f_lambda G^lambda) x   (Eq. 5 / Eq. 12) */
+static void couple(const ora_sys *S, const double *f, const double complex *x, double complex *y)
+{
+    for (int b = 0; b < S->n_blk; ++b) {
+        int sz = S->blk_size[b];
+        const int *mem = S->members + S->blk_start[b];
+        const double *Gb = S->Gb + S->blk_goff[b];
+        for (int r = 0; r < sz; ++r) {
+            double complex acc = 0.0;
+            for (int c = 0; c < sz; ++c) {
+                double mrc = 0.0;
+                for (int l = 0; l < S->L; ++l) mrc += f[l] * Gb[((size_t)l * sz + r) * sz + c];
+                acc += mrc * x[mem[c]];
+            }
+            y[mem[r]] = acc;
+        }
+    }
+}
+
+/* (D x)_s = A-_s x_{m-1} - A+_s x_{m+1},  D = J+ - J- */
+static double complex ladder(const ora_sys *S, const double complex *x, int s)
+{
+    double complex r = 0.0;
+    if (S->dn[s] >= 0) r += S->adn[s] * x[S->dn[s]];
+    if (S->up[s] >= 0) r -= S->aup[s] * x[S->up[s]];
+    return r;
+}
+
+typedef struct {
+    double complex *c, *w, *u, *u2, *tmp, *tmp2;
+    double *v, *dv, *d2v, *pv, *pdv, *pd2v;
+} ora_work;
+
+static int work_alloc(ora_work *W, int n, int L)
+{
+    W->c = malloc(sizeof(double complex) * n);
+    W->w = malloc(sizeof(double complex) * n);
+    W->u = malloc(sizeof(double complex) * n);
+    W->u2 = malloc(sizeof(double complex) * n);
+    W->tmp = malloc(sizeof(double complex) * n);
+    W->tmp2 = malloc(sizeof(double complex) * n);
+    W->v = malloc(sizeof(double) * L * 6);
+    if (!W->c || !W->w || !W->u || !W->u2 || !W->tmp || !W->tmp2 || !W->v) return ORA_ENOMEM;
+    W->dv = W->v + L; W->d2v = W->v + 2 * L; W->pv = W->v + 3 * L; W->pdv = W->v + 4 * L; W->pd2v = W->v + 5 * L;
+    return ORA_OK;
+}
+
+static void work_free(ora_work *W)
+{
+    free(W->c); free(W->w); free(W->u); free(W->u2); free(W->tmp); free(W->tmp2); free(W->v);
+}
+
+/* classical state q = (R, P_R, Phi, P_Phi) */
+typedef struct {
+    int flags;
+    double jy_sign; /* +1, or -1 with ORA_F_FLIP_JY */
+    double line_b, line_v, line_t0; /* prescribed straight line (ORA_F_PRESCRIBED) */
+} ora_opts;
+
+/* quantities of a right-hand-side evaluation, for the diagnostics */
+typedef struct {
+    double vc;   /* Re(c^dag M c) */
+    double jy;   /* <J_y> = Im(a^dag D a)/2 */
+    double norm; /* sum |a|^2 */
+    double erot; /* sum E |a|^2 */
+    int below;   /* R < r_min */
+} ora_eval;
+
+/* f(t, y): Eqs. 5 and 7-10 in the reading stated in the header */
+static void rhs(const ora_sys *S, const ora_opts *o, double t, const double complex *a, const double *q,
+                double complex *da, double *dq, ora_work *W, ora_eval *ev)
+{
+    int n = S->n;
+    double R = q[0], PR = q[1], PPhi = q[3], phidot;
+    if (o->flags & ORA_F_PRESCRIBED) {
+        double s = o->line_v * (t - o->line_t0);
+        R = sqrt(o->line_b * o->line_b + s * s);
+        phidot = o->line_b * o->line_v / (R * R);
+    } else {
+        phidot = PPhi / (S->mu * R * R);
+    }
+    eval_terms(S, S->coef, R, W->v, W->dv, W->d2v);
+    for (int s = 0; s < n; ++s) W->c[s] = cexp(-I * S->E[s] * t) * a[s];
+    couple(S, W->v, W->c, W->w);  /* w = M c   */
+    couple(S, W->dv, W->c, W->u); /* u = M' c  */
+    double force = 0.0, torque = 0.0;
+    for (int s = 0; s < n; ++s) {
+        force -= creal(conj(W->c[s]) * W->u[s]);
+        torque += creal(conj(W->c[s]) * ladder(S, W->w, s));
+    }
+    force += PPhi * PPhi / (S->mu * R * R * R);
+    torque *= o->jy_sign;
+    if (o->flags & ORA_F_PLANT_TORQUE) torque = -torque;
+    double kc = (o->flags & ORA_F_PLANT_CORIOLIS) ? 1.0 : 0.5;
+    for (int s = 0; s < n; ++s)
+        da[s] = -I * cexp(I * S->E[s] * t) * W->w[s] + o->jy_sign * kc * phidot * ladder(S, a, s);
+    if (o->flags & ORA_F_PRESCRIBED) {
+        dq[0] = dq[1] = dq[2] = dq[3] = 0.0;
+    } else {
+        dq[0] = PR / S->mu;
+        dq[1] = force;
+        dq[2] = phidot;
+        dq[3] = torque;
+    }
+    if (ev) {
+        double vc = 0.0, jy = 0.0, nrm = 0.0, er = 0.0;
+        for (int s = 0; s < n; ++s) {
+            vc += creal(conj(W->c[s]) * W->w[s]);
+            jy += cimag(conj(a[s]) * ladder(S, a, s));
+            double p = creal(a[s]) * creal(a[s]) + cimag(a[s]) * cimag(a[s]);
+            nrm += p;
+            er += S->E[s] * p;
+        }
+        ev->vc = vc;
+        ev->jy = 0.5 * o->jy_sign * jy;
+        ev->norm = nrm;
+        ev->erot = er;
+        ev->below = R < S->r_min;
+    }
+}
+
+static double total_energy(const ora_sys *S, const double *q, const ora_eval *ev)
+{
+    double R = q[0];
+    return q[1] * q[1] / (2.0 * S->mu) + q[3] * q[3] / (2.0 * S->mu * R * R) + ev->erot + ev->vc;
+}
+
+static int finite_state(int n, const double complex *a, const double *q)
+{
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(q[i])) return 0;
+    for (int s = 0; s < n; ++s)
+        if (!isfinite(creal(a[s])) || !isfinite(cimag(a[s]))) return 0;
+    return 1;
+}
+
+static void initial_state(const ora_sys *S, const ora_traj *tr, double complex *a, double *q, double *m00_out)
+{
+    for (int s = 0; s < S->n; ++s) a[s] = 0.0;
+    a[tr->init_state] = 1.0;
+    /* diagonal coupling of the initial state at R0 */
+    double *pv = malloc(sizeof(double) * 3 * S->L);
+    eval_terms(S, S->coef, tr->r0, pv, pv + S->L, pv + 2 * S->L);
+    int s0 = tr->init_state, b = -1, r = -1;
+    for (int q2 = 0; q2 < S->n_blk && b < 0; ++q2)
+        for (int i = 0; i < S->blk_size[q2]; ++i)
+            if (S->members[S->blk_start[q2] + i] == s0) { b = q2; r = i; }
+    int sz = S->blk_size[b];
+    double m00 = 0.0;
+    for (int l = 0; l < S->L; ++l) m00 += pv[l] * S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + r];
+    free(pv);
+    double lz = tr->b * sqrt(2.0 * S->mu * tr->e_coll);
+    q[0] = tr->r0;
+    q[2] = 0.0;
+    q[3] = lz;
+    q[1] = -sqrt(2.0 * S->mu * (tr->e_coll - m00) - lz * lz / (tr->r0 * tr->r0));
+    if (m00_out) *m00_out = m00;
+}
+
+static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o, double complex *a_out, ora_result *res)
+{
+    int n = S->n, status = 0;
+    ora_work W;
+    double complex *a = malloc(sizeof(double complex) * n * 6);
+    if (!a || work_alloc(&W, n, S->L)) { free(a); work_free(&W); return ORA_ENOMEM; }
+    double complex *k1 = a + n, *k2 = a + 2 * n, *k3 = a + 3 * n, *k4 = a + 4 * n, *ys = a + 5 * n;
+    double q[4], qs[4], l1[4], l2[4], l3[4], l4[4];
+    initial_state(S, tr, a, q, NULL);
+    if (o->flags & ORA_F_PRESCRIBED) {
+        double s = o->line_v * (0.0 - o->line_t0);
+        q[0] = sqrt(o->line_b * o->line_b + s * s);
+        q[1] = q[2] = q[3] = 0.0;
+    }
+    double dt = tr->dt, e0 = 0.0, j0 = 0.0, ndev = 0.0, edev = 0.0, jdev = 0.0;
+    ora_eval ev;
+    int steps = 0, stopped = 0;
+    for (int step = 0; step < tr->max_steps; ++step) {
+        double t = step * dt;
+        rhs(S, o, t, a, q, k1, l1, &W, &ev);
+        if (ev.below) status |= ORA_ST_TABLE_RANGE;
+        {
+            double et = total_energy(S, q, &ev), jt = q[3] + ev.jy;
+            if (step == 0) { e0 = et; j0 = jt; }
+            if (fabs(ev.norm - 1.0) > ndev) ndev = fabs(ev.norm - 1.0);
+            if (fabs(et - e0) > edev) edev = fabs(et - e0);
+            if (fabs(jt - j0) > jdev) jdev = fabs(jt - j0);
+        }
+        for (int s = 0; s < n; ++s) ys[s] = a[s] + 0.5 * dt * k1[s];
+        for (int i = 0; i < 4; ++i) qs[i] = q[i] + 0.5 * dt * l1[i];
+        rhs(S, o, t + 0.5 * dt, ys, qs, k2, l2, &W, &ev);
+        if (ev.below) status |= ORA_ST_TABLE_RANGE;
+        for (int s = 0; s < n; ++s) ys[s] = a[s] + 0.5 * dt * k2[s];
+        for (int i = 0; i < 4; ++i) qs[i] = q[i] + 0.5 * dt * l2[i];
+        rhs(S, o, t + 0.5 * dt, ys, qs, k3, l3, &W, &ev);
+        if (ev.below) status |= ORA_ST_TABLE_RANGE;
+        for (int s = 0; s < n; ++s) ys[s] = a[s] + dt * k3[s];
+        for (int i = 0; i < 4; ++i) qs[i] = q[i] + dt * l3[i];
+        rhs(S, o, t + dt, ys, qs, k4, l4, &W, &ev);
+        if (ev.below) status |= ORA_ST_TABLE_RANGE;
+        for (int s = 0; s < n; ++s) a[s] += dt / 6.0 * (k1[s] + 2.0 * k2[s] + 2.0 * k3[s] + k4[s]);
+        for (int i = 0; i < 4; ++i) q[i] += dt / 6.0 * (l1[i] + 2.0 * l2[i] + 2.0 * l3[i] + l4[i]);
+        if (o->flags & ORA_F_PRESCRIBED) {
+            double s = o->line_v * ((step + 1) * dt - o->line_t0);
+            q[0] = sqrt(o->line_b * o->line_b + s * s);
+        }
+        steps = step + 1;
+        if (!finite_state(n, a, q)) { status |= ORA_ST_NONFINITE; stopped = 1; break; }
+        if (!(o->flags & (ORA_F_NO_STOP | ORA_F_PRESCRIBED)) && q[0] >= tr->r_end && q[1] > 0.0) { stopped = 1; break; }
+    }
+    if (!stopped) status |= ORA_ST_MAX_STEPS;
+    if (!(status & ORA_ST_NONFINITE)) {
+        /* diagnostics of the final state */
+        rhs(S, o, steps * dt, a, q, k1, l1, &W, &ev);
+        double et = total_energy(S, q, &ev), jt = q[3] + ev.jy;
+        if (steps == 0) { e0 = et; j0 = jt; }
+        if (fabs(ev.norm - 1.0) > ndev) ndev = fabs(ev.norm - 1.0);
+        if (fabs(et - e0) > edev) edev = fabs(et - e0);
+        if (fabs(jt - j0) > jdev) jdev = fabs(jt - j0);
+    }
+    for (int s = 0; s < n; ++s) a_out[s] = a[s];
+    res->steps = steps;
+    res->status = status;
+    res->norm_dev = ndev;
+    res->energy_dev = edev;
+    res->angmom_dev = jdev;
+    res->t_final = steps * dt;
+    res->R = q[0]; res->PR = q[1]; res->Phi = q[2]; res->PPhi = q[3];
+    free(a);
+    work_free(&W);
+    return ORA_OK;
+}
+
+/* Propagate n_traj trajectories (Sec. II / III).  final_amp: [n_traj][n] complex (interleaved re, im).
+ * line_speed: prescribed-line speed per trajectory (only with ORA_F_PRESCRIBED; the line is
+ * time-symmetric about max_steps*dt/2 with impact parameter b). */
+int ora_propagate(const ora_system_desc *d, const ora_traj *tr, int n_traj, int flags, const double *line_speed,
+                  int n_threads, double *final_amp, ora_result *res)
+{
+    ora_sys S;
+    int e = sys_build(d, &S);
+    if (e) return e;
+    for (int i = 0; i < n_traj; ++i)
+        if (tr[i].init_state < 0 || tr[i].init_state >= d->n || !(tr[i].dt > 0) || tr[i].max_steps < 0) {
+            sys_free(&S);
+            return ORA_EINVAL;
+        }
+    int err = 0;
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int i = 0; i < n_traj; ++i) {
+        ora_opts o;
+        o.flags = flags;
+        o.jy_sign = (flags & ORA_F_FLIP_JY) ? -1.0 : 1.0;
+        o.line_b = tr[i].b;
+        o.line_v = line_speed ? line_speed[i] : 0.0;
+        o.line_t0 = 0.5 * tr[i].max_steps * tr[i].dt;
+        if (propagate_one(&S, tr + i, &o, (double complex *)(final_amp + 2 * (size_t)i * d->n), res + i))
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = ORA_ENOMEM;
+    }
+    sys_free(&S);
+    return err;
+}
+
+/* ------------------------------------------------------------------ */
+/* Forward tangent: exact derivative of the same discrete RK4 map with */
+/* respect to the parameters whose dv_lambda/dtheta tables are given.  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double complex *da;
+    double dq[4];
+} tan_state;
+
+/* tangent right-hand side for parameter p: given (a, q), the tangents (ta, tq) and the forward
+ * quantities already in W (c, w = M c, u = M' c) */
+static void rhs_tangent(const ora_sys *S, const ora_opts *o, double t, int p, const double complex *a, const double *q,
+                        const double complex *ta, const double *tq, double complex *dta, double *dtq, ora_work *W,
+                        double complex *tc, double complex *tw, double complex *tu, double complex *scr)
+{
+    int n = S->n, L = S->L;
+    double R = q[0], PPhi = q[3], mu = S->mu;
+    double phidot = PPhi / (mu * R * R);
+    double tphidot = tq[3] / (mu * R * R) - 2.0 * PPhi * tq[0] / (mu * R * R * R);
+    eval_terms(S, S->dcoef + (size_t)p * L * S->n_int * 4, R, W->pv, W->pdv, W->pd2v);
+    for (int s = 0; s < n; ++s) tc[s] = cexp(-I * S->E[s] * t) * ta[s];
+    /* tw = M tc + tR M' c + M_theta c */
+    couple(S, W->v, tc, tw);
+    couple(S, W->pv, W->c, scr);
+    for (int s = 0; s < n; ++s) tw[s] += tq[0] * W->u[s] + scr[s];
+    /* tu = M' tc + tR M'' c + M'_theta c */
+    couple(S, W->dv, tc, tu);
+    couple(S, W->pdv, W->c, scr);
+    for (int s = 0; s < n; ++s) tu[s] += tq[0] * W->u2[s] + scr[s];
+    double tforce = 0.0, ttorque = 0.0;
+    for (int s = 0; s < n; ++s) {
+        tforce -= creal(conj(tc[s]) * W->u[s] + conj(W->c[s]) * tu[s]);
+        ttorque += creal(conj(tc[s]) * ladder(S, W->w, s) + conj(W->c[s]) * ladder(S, tw, s));
+    }
+    tforce += 2.0 * PPhi * tq[3] / (mu * R * R * R) - 3.0 * PPhi * PPhi * tq[0] / (mu * R * R * R * R);
+    ttorque *= o->jy_sign;
+    for (int s = 0; s < n; ++s)
+        dta[s] = -I * cexp(I * S->E[s] * t) * tw[s] +
+                 o->jy_sign * 0.5 * (tphidot * ladder(S, a, s) + phidot * ladder(S, ta, s));
+    dtq[0] = tq[1] / mu;
+    dtq[1] = tforce;
+    dtq[2] = tphidot;
+    dtq[3] = ttorque;
+}
+
+static int tangent_one(const ora_sys *S, const ora_traj *tr, double complex *a_out, double *dpop, ora_result *res)
+{
+    int n = S->n, P = S->P;
+    ora_opts o;
+    memset(&o, 0, sizeof(o));
+    o.jy_sign = 1.0;
+    ora_work W;
+    if (work_alloc(&W, n, S->L)) { work_free(&W); return ORA_ENOMEM; }
+    size_t na = (size_t)n;
+    /* forward: a, k1..k4, ys; tangents: ta[P], tk[4][P], tys; scratch */
+    double complex *buf = malloc(sizeof(double complex) * na * (6 + 6 * (size_t)P + 4));
+    double *tqbuf = malloc(sizeof(double) * 4 * 6 * (size_t)(P > 0 ? P : 1));
+    if (!buf || !tqbuf) { free(buf); free(tqbuf); work_free(&W); return ORA_ENOMEM; }
+    double complex *a = buf, *k[4] = {buf + na, buf + 2 * na, buf + 3 * na, buf + 4 * na}, *ys = buf + 5 * na;
+    double complex *ta = buf + 6 * na;                          /* [P][n]    */
+    double complex *tk = ta + (size_t)P * na;                   /* [4][P][n] */
+    double complex *tys = tk + 4 * (size_t)P * na;              /* [P][n]    */
+    double complex *tc = tys + (size_t)P * na, *tw = tc + na, *tu = tw + na, *scr = tu + na;
+    double *tq = tqbuf, *tl = tqbuf + 4 * P, *tqs = tqbuf + 20 * P; /* tq[P][4], tl[4][P][4], tqs[P][4] */
+    double q[4], qs[4], l[4][4];
+    double m00;
+    initial_state(S, tr, a, q, &m00);
+    /* tangent of the initial state: only P_R depends on theta through M_s0s0(R0) */
+    memset(ta, 0, sizeof(double complex) * (size_t)P * na);
+    memset(tq, 0, sizeof(double) * 4 * P);
+    {
+        int s0 = tr->init_state, b = -1, r = -1;
+        for (int q2 = 0; q2 < S->n_blk && b < 0; ++q2)
+            for (int i = 0; i < S->blk_size[q2]; ++i)
+                if (S->members[S->blk_start[q2] + i] == s0) { b = q2; r = i; }
+        int sz = S->blk_size[b];
+        for (int p = 0; p < P; ++p) {
+            eval_terms(S, S->dcoef + (size_t)p * S->L * S->n_int * 4, tr->r0, W.pv, W.pdv, W.pd2v);
+            double dm00 = 0.0;
+            for (int l2 = 0; l2 < S->L; ++l2) dm00 += W.pv[l2] * S->Gb[S->blk_goff[b] + ((size_t)l2 * sz + r) * sz + r];
+            tq[4 * p + 1] = -S->mu * dm00 / q[1];
+        }
+    }
+    double dt = tr->dt;
+    int steps = 0, stopped = 0, status = 0;
+    static const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int step = 0; step < tr->max_steps; ++step) {
+        double t = step * dt;
+        for (int st = 0; st < 4; ++st) {
+            double ts = t + cst[st] * dt;
+            const double complex *ya = a;
+            const double *yq = q;
+            if (st > 0) {
+                double f = cst[st] * dt;
+                for (int s = 0; s < n; ++s) ys[s] = a[s] + f * k[st - 1][s];
+                for (int i = 0; i < 4; ++i) qs[i] = q[i] + f * l[st - 1][i];
+                for (int p = 0; p < P; ++p) {
+                    for (int s = 0; s < n; ++s)
+                        tys[(size_t)p * na + s] = ta[(size_t)p * na + s] + f * tk[((size_t)(st - 1) * P + p) * na + s];
+                    for (int i = 0; i < 4; ++i) tqs[4 * p + i] = tq[4 * p + i] + f * tl[((st - 1) * P + p) * 4 + i];
+                }
+                ya = ys;
+                yq = qs;
+            } else {
+                memcpy(tys, ta, sizeof(double complex) * (size_t)P * na);
+                memcpy(tqs, tq, sizeof(double) * 4 * P);
+            }
+            ora_eval ev;
+            rhs(S, &o, ts, ya, yq, k[st], l[st], &W, &ev);
+            if (ev.below) status |= ORA_ST_TABLE_RANGE;
+            couple(S, W.d2v, W.c, W.u2); /* M'' c for the tangents */
+            for (int p = 0; p < P; ++p)
+                rhs_tangent(S, &o, ts, p, ya, yq, tys + (size_t)p * na, tqs + 4 * p,
+                            tk + ((size_t)st * P + p) * na, tl + (st * P + p) * 4, &W, tc, tw, tu, scr);
+        }
+        for (int s = 0; s < n; ++s) a[s] += dt / 6.0 * (k[0][s] + 2.0 * k[1][s] + 2.0 * k[2][s] + k[3][s]);
+        for (int i = 0; i < 4; ++i) q[i] += dt / 6.0 * (l[0][i] + 2.0 * l[1][i] + 2.0 * l[2][i] + l[3][i]);
+        for (int p = 0; p < P; ++p) {
+            for (int s = 0; s < n; ++s) {
+                size_t o2 = (size_t)p * na + s;
+                ta[o2] += dt / 6.0 * (tk[o2] + 2.0 * tk[(size_t)P * na + o2] + 2.0 * tk[2 * (size_t)P * na + o2] +
+                                      tk[3 * (size_t)P * na + o2]);
+            }
+            for (int i = 0; i < 4; ++i)
+                tq[4 * p + i] += dt / 6.0 * (tl[(0 * P + p) * 4 + i] + 2.0 * tl[(1 * P + p) * 4 + i] +
+                                             2.0 * tl[(2 * P + p) * 4 + i] + tl[(3 * P + p) * 4 + i]);
+        }
+        steps = step + 1;
+        if (!finite_state(n, a, q)) { status |= ORA_ST_NONFINITE; stopped = 1; break; }
+        if (q[0] >= tr->r_end && q[1] > 0.0) { stopped = 1; break; }
+    }
+    if (!stopped) status |= ORA_ST_MAX_STEPS;
+    for (int s = 0; s < n; ++s) a_out[s] = a[s];
+    /* d|a_s|^2 / d theta_p = 2 Re(conj(a_s) ta_s) */
+    for (int p = 0; p < P; ++p)
+        for (int s = 0; s < n; ++s) dpop[(size_t)p * n + s] = 2.0 * creal(conj(a[s]) * ta[(size_t)p * na + s]);
+    memset(res, 0, sizeof(*res));
+    res->steps = steps;
+    res->status = status;
+    res->t_final = steps * dt;
+    res->R = q[0]; res->PR = q[1]; res->Phi = q[2]; res->PPhi = q[3];
+    free(buf);
+    free(tqbuf);
+    work_free(&W);
+    return ORA_OK;
+}
+
+/* final amplitudes and d|a|^2/dtheta: dpop[n_traj][P][n] */
+int ora_tangent(const ora_system_desc *d, const ora_traj *tr, int n_traj, int n_threads, double *final_amp,
+                double *dpop, ora_result *res)
+{
+    if (d->n_params < 1 || !d->dvp || !d->dvp_ends) return ORA_EINVAL;
+    ora_sys S;
+    int e = sys_build(d, &S);
+    if (e) return e;
+    for (int i = 0; i < n_traj; ++i)
+        if (tr[i].init_state < 0 || tr[i].init_state >= d->n || !(tr[i].dt > 0) || tr[i].max_steps < 0) {
+            sys_free(&S);
+            return ORA_EINVAL;
+        }
+    int err = 0;
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int i = 0; i < n_traj; ++i)
+        if (tangent_one(&S, tr + i, (double complex *)(final_amp + 2 * (size_t)i * d->n),
+                        dpop + (size_t)i * d->n_params * d->n, res + i))
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = ORA_ENOMEM;
+    sys_free(&S);
+    return err;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cross sections (Sec. II): populations summed over the final level,  */
+/* weighted (impact-parameter quadrature and initial-m average) and    */
+/* summed over the trajectories of each group.                         */
+/* ------------------------------------------------------------------ */
+void ora_cross_sections(int n, const int *level, int n_levels, int n_traj, const double *pop, const double *weight,
+                        const int *group, int n_groups, double *sigma)
+{
+    memset(sigma, 0, sizeof(double) * (size_t)n_groups * n_levels);
+    for (int t = 0; t < n_traj; ++t) {
+        if (group[t] < 0 || group[t] >= n_groups) continue;
+        for (int s = 0; s < n; ++s)
+            sigma[(size_t)group[t] * n_levels + level[s]] += weight[t] * pop[(size_t)t * n + s];
+    }
+}
+
+int ora_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
