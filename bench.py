@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""MQCT trajectory-steps/s on one GB300 (and N GPUs as independent replicas).
+
+Workload: the N = 441 atom + diatom system (j <= 20), E in {100, 300, 1000, 3000} cm^-1,
+j' in {0, 1, 2}, 256 midpoint impact parameters on 0-15 bohr per (E, j'): 3072
+trajectories, 400-point spline grid, RK4 dt = 5 a.u.  One step = propagate every
+trajectory to its end (Eqs. 4-10) plus the cross-section reduction (Sec. II), inputs
+resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--path plain|factorised] [--precision fp64|fp32]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_02322_gb300 import inputs as W  # noqa: E402
+
+METRIC = "MQCT trajectory-steps/s at N=441/1600, batched mixed vs plain FP64, same error"
+WORKLOAD = "diatom j<=20 (N=441), 3072 trajectories: E in {100,300,1000,3000} cm^-1 x j' in {0,1,2} x 256 b on 0-15 bohr"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--path", default="plain", choices=["plain", "factorised"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-traj", type=int, default=0,
+                    help="run a seeded subset of this many trajectories (profiling of a small case)")
+    ap.add_argument("--energy", type=float, default=0.0,
+                    help="keep only the trajectories at this collision energy (cm^-1)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def oracle_sample(p, ts, n_sample, seed=11):
+    """Bounded, seeded sample of the workload: n_sample trajectories stratified over the
+    collision energies (the step count per trajectory depends mostly on E)."""
+    rng = np.random.default_rng(seed)
+    es = np.unique(ts.e_coll)
+    per = max(1, n_sample // len(es))
+    pick = np.concatenate([rng.choice(np.flatnonzero(ts.e_coll == e), per, replace=False) for e in es])
+    return ts.subset(np.sort(pick))
+
+
+def run_oracle(p, sub, threads):
+    import oracle
+
+    oracle.build()
+    osys = oracle.diatom_system(p.jmax, p.bconst, p.mu, p.A, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max)
+    init = [j * j + j + m for j, m in zip(sub.init_j, sub.init_m)]
+    t0 = time.perf_counter()
+    amp, res = oracle.propagate(osys, sub.e_coll, sub.b, init, r0=sub.r0, r_end=sub.r_end, dt=sub.dt,
+                                max_steps=sub.max_steps, n_threads=threads)
+    t1 = time.perf_counter()
+    return float(res["steps"].sum()), t1 - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------- reference arm
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    p, ts = W.workload2()
+    sub = oracle_sample(p, ts, 16)
+    cores = cpu_cores()
+    for _ in range(args.warmup):
+        run_oracle(p, oracle_sample(p, ts, 4, seed=99), cores)
+    steps_tot, t_tot = 0.0, 0.0
+    for _ in range(args.steps):
+        s, t = run_oracle(p, sub, cores)
+        steps_tot += s
+        t_tot += t
+    v = steps_tot / t_tot
+    sample = f"{sub.n} trajectories of the workload (4 per collision energy, seeded) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "traj-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "traj-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "traj-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2312_02322_gb300 import api, build
+
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p, ts = W.workload2()
+    workload = WORKLOAD
+    if args.energy:
+        ts = ts.subset(np.flatnonzero(np.isclose(ts.e_coll, float(W.cm(args.energy)))))
+        workload = f"E = {args.energy} cm^-1 part of: {WORKLOAD}"
+    if args.max_traj:
+        ts = oracle_sample(p, ts, args.max_traj, seed=5)
+        workload = f"seeded subset of {ts.n} trajectories of: {workload}"
+    sys_ = api.System.diatom(p, path=args.path, precision=args.precision)
+    info = sys_.info
+    tr = api.make_trajs(ts, sys_)
+    trd = torch.from_numpy(tr.view(np.uint8).copy()).to(dev)
+    group_d = torch.from_numpy(ts.group.astype(np.int32)).to(dev)
+
+    # first pass: step counts and statuses (identical on every pass: the work is deterministic)
+    pop, _, diag = api.propagate(sys_, trd, device=True, stream=stream)
+    torch.cuda.synchronize()
+    dg = api.diag_to_numpy(diag)
+    w = api.sigma_weights(ts, dg["status"])
+    w_d = torch.from_numpy(w).to(dev)
+    traj_steps = float(dg["steps"].sum())
+    n_bad = int(np.count_nonzero(dg["status"] & (api.TRAJ_MAX_STEPS | api.TRAJ_NONFINITE)))
+
+    def step():
+        pop, _, _ = api.propagate(sys_, trd, want_diag=False, device=True, stream=stream)
+        return api.cross_sections(sys_, pop, w_d, group_d, ts.n_groups, stream=stream)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    value = traj_steps * ws / (ms * 1e-3 / args.steps)
+
+    # dominant kernel (the persistent RK4 launch): timed alone, same stream
+    kt = []
+    for _ in range(max(2, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        api.propagate(sys_, trd, want_diag=False, device=True, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        kt.append(a.elapsed_time(b))
+    k_ms = float(np.mean(kt))
+    stages = 4.0 * traj_steps + ts.n  # four RK4 stages per step + one final diagnostic evaluation
+    n = info["n_states"]
+    if args.path == "plain":
+        flops_stage = 16.0 * info["table_nnz"] + 40.0 * n
+        bytes_stage = 32.0 * info["table_nnz"] * (1.0 if args.precision == "fp64" else 0.5)
+    else:
+        flops_stage = 4.0 * info["glambda_nnz"] + (8.0 * p.n_terms + 40.0) * n
+        bytes_stage = 0.0
+    fp64_peak = api.fma_rate("fp64") if args.precision == "fp64" else api.fma_rate("fp32")
+    achieved = flops_stage * stages / (k_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
+                "frac": achieved * 1e3 / fp64_peak, "traffic": None,
+                "kernel": "k_propagate_fp64", "peak_source": f"measured {args.precision.upper()} FMA probe (mqct_probe_fma_rate)",
+                "algorithmic_flops_per_traj_stage": flops_stage, "traj_stages_per_launch": stages,
+                "kernel_ms": k_ms}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = peaks.get("hbm_gbs")
+    except Exception:
+        hbm = None
+    if bytes_stage and hbm:
+        gbs = bytes_stage * stages / (k_ms * 1e-3) / 1e9
+        roofline["hbm_view"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                                "note": "algorithmic table bytes; the table is L2-resident, so DRAM traffic is lower"}
+
+    # end-to-end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        tr_pin = torch.from_numpy(tr.view(np.uint8).copy()).pin_memory()
+        tr_host = tr_pin.numpy().view(api.TRAJ_DTYPE)
+        pop_h = np.zeros((ts.n, n))
+        e_ms = []
+        for k in range(max(1, min(args.steps, 2))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pop_h, _, diag_h = api.propagate(sys_, tr_host, device=False, stream=stream)
+            sig = api.cross_sections(sys_, pop_h, w, ts.group, ts.n_groups, stream=stream)
+            e_ms.append(1e3 * (time.perf_counter() - t0))
+        e_ms_step = float(np.mean(e_ms))
+        h2d = tr.nbytes + pop_h.nbytes + w.nbytes + ts.group.astype(np.int32).nbytes
+        d2h = pop_h.nbytes + ts.n * api.DIAG_DTYPE.itemsize + sig.nbytes
+        e2e = {"value": traj_steps * ws / (e_ms_step * 1e-3), "unit": "traj-steps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms_step}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sub = oracle_sample(p, ts, 16)
+        cores = cpu_cores()
+        s, t = run_oracle(p, sub, cores)
+        cpu = {"value": s / t, "unit": "traj-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{sub.n} trajectories of the workload (4 per collision energy, seeded), {int(s)} traj-steps"}
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    launches_per_step = 4  # order keys, persistent RK4, level sums, group sums (plus CUB's radix-sort passes)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": workload, "path": args.path, "precision": args.precision, "n_states": n,
+                   "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,
+                   "l2": "flushed (256 MB write) before every timed step", "seed": W.DEFAULT_SEED},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

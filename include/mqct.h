@@ -1,0 +1,232 @@
+/*
+ * mqct.h -- C ABI of the GB300 MQCT trajectory library.
+ *
+ * The library propagates many mixed quantum/classical (Ehrenfest mean-field)
+ * trajectories of an atom + rigid rotor collision on one GPU and turns their
+ * final state populations into state-to-state cross sections, following
+ * Joy, Mandal, Bostan, Dubernet & Babikov, arXiv 2312.02322:
+ *
+ *   Eq. 4     a_n(t): amplitudes in the interaction picture, c_n = exp(-i E_n t) a_n
+ *   Eq. 5     da/dt = -i exp(iEt) M(R) c  +  (dPhi/dt / 2) (J+ - J-) a      (Coriolis, m +- 1)
+ *   Eq. 6     M(R): real, symmetric, block-diagonal in m
+ *   Eqs. 7-10 dR/dt = P_R/mu, dPhi/dt = P_Phi/(mu R^2),
+ *             dP_R/dt = -Re(c^dag M'(R) c) + P_Phi^2/(mu R^3),
+ *             dP_Phi/dt = Re(c^dag (J+ - J-) M(R) c)
+ *   Eq. 12    M(R) = sum_lambda v_lambda(R) G^lambda   (angular expansion of the PES)
+ *   Sec. III  v_lambda(R) (and thus M(R)) interpolated by cubic splines on an R grid
+ *   Sec. II   cross sections: final |a|^2 summed over the final level, averaged over the
+ *             initial degenerate states and integrated over impact parameter
+ *
+ * Conventions shared by every call:
+ *   - atomic units throughout: hartree, bohr, electron masses, atomic units of time;
+ *   - arrays are C-contiguous, row-major; "[A][B]" means A slow, B fast;
+ *   - a pointer argument may be a host or a device pointer unless stated otherwise
+ *     (the library asks the CUDA driver which one it is);
+ *   - the caller keeps ownership of every array it passes; nothing is retained after
+ *     the call returns except what mqct_create_system copies into the system;
+ *   - no call aborts the process or traps the GPU: failures are reported by the
+ *     returned status and a thread-local message (mqct_last_error);
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Readings of the paper where its printed text is garbled or silent:
+ *   - Coriolis term of Eq. 5: the anti-Hermitian form above, i.e. the quantum
+ *     Hamiltonian H_rot + V - dPhi/dt J_y, J_y = (J+ - J-)/(2i);
+ *   - torque of Eq. 10: i<[J_y, V]> = Re(c^dag (J+ - J-) M c), the form for which the
+ *     total energy and P_Phi + <J_y> are conserved;
+ *   - initial state: a = e_{init_state}, R = r0, Phi = 0, P_Phi = b sqrt(2 mu E),
+ *     P_R = -sqrt(2 mu (E - M_ss(r0)) - P_Phi^2 / r0^2);
+ *   - splines: clamped cubic on a uniform grid; interval k = floor((R - r_min)/h) clamped
+ *     to [0, n_grid-2]; outside the grid the end cubic is extrapolated;
+ *   - integrator: classical 4-stage RK4 with fixed dt, stage times t, t+dt/2, t+dt/2, t+dt,
+ *     t = n dt; a trajectory ends after the first step that ends with R >= r_end and
+ *     P_R > 0, or after max_steps steps.
+ */
+#ifndef MQCT_H
+#define MQCT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mqct_system_s *mqct_system; /* opaque; owns all of its device memory */
+
+typedef enum {
+    MQCT_OK = 0,
+    MQCT_ERR_INVALID_ARG = 1, /* a size, pointer or value failed validation           */
+    MQCT_ERR_OOM = 2,         /* host or device allocation failed                      */
+    MQCT_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    MQCT_ERR_UNSUPPORTED = 4, /* combination of options not implemented                */
+    MQCT_ERR_TIMEOUT = 5,     /* a bounded device wait ran out                          */
+    MQCT_ERR_TRAJ = 6         /* the call ran, but at least one trajectory status != 0 */
+} mqct_status;
+
+/* Coupling evaluation (both are the same mathematics, Eq. 12 and Sec. III):
+ *   PLAIN:      spline table of every structurally non-zero M_nm(R) (M is block-diagonal
+ *               in m, Eq. 6), evaluated per trajectory and fused with the mat-vec;
+ *   FACTORISED: M(R) c = sum_lambda v_lambda(R) (G^lambda c), G^lambda constant. */
+typedef enum { MQCT_PATH_PLAIN = 0, MQCT_PATH_FACTORISED = 1 } mqct_path;
+
+/* Precision of the amplitudes and of the coupling contraction.  Phase arguments E_n t,
+ * the classical variables and the conserved-quantity bookkeeping are FP64 in every mode. */
+typedef enum { MQCT_FP64 = 0, MQCT_FP32 = 1, MQCT_BF16X3 = 2 } mqct_precision;
+
+/* per-trajectory status bits (mqct_diag.status) */
+#define MQCT_TRAJ_MAX_STEPS 1   /* max_steps reached before the stop rule (e.g. orbiting)   */
+#define MQCT_TRAJ_TABLE_RANGE 2 /* some stage had R < r_min (end cubic extrapolated)        */
+#define MQCT_TRAJ_NONFINITE 4   /* a non-finite value appeared; the trajectory was stopped  */
+#define MQCT_TRAJ_TIMEOUT 8     /* a bounded device wait ran out while running it           */
+#define MQCT_TRAJ_INVALID 16    /* device-resident trajectory failed validation; not run    */
+
+/* Description of one atom + rotor system.  All pointers are HOST pointers, read and
+ * copied during mqct_create_system only. */
+typedef struct {
+    int32_t n_states;        /* N >= 1                                                        */
+    const double *energy;    /* [N] internal energies E_n (hartree); equal within a level    */
+    const int32_t *level;    /* [N] non-degenerate level id in [0, n_levels); sigma is per level */
+    const int32_t *j;        /* [N] angular momentum label for the Coriolis ladder;
+                                j < 0 switches the Coriolis term off for the state            */
+    const int32_t *m;        /* [N] projection m (|m| <= j when j >= 0); M is block-diagonal in m */
+    double mu;               /* reduced mass (electron masses), > 0                          */
+    int32_t n_terms;         /* L >= 1 expansion terms of Eq. 12                             */
+    const double *G;         /* [L][N][N] real symmetric G^lambda, or NULL to use triplets   */
+    int64_t g_nnz;           /* triplet form (used when G == NULL): entries (term,row,col,val); */
+    const int32_t *g_term;   /*   each stored entry of a symmetric matrix must appear for both */
+    const int32_t *g_row;    /*   (row,col) and (col,row); duplicates are summed              */
+    const int32_t *g_col;
+    const double *g_val;
+    int32_t n_grid;          /* >= 4 uniform grid points R_k = r_min + k (r_max-r_min)/(n_grid-1) */
+    double r_min, r_max;
+    const double *v;         /* [L][n_grid] v_lambda(R_k) (hartree)                          */
+    const double *dv_ends;   /* [L][2] dv_lambda/dR at r_min and r_max (clamped spline)      */
+    int32_t n_params;        /* P >= 0 parameters theta for mqct_adjoint                     */
+    const double *dv_dparam; /* [P][L][n_grid] d v_lambda(R_k) / d theta_p, or NULL if P = 0 */
+    const double *ddv_ends;  /* [P][L][2] their R-derivatives at both ends                   */
+    int32_t path;            /* mqct_path                                                    */
+    int32_t precision;       /* mqct_precision                                               */
+    int32_t flags;           /* reserved, must be 0                                          */
+} mqct_system_desc;
+
+/* One trajectory (Sec. III: collision energy, impact parameter, initial state). */
+typedef struct {
+    double e_coll;      /* collision energy (hartree), > 0                     */
+    double b;           /* impact parameter (bohr), >= 0                       */
+    double r0;          /* initial R (bohr), > 0                               */
+    double r_end;       /* stop once R >= r_end with P_R > 0                   */
+    double dt;          /* RK4 step (a.u. of time), > 0                        */
+    int32_t init_state; /* index in [0, N) of the system's caller state order  */
+    int32_t max_steps;  /* >= 0                                                */
+    int32_t system_idx; /* index into the `systems` array of mqct_propagate    */
+} mqct_traj;
+
+/* Per-trajectory diagnostics.  Deviations are maxima over the states at the start of
+ * every step and the final state: | sum|a|^2 - 1 |, | E_tot - E_tot(0) | with
+ * E_tot = P_R^2/(2mu) + P_Phi^2/(2mu R^2) + sum E|a|^2 + Re(c^dag M c), and
+ * | (P_Phi + <J_y>) - (P_Phi + <J_y>)(0) |. */
+typedef struct {
+    int32_t steps;   /* RK4 steps taken                 */
+    int32_t status;  /* MQCT_TRAJ_* bits; 0 = OK        */
+    double norm_dev;
+    double energy_dev;
+    double angmom_dev;
+    double t_final;  /* steps * dt                       */
+} mqct_diag;
+
+/* Read-only facts about a created system (host struct filled by mqct_system_info). */
+typedef struct {
+    int32_t n_states, n_levels, n_terms, n_grid, n_blocks, max_block;
+    int32_t path, precision;
+    int64_t table_nnz;        /* PLAIN: structurally non-zero M_nm per interval          */
+    int64_t table_bytes;      /* PLAIN: device bytes of the spline table                 */
+    int64_t glambda_nnz;      /* FACTORISED: sum over lambda of non-zero G^lambda entries */
+    int64_t device_bytes;     /* all device memory the system owns                        */
+} mqct_system_info_t;
+
+/* Parameters of the built-in atom + linear rotor system (helper for users and tests):
+ * E_j = B j (j+1), states (j, m) for j <= jmax in j-major order s = j^2 + j + m,
+ * V(R, theta) = sum_l A_l exp(-beta_l R) P_l(cos theta) - C6 R^-6 (1 - exp(-(R/Rd)^6)),
+ * G^lambda_{(j''m),(j'm)} = <j'' m|P_lambda|j' m> (Eq. 15).  With with_params != 0 the
+ * derivative tables for theta = (A_0..A_{L-1}, beta_0..beta_{L-1}) are filled (P = 2L). */
+typedef struct {
+    int32_t jmax;
+    double bconst;       /* hartree            */
+    double mu;           /* electron masses    */
+    int32_t n_terms;     /* L <= 16            */
+    double A[16];        /* hartree            */
+    double beta[16];     /* 1/bohr             */
+    double c6;           /* hartree bohr^6     */
+    double rd;           /* bohr               */
+    int32_t n_grid;
+    double r_min, r_max;
+    int32_t with_params;
+    int32_t path, precision;
+} mqct_diatom_params;
+
+/* Build the description of the atom + linear rotor system above.  Allocates the host
+ * arrays of *out (released by mqct_free_desc); G is returned in triplet form.
+ * Host-only: needs no GPU.  Errors: MQCT_ERR_INVALID_ARG (jmax < 0, n_terms outside
+ * [1, 16], n_grid < 4, r_max <= r_min, mu <= 0), MQCT_ERR_OOM. */
+mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_system_desc *out);
+/* Free the arrays allocated by mqct_build_diatom and zero *desc. */
+void mqct_free_desc(mqct_system_desc *desc);
+
+/* Validate `desc`, build the spline tables (Sec. III) and coupling layouts of Eq. 12 in
+ * device memory and return an immutable system (safe to use from several streams).
+ * Validation: N >= 1; finite energies, equal within a level; levels in [0, N); G real
+ * symmetric within 1e-12 max|G| and zero between different m (Eq. 6); n_grid >= 4;
+ * r_max > r_min; mu > 0; path and precision known; flags == 0.
+ * Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_OOM, MQCT_ERR_CUDA. */
+mqct_status mqct_create_system(const mqct_system_desc *desc, mqct_system *out);
+mqct_status mqct_destroy_system(mqct_system sys);
+mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out);
+
+/* Propagate n trajectories (Eqs. 4-10, RK4) in one persistent launch; trajectories may
+ * refer to different systems (uneven basis sizes), which must share path and precision.
+ *   trajs      [n] mqct_traj (host or device)
+ *   final_pop  [n][N_t] |a_s|^2 in the caller's state order of the trajectory's system,
+ *              rows packed with stride N_max = max over the systems used; or NULL
+ *   final_amp  [n][N_max][2] final interaction-picture amplitudes (re, im); or NULL
+ *   diag       [n] mqct_diag; or NULL
+ * Work order: trajectories are claimed from a device work queue, longest estimated
+ * first.  Scratch memory is taken with stream-ordered allocation on `cuda_stream`.
+ * With device output pointers the call only enqueues work and returns MQCT_OK; with
+ * any host output it synchronises the stream and returns MQCT_ERR_TRAJ if a trajectory
+ * status is non-zero.  Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_OOM,
+ * MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
+mqct_status mqct_propagate(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
+                           double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream);
+
+/* Cross sections (Sec. II):
+ *   sigma_out[g][l''] = sum_{t : group[t] = g} weight[t] * sum_{s in level l''} final_pop[t][s]
+ * final_pop [n][N] (row stride N of `sys`), weight [n], group [n] (entries outside
+ * [0, n_groups) are skipped), sigma_out [n_groups][n_levels].  The weight carries the
+ * impact-parameter quadrature (e.g. 2 pi b db) and the 1/g average over initial states;
+ * a zero weight excludes a trajectory.  Device-side reduction in FP64.  Errors:
+ * MQCT_ERR_INVALID_ARG, MQCT_ERR_OOM, MQCT_ERR_CUDA. */
+mqct_status mqct_cross_sections(mqct_system sys, const double *final_pop, const double *weight, const int32_t *group,
+                                int32_t n, int32_t n_groups, double *sigma_out, void *cuda_stream);
+
+/* Vector-Jacobian product of the cross sections with respect to the P parameters whose
+ * tables were given at create time:
+ *   dL_dparam[p] = sum_{g,l''} dL_dsigma[g][l''] * d sigma[g][l''] / d theta_p,
+ * by a discrete adjoint of the same RK4 map (the number of steps of every trajectory is
+ * held at its forward value), recomputing the forward pass from checkpoints taken every
+ * `ckpt` steps.  Arguments as for mqct_propagate / mqct_cross_sections; dL_dsigma
+ * [n_groups][n_levels]; dL_dparam [P].  Single system.  Errors: MQCT_ERR_INVALID_ARG,
+ * MQCT_ERR_UNSUPPORTED (no parameter tables), MQCT_ERR_OOM, MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
+mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int32_t n, const double *weight,
+                         const int32_t *group, int32_t n_groups, const double *dL_dsigma, int32_t ckpt,
+                         double *dL_dparam, void *cuda_stream);
+
+/* Thread-local message describing the last failure of a call on this thread. */
+const char *mqct_last_error(void);
+
+/* Library version string. */
+const char *mqct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MQCT_H */

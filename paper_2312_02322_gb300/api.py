@@ -1,0 +1,299 @@
+"""Thin Python binding of the C ABI in include/mqct.h (argument marshalling only).
+
+Every step of the trajectory path runs in the CUDA library ``_build/libmqct.so``; this
+module converts numpy / torch arguments to pointers and back.  torch provides device
+memory and streams.  The library must be built (``paper_2312_02322_gb300.build``):
+importing the binding without it raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmqct.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_TRAJ = range(7)
+PATH_PLAIN, PATH_FACTORISED = 0, 1
+FP64, FP32, BF16X3 = 0, 1, 2
+TRAJ_MAX_STEPS, TRAJ_TABLE_RANGE, TRAJ_NONFINITE, TRAJ_TIMEOUT, TRAJ_INVALID = 1, 2, 4, 8, 16
+
+_PATHS = {"plain": PATH_PLAIN, "factorised": PATH_FACTORISED}
+_PRECS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+
+
+class MQCTError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mqct status {status}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("n_states", C.c_int32), ("energy", C.c_void_p), ("level", C.c_void_p), ("j", C.c_void_p),
+        ("m", C.c_void_p), ("mu", C.c_double), ("n_terms", C.c_int32), ("G", C.c_void_p),
+        ("g_nnz", C.c_int64), ("g_term", C.c_void_p), ("g_row", C.c_void_p), ("g_col", C.c_void_p),
+        ("g_val", C.c_void_p), ("n_grid", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double),
+        ("v", C.c_void_p), ("dv_ends", C.c_void_p), ("n_params", C.c_int32), ("dv_dparam", C.c_void_p),
+        ("ddv_ends", C.c_void_p), ("path", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_states", C.c_int32), ("n_levels", C.c_int32), ("n_terms", C.c_int32), ("n_grid", C.c_int32),
+                ("n_blocks", C.c_int32), ("max_block", C.c_int32), ("path", C.c_int32), ("precision", C.c_int32),
+                ("table_nnz", C.c_int64), ("table_bytes", C.c_int64), ("glambda_nnz", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+class DiatomParams(C.Structure):
+    _fields_ = [("jmax", C.c_int32), ("bconst", C.c_double), ("mu", C.c_double), ("n_terms", C.c_int32),
+                ("A", C.c_double * 16), ("beta", C.c_double * 16), ("c6", C.c_double), ("rd", C.c_double),
+                ("n_grid", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double), ("with_params", C.c_int32),
+                ("path", C.c_int32), ("precision", C.c_int32)]
+
+
+TRAJ_DTYPE = np.dtype([("e_coll", "<f8"), ("b", "<f8"), ("r0", "<f8"), ("r_end", "<f8"), ("dt", "<f8"),
+                       ("init_state", "<i4"), ("max_steps", "<i4"), ("system_idx", "<i4"), ("_pad", "<i4")])
+DIAG_DTYPE = np.dtype([("steps", "<i4"), ("status", "<i4"), ("norm_dev", "<f8"), ("energy_dev", "<f8"),
+                       ("angmom_dev", "<f8"), ("t_final", "<f8")])
+assert TRAJ_DTYPE.itemsize == 56 and DIAG_DTYPE.itemsize == 40
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libmqct.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"CUDA library not built: {LIB_PATH} (run python -m paper_2312_02322_gb300.build)")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+            L.mqct_build_diatom.argtypes = [C.POINTER(DiatomParams), C.POINTER(Desc)]
+            L.mqct_free_desc.argtypes = [C.POINTER(Desc)]
+            L.mqct_free_desc.restype = None
+            L.mqct_create_system.argtypes = [C.POINTER(Desc), C.POINTER(vp)]
+            L.mqct_destroy_system.argtypes = [vp]
+            L.mqct_system_info.argtypes = [vp, C.POINTER(Info)]
+            L.mqct_propagate.argtypes = [C.POINTER(vp), i32, vp, i32, vp, vp, vp, vp]
+            L.mqct_cross_sections.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp]
+            L.mqct_adjoint.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, vp]
+            L.mqct_probe_fma_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
+            L.mqct_probe_fma_rate.restype = C.c_int
+            L.mqct_last_error.restype = C.c_char_p
+            L.mqct_version.restype = C.c_char_p
+            for f in ("mqct_build_diatom", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
+                      "mqct_propagate", "mqct_cross_sections", "mqct_adjoint"):
+                getattr(L, f).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st: int, allow=()):
+    if st != OK and st not in allow:
+        msg = lib().mqct_last_error()
+        raise MQCTError(st, msg.decode() if msg else "")
+    return st
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class System:
+    """An mqct_system (immutable, owns its device memory).
+
+    Keeps host copies of the state labels so that initial states can be addressed by
+    (j, m) label; state indices are the caller order of the description."""
+
+    def __init__(self, desc: Desc, keep=None):
+        h = C.c_void_p()
+        _check(lib().mqct_create_system(C.byref(desc), C.byref(h)))
+        self._h = h
+        n = desc.n_states
+        self.n = n
+        self.j = np.ctypeslib.as_array(C.cast(desc.j, C.POINTER(C.c_int32)), (n,)).copy()
+        self.m = np.ctypeslib.as_array(C.cast(desc.m, C.POINTER(C.c_int32)), (n,)).copy()
+        self.level = np.ctypeslib.as_array(C.cast(desc.level, C.POINTER(C.c_int32)), (n,)).copy()
+        self.energy = np.ctypeslib.as_array(C.cast(desc.energy, C.POINTER(C.c_double)), (n,)).copy()
+        self.mu = desc.mu
+        self.n_params = desc.n_params
+        self._keep = keep
+        self._index = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(self.j, self.m))}
+
+    @classmethod
+    def diatom(cls, p: "_inputs.DiatomParams", path="plain", precision="fp64", with_params=False) -> "System":
+        dp = DiatomParams()
+        dp.jmax, dp.bconst, dp.mu, dp.n_terms = p.jmax, p.bconst, p.mu, p.n_terms
+        for i in range(p.n_terms):
+            dp.A[i] = float(p.A[i])
+            dp.beta[i] = float(p.beta[i])
+        dp.c6, dp.rd, dp.n_grid, dp.r_min, dp.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
+        dp.with_params = int(bool(with_params))
+        dp.path, dp.precision = _PATHS[path], _PRECS[precision]
+        d = Desc()
+        _check(lib().mqct_build_diatom(C.byref(dp), C.byref(d)))
+        try:
+            return cls(d)
+        finally:
+            lib().mqct_free_desc(C.byref(d))
+
+    def state(self, j, m) -> int:
+        return self._index[(int(j), int(m))]
+
+    @property
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().mqct_system_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_levels(self) -> int:
+        return self.info["n_levels"]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mqct_destroy_system(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_trajs(ts: "_inputs.TrajSet", systems) -> np.ndarray:
+    """mqct_traj array for a TrajSet; initial states addressed by their (j, m) labels."""
+    systems = systems if isinstance(systems, (list, tuple)) else [systems]
+    tr = np.zeros(ts.n, TRAJ_DTYPE)
+    tr["e_coll"], tr["b"] = ts.e_coll, ts.b
+    tr["r0"], tr["r_end"], tr["dt"], tr["max_steps"] = ts.r0, ts.r_end, ts.dt, ts.max_steps
+    sidx = ts.system if len(ts.system) else np.zeros(ts.n, np.int32)
+    tr["system_idx"] = sidx
+    tr["init_state"] = [systems[s].state(j, m) for s, j, m in zip(sidx, ts.init_j, ts.init_m)]
+    return tr
+
+
+def propagate(systems, trajs, want_pop=True, want_amp=False, want_diag=True, device=None, stream=None,
+              allow_traj_status=True):
+    """Run mqct_propagate.
+
+    trajs: numpy TRAJ_DTYPE array (host) or a torch uint8 CUDA tensor holding the same bytes.
+    device=True returns torch CUDA tensors (asynchronous); device=False returns numpy arrays.
+    Returns (pop [n][N_max], amp [n][N_max] complex, diag) with None for outputs not requested."""
+    systems = systems if isinstance(systems, (list, tuple)) else [systems]
+    hs = (C.c_void_p * len(systems))(*[s.handle.value for s in systems])
+    nmax = max(s.n for s in systems)
+    if isinstance(trajs, np.ndarray):
+        n = trajs.shape[0]
+    else:
+        n = trajs.numel() // TRAJ_DTYPE.itemsize
+    if device is None:
+        device = not isinstance(trajs, np.ndarray)
+    pop = amp = diag = None
+    if device:
+        import torch
+
+        dev = torch.device("cuda")
+        if want_pop:
+            pop = torch.empty((n, nmax), dtype=torch.float64, device=dev)
+        if want_amp:
+            amp = torch.empty((n, nmax, 2), dtype=torch.float64, device=dev)
+        if want_diag:
+            diag = torch.empty((n * DIAG_DTYPE.itemsize,), dtype=torch.uint8, device=dev)
+    else:
+        if want_pop:
+            pop = np.zeros((n, nmax))
+        if want_amp:
+            amp = np.zeros((n, nmax, 2))
+        if want_diag:
+            diag = np.zeros(n, DIAG_DTYPE)
+    st = lib().mqct_propagate(hs, len(systems), _ptr(trajs), n, _ptr(pop), _ptr(amp), _ptr(diag), _stream(stream))
+    _check(st, allow=(ERR_TRAJ,) if allow_traj_status else ())
+    if amp is not None and not device:
+        amp = amp[..., 0] + 1j * amp[..., 1]
+    return pop, amp, diag
+
+
+def diag_to_numpy(diag) -> np.ndarray:
+    if isinstance(diag, np.ndarray):
+        return diag
+    return diag.cpu().numpy().view(DIAG_DTYPE)
+
+
+def cross_sections(system: System, pop, weight, group, n_groups: int, stream=None):
+    """sigma[g][level] = sum_{t in g} weight_t sum_{s in level} pop_t[s] (device reduction)."""
+    n = pop.shape[0]
+    if isinstance(pop, np.ndarray):
+        pop = np.ascontiguousarray(pop, np.float64)
+        weight = np.ascontiguousarray(weight, np.float64)
+        group = np.ascontiguousarray(group, np.int32)
+        sig = np.zeros((n_groups, system.n_levels))
+    else:
+        import torch
+
+        sig = torch.empty((n_groups, system.n_levels), dtype=torch.float64, device=pop.device)
+    _check(lib().mqct_cross_sections(system.handle, _ptr(pop), _ptr(weight), _ptr(group), n, n_groups, _ptr(sig),
+                                     _stream(stream)))
+    return sig
+
+
+def sigma_weights(ts: "_inputs.TrajSet", status=None) -> np.ndarray:
+    """Per-trajectory weights of the cross-section quadrature (Sec. III sampling):
+    regular midpoint grid 2 pi b db (divided by 2j'+1 when every m' is run), Monte-Carlo
+    2 pi b_max b / (trajectories in the group); trajectories with MAX_STEPS / NONFINITE /
+    INVALID status get weight 0."""
+    if ts.sampling == "regular":
+        w = 2.0 * np.pi * ts.b * (ts.b_max / ts.n_b)
+        if ts.m_avg == "all":
+            w = w / (2 * ts.init_j + 1)
+    else:
+        counts = np.bincount(ts.group, minlength=ts.n_groups).astype(np.float64)
+        w = 2.0 * np.pi * ts.b_max * ts.b / counts[ts.group]
+    if status is not None:
+        bad = (np.asarray(status) & (TRAJ_MAX_STEPS | TRAJ_NONFINITE | TRAJ_INVALID | TRAJ_TIMEOUT)) != 0
+        w = np.where(bad, 0.0, w)
+    return w
+
+
+def fma_rate(kind: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput of the current GPU in GFLOP/s ("fp64" or "fp32")."""
+    out = C.c_double()
+    _check(lib().mqct_probe_fma_rate({"fp64": 0, "fp32": 1}[kind], C.byref(out), _stream(stream)))
+    return out.value
+
+
+def version() -> str:
+    return lib().mqct_version().decode()

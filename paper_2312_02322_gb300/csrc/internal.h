@@ -1,0 +1,80 @@
+// Internal layout shared by the host builder and the kernels of the MQCT library.
+// Not part of the C ABI (see include/mqct.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mqct.h"
+
+namespace mqct {
+
+// four spline coefficients (c0..c3) of one interval, 32-byte aligned
+struct alignas(32) dbl4 {
+    double x, y, z, w;
+};
+inline __host__ __device__ dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
+constexpr int kSlice = 32;     // rows per SELL slice (one warp)
+constexpr int kMaxTerms = 64;  // expansion terms held in shared memory per stage
+constexpr int kMaxWarps = 32;
+
+// Device view of one system; an array of these lives in device memory so that one
+// persistent launch can serve trajectories of several systems (uneven basis sizes).
+// State indices are INTERNAL: states sorted by m-block (Eq. 6: M is block-diagonal in m),
+// so that each block is contiguous; perm[] maps back to the caller's order.
+struct DevSys {
+    int n, n_levels, L, n_int, n_slices, P;
+    int path, precision;
+    double mu, r_min, h, inv_h;
+    const double *lev_energy;  // [n_levels]
+    const int *lev;            // [n]  level of each internal state
+    const int *perm;           // [n]  internal -> caller index
+    const int *inv;            // [n]  caller -> internal index
+    const int *up, *dn;        // [n]  Coriolis partners m+1 / m-1 (self when absent)
+    const double *aup, *adn;   // [n]  ladder factors (0 when absent or Coriolis off)
+    const double *diag_g;      // [L][n] G^lambda_ss (initial mean-field energy)
+    const dbl4 *vcoef;      // [L][n_int] spline coefficients of v_lambda (c0..c3)
+    const dbl4 *dvcoef;     // [P][L][n_int] spline coefficients of dv_lambda/dtheta_p
+    // PLAIN path: sliced-ELL (32-row slices) spline table of the non-zero M_nm(R)
+    const int *sl_off;         // [n_slices+1] entry offsets (multiples of 32)
+    const int *cols;           // [nnz_pad] internal column (padding: row itself, zero coefficients)
+    const double2 *T01;        // [n_int][nnz_pad] (c0, c1)
+    const double2 *T23;        // [n_int][nnz_pad] (c2, c3)
+    const float2 *T01f;        // FP32 copies (precision != FP64)
+    const float2 *T23f;
+    long long nnz_pad;
+    // FACTORISED path: per stored term f (a lambda whose G is not the identity) a sliced-ELL
+    // matrix; identity terms are applied directly (id_mask bit lambda).
+    int n_f;
+    unsigned long long id_mask;
+    const int *f_term;         // [n_f] lambda of stored term f
+    const int *f_sl_off;       // [n_f][n_slices+1] offsets into f_cols / f_val
+    const int *f_cols;
+    const double *f_val;
+    const float *f_valf;
+};
+
+struct System {
+    DevSys h;                  // host copy of the device view (pointers are device pointers)
+    DevSys *d = nullptr;       // device copy
+    std::vector<void *> allocs;
+    mqct_system_info_t info{};
+    // host copies needed by the host side of later calls
+    std::vector<int> perm, inv, lev;
+    int max_block = 0;
+};
+
+void set_error(const std::string &msg);
+const char *last_error_cstr();
+mqct_status fail(mqct_status st, const std::string &msg);
+mqct_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace mqct
+
+struct mqct_system_s {
+    mqct::System s;
+};

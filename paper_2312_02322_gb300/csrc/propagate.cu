@@ -1,0 +1,558 @@
+// Persistent RK4 trajectory kernels and mqct_propagate.
+//
+// One CTA integrates one trajectory at a time, claiming trajectories from a device
+// work queue (longest estimated first) until the queue is empty; the whole RK4 loop of a
+// trajectory runs on the device with its amplitudes resident in shared memory.  Per
+// RK4 stage (Eq. 4-10):
+//   P3  coupling: w = M(R) c and u = M'(R) c for the phase-rotated stage amplitudes
+//       c = exp(-i E t_s) a_s, row by row over 32-row sliced-ELL slices (one warp per slice)
+//         PLAIN:      M_nm(R) from the spline table of Sec. III, M = sum_p T_p x^p,
+//                     computed as w = sum_p x^p (T_p c), u = sum_p p x^(p-1) (T_p c);
+//         FACTORISED: w = sum_l v_l(R) (G^l c), u = sum_l v_l'(R) (G^l c)  (Eq. 12);
+//   P4  derivative assembly: da/dt = -i exp(iEt) w + (dPhi/dt / 2)(J+ - J-) a (Eq. 5),
+//       torque Re(c^dag (J+ - J-) w) (Eq. 10), RK4 accumulation, next stage input and
+//       its phase rotation; block reduction of force / torque / diagnostics;
+//   C   classical stage update of R, P_R, Phi, P_Phi (Eqs. 7-9) by one thread in FP64.
+// Phase arguments E_n t are FP64 and evaluated per level (states of a level share E_n).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cub/device/device_radix_sort.cuh>
+#include <vector>
+
+#include "internal.h"
+
+namespace mqct {
+
+constexpr int kPropThreads = 512;  // upper bound of the block size (register budget)
+
+struct PropArgs {
+    const DevSys *sys;
+    const mqct_traj *trajs;
+    const int *order;
+    int n, n_systems;
+    int *queue;
+    double *pop;
+    double *amp;
+    mqct_diag *diag;
+    int nmax;      // row stride of pop / amp
+    int smem_n;    // shared-memory vector length (max n over systems)
+    int smem_lev;  // max n_levels over systems
+};
+
+struct Ctl {
+    double q[4], qs[4], lacc[4];
+    double phidot, x, dt, r_end;
+    double e0, j0, ndev, edev, jdev;
+    double v[kMaxTerms], dv[kMaxTerms];
+    double vid, dvid;
+    int kint, status, steps, done, max_steps, t, item;
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// spline of the expansion terms at R (factorised path and initial mean field)
+__device__ __forceinline__ void term_at(const DevSys &S, int l, int k, double x, double &v, double &dv)
+{
+    dbl4 c = S.vcoef[(size_t)l * S.n_int + k];
+    v = c.x + x * (c.y + x * (c.z + x * c.w));
+    dv = c.y + x * (2.0 * c.z + 3.0 * x * c.w);
+}
+
+__device__ __forceinline__ void locate(const DevSys &S, double R, int &k, double &x)
+{
+    int kk = (int)floor((R - S.r_min) * S.inv_h);
+    kk = kk < 0 ? 0 : (kk > S.n_int - 1 ? S.n_int - 1 : kk);
+    k = kk;
+    x = R - (S.r_min + kk * S.h);
+}
+
+// thread 0: stage quantities at the classical stage state qs
+__device__ void prepare_stage(const DevSys &S, Ctl &c)
+{
+    double R = c.qs[0];
+    locate(S, R, c.kint, c.x);
+    c.phidot = c.qs[3] / (S.mu * R * R);
+    if (R < S.r_min) c.status |= MQCT_TRAJ_TABLE_RANGE;
+    if (S.path == MQCT_PATH_FACTORISED) {
+        double vid = 0.0, dvid = 0.0;
+        for (int l = 0; l < S.L; ++l) {
+            double v, dv;
+            term_at(S, l, c.kint, c.x, v, dv);
+            c.v[l] = v;
+            c.dv[l] = dv;
+            if ((S.id_mask >> l) & 1ull) { vid += v; dvid += dv; }
+        }
+        c.vid = vid;
+        c.dvid = dvid;
+    }
+}
+
+// P3: coupling for the rows of this warp; writes W[r] and returns the partial sums
+// -Re(c_r^* u_r) (force) and Re(c_r^* w_r) (mean-field energy).
+__device__ __forceinline__ void coupling_fp64(const DevSys &S, const Ctl &c, const double2 *__restrict__ C,
+                                              double2 *__restrict__ W, int warp, int nwarps, int lane,
+                                              double &force, double &vc)
+{
+    const double x = c.x;
+    for (int sl = warp; sl < S.n_slices; sl += nwarps) {
+        const int r = sl * kSlice + lane;
+        double2 w, u;
+        if (S.path == MQCT_PATH_PLAIN) {
+            const int off = S.sl_off[sl], width = (S.sl_off[sl + 1] - off) / kSlice;
+            const size_t base = (size_t)c.kint * S.nnz_pad + off + lane;
+            const double2 *t01 = S.T01 + base, *t23 = S.T23 + base;
+            const int *cl = S.cols + off + lane;
+            double2 u0 = {0, 0}, u1 = {0, 0}, u2 = {0, 0}, u3 = {0, 0};
+            for (int k = 0; k < width; ++k) {
+                const int col = __ldg(cl + k * kSlice);
+                const double2 a = __ldg(t01 + k * kSlice), b = __ldg(t23 + k * kSlice);
+                const double2 z = C[col];
+                u0.x = fma(a.x, z.x, u0.x); u0.y = fma(a.x, z.y, u0.y);
+                u1.x = fma(a.y, z.x, u1.x); u1.y = fma(a.y, z.y, u1.y);
+                u2.x = fma(b.x, z.x, u2.x); u2.y = fma(b.x, z.y, u2.y);
+                u3.x = fma(b.y, z.x, u3.x); u3.y = fma(b.y, z.y, u3.y);
+            }
+            w.x = fma(x, fma(x, fma(x, u3.x, u2.x), u1.x), u0.x);
+            w.y = fma(x, fma(x, fma(x, u3.y, u2.y), u1.y), u0.y);
+            u.x = fma(x, fma(3.0 * x, u3.x, 2.0 * u2.x), u1.x);
+            u.y = fma(x, fma(3.0 * x, u3.y, 2.0 * u2.y), u1.y);
+        } else {
+            const double2 z0 = r < S.n ? C[r] : make_double2(0.0, 0.0);
+            w = make_double2(c.vid * z0.x, c.vid * z0.y);
+            u = make_double2(c.dvid * z0.x, c.dvid * z0.y);
+            for (int f = 0; f < S.n_f; ++f) {
+                const int *so = S.f_sl_off + (size_t)f * (S.n_slices + 1);
+                const int off = so[sl], width = (so[sl + 1] - off) / kSlice;
+                const int *cl = S.f_cols + off + lane;
+                const double *gv = S.f_val + off + lane;
+                double2 y = {0, 0};
+                for (int k = 0; k < width; ++k) {
+                    const double g = __ldg(gv + k * kSlice);
+                    const double2 z = C[__ldg(cl + k * kSlice)];
+                    y.x = fma(g, z.x, y.x);
+                    y.y = fma(g, z.y, y.y);
+                }
+                const int l = S.f_term[f];
+                const double v = c.v[l], dv = c.dv[l];
+                w.x = fma(v, y.x, w.x); w.y = fma(v, y.y, w.y);
+                u.x = fma(dv, y.x, u.x); u.y = fma(dv, y.y, u.y);
+            }
+        }
+        if (r < S.n) {
+            W[r] = w;
+            const double2 z = C[r];
+            force -= z.x * u.x + z.y * u.y;
+            vc += z.x * w.x + z.y * w.y;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
+{
+    extern __shared__ double2 smem[];
+    __shared__ Ctl c;
+    __shared__ DevSys S;
+    __shared__ double red[kMaxWarps][6];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const int NN = a.smem_n;
+    double2 *A = smem, *Y0 = A + NN, *Y1 = Y0 + NN, *ACC = Y1 + NN, *C = ACC + NN, *W = C + NN;
+    double2 *PHa = W + NN, *PHb = PHa + a.smem_lev;
+
+    for (;;) {
+        if (tid == 0) c.item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int item = c.item;
+        if (item >= a.n) break;
+        const int t = a.order ? a.order[item] : item;
+        const mqct_traj tr = a.trajs[t];
+        // trajectories that live in device memory were not seen by the host: validate here
+        bool ok = tr.system_idx >= 0 && tr.system_idx < a.n_systems && tr.dt > 0.0 && tr.e_coll > 0.0 &&
+                  tr.b >= 0.0 && tr.r0 > 0.0 && tr.b < tr.r0 && isfinite(tr.r_end) && tr.max_steps >= 0;
+        if (ok) ok = tr.init_state >= 0 && tr.init_state < a.sys[tr.system_idx].n;
+        if (!ok) {
+            if (a.diag && tid == 0) {
+                mqct_diag d = {0, MQCT_TRAJ_INVALID, 0.0, 0.0, 0.0, 0.0};
+                a.diag[t] = d;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) S = a.sys[tr.system_idx];
+        __syncthreads();
+        const int n = S.n;
+        const int s0 = S.inv[tr.init_state];
+        // ---- initial state
+        for (int r = tid; r < n; r += nt) {
+            double2 v = make_double2(r == s0 ? 1.0 : 0.0, 0.0);
+            A[r] = v; Y0[r] = v; C[r] = v;  // phase at t = 0 is 1
+        }
+        for (int l = tid; l < S.n_levels; l += nt) PHa[l] = make_double2(1.0, 0.0);
+        if (tid == 0) {
+            int k; double x;
+            locate(S, tr.r0, k, x);
+            double m00 = 0.0;
+            for (int l = 0; l < S.L; ++l) {
+                double v, dv;
+                term_at(S, l, k, x, v, dv);
+                m00 += v * S.diag_g[(size_t)l * n + s0];
+            }
+            const double lz = tr.b * sqrt(2.0 * S.mu * tr.e_coll);
+            c.q[0] = tr.r0; c.q[2] = 0.0; c.q[3] = lz;
+            c.q[1] = -sqrt(2.0 * S.mu * (tr.e_coll - m00) - lz * lz / (tr.r0 * tr.r0));
+            for (int i = 0; i < 4; ++i) c.qs[i] = c.q[i];
+            c.dt = tr.dt; c.r_end = tr.r_end; c.max_steps = tr.max_steps;
+            c.status = 0; c.steps = 0; c.done = tr.max_steps <= 0;
+            if (c.done) c.status |= MQCT_TRAJ_MAX_STEPS;
+            c.ndev = c.edev = c.jdev = 0.0;
+            c.t = t;
+            prepare_stage(S, c);
+        }
+        __syncthreads();
+        int ycur = 0;
+        const double dt = tr.dt;
+        // ---- RK4 steps
+        while (!c.done) {
+            const int step = c.steps;
+            const double t0 = step * dt;
+            for (int s = 0; s < 4; ++s) {
+                double2 *Yc = ycur ? Y1 : Y0, *Yn = ycur ? Y0 : Y1;
+                const double2 *PHc = (s == 0 || s == 3) ? PHa : PHb;
+                const double2 *PHn = (s == 0 || s == 1) ? PHb : PHa;
+                // P3 (+ phases of the next distinct stage time)
+                if (s == 0 || s == 2) {
+                    const double tn = s == 0 ? t0 + 0.5 * dt : t0 + dt;
+                    double2 *dst = s == 0 ? PHb : PHa;
+                    for (int l = tid; l < S.n_levels; l += nt) {
+                        double sn, cs;
+                        sincos(S.lev_energy[l] * tn, &sn, &cs);
+                        dst[l] = make_double2(cs, -sn);
+                    }
+                }
+                double force = 0.0, vc = 0.0;
+                coupling_fp64(S, c, C, W, warp, nwarps, lane, force, vc);
+                __syncthreads();
+                // P4
+                const double hp = 0.5 * c.phidot;
+                const double wk = (s == 1 || s == 2) ? 2.0 : 1.0;
+                const double bn = s == 2 ? dt : 0.5 * dt;
+                double torque = 0.0, nrm = 0.0, erot = 0.0, jy = 0.0;
+                for (int r = tid; r < n; r += nt) {
+                    const int ru = S.up[r], rd = S.dn[r];
+                    const double au = S.aup[r], ad = S.adn[r];
+                    const double2 y = Yc[r], yu = Yc[ru], yd = Yc[rd];
+                    const double2 w = W[r], wu = W[ru], wd = W[rd];
+                    const double2 z = C[r];
+                    const double2 p = PHc[S.lev[r]];
+                    const double2 Dy = make_double2(ad * yd.x - au * yu.x, ad * yd.y - au * yu.y);
+                    const double2 Dw = make_double2(ad * wd.x - au * wu.x, ad * wd.y - au * wu.y);
+                    torque += z.x * Dw.x + z.y * Dw.y;
+                    // k = -i conj(p) w + (phidot/2) D y
+                    double2 k;
+                    k.x = fma(hp, Dy.x, p.x * w.y - p.y * w.x);
+                    k.y = fma(hp, Dy.y, -(p.x * w.x + p.y * w.y));
+                    if (s == 0) {
+                        const double pp = y.x * y.x + y.y * y.y;
+                        nrm += pp;
+                        erot += S.lev_energy[S.lev[r]] * pp;
+                        jy += y.x * Dy.y - y.y * Dy.x;
+                        ACC[r] = k;
+                    } else {
+                        double2 acc = ACC[r];
+                        acc.x = fma(wk, k.x, acc.x);
+                        acc.y = fma(wk, k.y, acc.y);
+                        ACC[r] = acc;
+                        if (s == 3) {
+                            double2 an = A[r];
+                            an.x = fma(dt / 6.0, acc.x, an.x);
+                            an.y = fma(dt / 6.0, acc.y, an.y);
+                            A[r] = an;
+                            Yn[r] = an;
+                            const double2 pn = PHn[S.lev[r]];
+                            C[r] = make_double2(pn.x * an.x - pn.y * an.y, pn.x * an.y + pn.y * an.x);
+                        }
+                    }
+                    if (s < 3) {
+                        const double2 a0 = A[r];
+                        const double2 yn = make_double2(fma(bn, k.x, a0.x), fma(bn, k.y, a0.y));
+                        Yn[r] = yn;
+                        const double2 pn = PHn[S.lev[r]];
+                        C[r] = make_double2(pn.x * yn.x - pn.y * yn.y, pn.x * yn.y + pn.y * yn.x);
+                    }
+                }
+                // block reduction
+                force = warp_sum(force);
+                torque = warp_sum(torque);
+                if (s == 0) {
+                    vc = warp_sum(vc); nrm = warp_sum(nrm); erot = warp_sum(erot); jy = warp_sum(jy);
+                }
+                if (lane == 0) {
+                    red[warp][0] = force; red[warp][1] = torque;
+                    if (s == 0) { red[warp][2] = vc; red[warp][3] = nrm; red[warp][4] = erot; red[warp][5] = jy; }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double F = 0, T = 0, V = 0, NR = 0, ER = 0, JY = 0;
+                    for (int w2 = 0; w2 < nwarps; ++w2) {
+                        F += red[w2][0]; T += red[w2][1];
+                        if (s == 0) { V += red[w2][2]; NR += red[w2][3]; ER += red[w2][4]; JY += red[w2][5]; }
+                    }
+                    const double R = c.qs[0], PR = c.qs[1], PP = c.qs[3], mu = S.mu;
+                    double l[4] = {PR / mu, F + PP * PP / (mu * R * R * R), c.phidot, T};
+                    if (s == 0) {
+                        const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + ER + V;
+                        const double jt = PP + 0.5 * JY;
+                        if (step == 0) { c.e0 = et; c.j0 = jt; }
+                        c.ndev = fmax(c.ndev, fabs(NR - 1.0));
+                        c.edev = fmax(c.edev, fabs(et - c.e0));
+                        c.jdev = fmax(c.jdev, fabs(jt - c.j0));
+                        for (int i = 0; i < 4; ++i) c.lacc[i] = l[i];
+                    } else {
+                        for (int i = 0; i < 4; ++i) c.lacc[i] = fma(wk, l[i], c.lacc[i]);
+                    }
+                    if (s < 3) {
+                        for (int i = 0; i < 4; ++i) c.qs[i] = fma(bn, l[i], c.q[i]);
+                    } else {
+                        for (int i = 0; i < 4; ++i) { c.q[i] = fma(dt / 6.0, c.lacc[i], c.q[i]); c.qs[i] = c.q[i]; }
+                        c.steps = step + 1;
+                        bool fin = isfinite(c.q[0]) && isfinite(c.q[1]) && isfinite(c.q[2]) && isfinite(c.q[3]);
+                        if (!fin) { c.status |= MQCT_TRAJ_NONFINITE; c.done = 1; }
+                        else if (c.q[0] >= c.r_end && c.q[1] > 0.0) c.done = 1;
+                        else if (c.steps >= c.max_steps) { c.status |= MQCT_TRAJ_MAX_STEPS; c.done = 1; }
+                    }
+                    if (!(c.status & MQCT_TRAJ_NONFINITE)) prepare_stage(S, c);
+                }
+                ycur ^= 1;
+                __syncthreads();
+            }
+        }
+        // ---- diagnostics of the final state (C holds exp(-iEt) a at t = steps dt)
+        if (!(c.status & MQCT_TRAJ_NONFINITE)) {
+            double force = 0.0, vc = 0.0;
+            coupling_fp64(S, c, C, W, warp, nwarps, lane, force, vc);
+            double nrm = 0.0, erot = 0.0, jy = 0.0;
+            for (int r = tid; r < n; r += nt) {
+                const double2 y = A[r], yu = A[S.up[r]], yd = A[S.dn[r]];
+                const double2 Dy = make_double2(S.adn[r] * yd.x - S.aup[r] * yu.x, S.adn[r] * yd.y - S.aup[r] * yu.y);
+                const double pp = y.x * y.x + y.y * y.y;
+                nrm += pp;
+                erot += S.lev_energy[S.lev[r]] * pp;
+                jy += y.x * Dy.y - y.y * Dy.x;
+            }
+            vc = warp_sum(vc); nrm = warp_sum(nrm); erot = warp_sum(erot); jy = warp_sum(jy);
+            __syncthreads();
+            if (lane == 0) { red[warp][2] = vc; red[warp][3] = nrm; red[warp][4] = erot; red[warp][5] = jy; }
+            __syncthreads();
+            if (tid == 0) {
+                double V = 0, NR = 0, ER = 0, JY = 0;
+                for (int w2 = 0; w2 < nwarps; ++w2) { V += red[w2][2]; NR += red[w2][3]; ER += red[w2][4]; JY += red[w2][5]; }
+                const double R = c.q[0], PR = c.q[1], PP = c.q[3], mu = S.mu;
+                const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + ER + V;
+                const double jt = PP + 0.5 * JY;
+                if (c.steps == 0) { c.e0 = et; c.j0 = jt; }
+                c.ndev = fmax(c.ndev, fabs(NR - 1.0));
+                c.edev = fmax(c.edev, fabs(et - c.e0));
+                c.jdev = fmax(c.jdev, fabs(jt - c.j0));
+            }
+        }
+        __syncthreads();
+        // ---- outputs in the caller's state order
+        if (a.pop)
+            for (int r = tid; r < n; r += nt) {
+                const double2 y = A[r];
+                a.pop[(size_t)t * a.nmax + S.perm[r]] = y.x * y.x + y.y * y.y;
+            }
+        if (a.amp)
+            for (int r = tid; r < n; r += nt) {
+                const double2 y = A[r];
+                a.amp[((size_t)t * a.nmax + S.perm[r]) * 2] = y.x;
+                a.amp[((size_t)t * a.nmax + S.perm[r]) * 2 + 1] = y.y;
+            }
+        if (a.diag && tid == 0) {
+            mqct_diag d;
+            d.steps = c.steps; d.status = c.status;
+            d.norm_dev = c.ndev; d.energy_dev = c.edev; d.angmom_dev = c.jdev;
+            d.t_final = c.steps * dt;
+            a.diag[t] = d;
+        }
+        __syncthreads();
+    }
+}
+
+// work-order keys: estimated cost of a trajectory (steps ~ 2 r0 / v, work per step ~ nnz)
+__global__ void k_order_keys(const DevSys *sys, int n_systems, const mqct_traj *trajs, int n, float *keys, int *idx)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const mqct_traj tr = trajs[i];
+    idx[i] = i;
+    if (tr.system_idx < 0 || tr.system_idx >= n_systems) { keys[i] = 0.0f; return; }
+    const DevSys &S = sys[tr.system_idx];
+    double v = sqrt(2.0 * fmax(tr.e_coll, 1e-30) / S.mu);
+    double steps = fmin(2.0 * tr.r0 / (v * tr.dt), (double)tr.max_steps);
+    double work = S.path == MQCT_PATH_PLAIN ? (double)S.nnz_pad : (double)S.n * (S.n_f + 1);
+    keys[i] = (float)(-(steps * (work + 64.0 * S.n)));  // ascending sort = longest first
+}
+
+}  // namespace mqct
+
+using namespace mqct;
+
+namespace {
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct StreamAllocs {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit StreamAllocs(cudaStream_t s) : st(s) {}
+    cudaError_t get(void **p, size_t bytes)
+    {
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~StreamAllocs()
+    {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+}  // namespace
+
+extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
+                                      double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream)
+{
+    if (!systems || n_systems < 1) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: no systems");
+    if (n < 0) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: n < 0");
+    if (n > 0 && !trajs) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: trajs is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int nmax = 0, maxlev = 0, max_slices = 0;
+    int path = -1, prec = -1;
+    for (int i = 0; i < n_systems; ++i) {
+        if (!systems[i]) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: NULL system");
+        const DevSys &h = systems[i]->s.h;
+        nmax = std::max(nmax, h.n);
+        maxlev = std::max(maxlev, h.n_levels);
+        max_slices = std::max(max_slices, h.n_slices);
+        if (path < 0) { path = h.path; prec = h.precision; }
+        if (h.path != path || h.precision != prec)
+            return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: systems differ in path or precision");
+    }
+    if (prec != MQCT_FP64) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: only FP64 systems in this build");
+    if (n == 0) return MQCT_OK;
+
+    const bool trajs_dev = is_device_ptr(trajs);
+    // host trajectories are validated on the host
+    if (!trajs_dev) {
+        for (int i = 0; i < n; ++i) {
+            const mqct_traj &t = trajs[i];
+            if (t.system_idx < 0 || t.system_idx >= n_systems) return fail(MQCT_ERR_INVALID_ARG, "trajectory system_idx out of range");
+            const DevSys &h = systems[t.system_idx]->s.h;
+            if (t.init_state < 0 || t.init_state >= h.n) return fail(MQCT_ERR_INVALID_ARG, "trajectory init_state out of range");
+            if (!(t.dt > 0) || !(t.e_coll > 0) || !(t.b >= 0) || !(t.r0 > 0) || t.max_steps < 0 || !std::isfinite(t.r_end))
+                return fail(MQCT_ERR_INVALID_ARG, "trajectory with invalid e_coll, b, r0, r_end, dt or max_steps");
+            double q = 2.0 * h.mu * t.e_coll - 2.0 * h.mu * t.e_coll * (t.b * t.b) / (t.r0 * t.r0);
+            if (!(q > 0)) return fail(MQCT_ERR_INVALID_ARG, "trajectory starts inside its centrifugal barrier (b >= r0)");
+        }
+    }
+    StreamAllocs sa(st);
+    cudaError_t e;
+    // device view of the system array
+    DevSys *dsys = nullptr;
+    {
+        std::vector<DevSys> hv(n_systems);
+        for (int i = 0; i < n_systems; ++i) hv[i] = systems[i]->s.h;
+        if ((e = sa.get((void **)&dsys, sizeof(DevSys) * n_systems)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        // pageable source: the copy is staged before cudaMemcpyAsync returns
+        if ((e = cudaMemcpyAsync(dsys, hv.data(), sizeof(DevSys) * n_systems, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    const mqct_traj *dtr = trajs;
+    if (!trajs_dev) {
+        mqct_traj *p = nullptr;
+        if ((e = sa.get((void **)&p, sizeof(mqct_traj) * n)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        if ((e = cudaMemcpyAsync(p, trajs, sizeof(mqct_traj) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync");
+        dtr = p;
+    }
+    // outputs: device pointers are written directly, host ones through staging buffers
+    const bool pop_dev = is_device_ptr(final_pop), amp_dev = is_device_ptr(final_amp), diag_dev = is_device_ptr(diag);
+    const bool any_host = (final_pop && !pop_dev) || (final_amp && !amp_dev) || (diag && !diag_dev);
+    double *dpop = final_pop, *damp = final_amp;
+    mqct_diag *ddiag = nullptr;
+    if (final_pop && !pop_dev && (e = sa.get((void **)&dpop, sizeof(double) * (size_t)n * nmax)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync");
+    if (final_amp && !amp_dev && (e = sa.get((void **)&damp, sizeof(double) * 2 * (size_t)n * nmax)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync");
+    if (diag && diag_dev) ddiag = diag;
+    else if ((diag || any_host) && (e = sa.get((void **)&ddiag, sizeof(mqct_diag) * (size_t)n)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync");
+    // work order: longest estimated trajectory first
+    float *keys = nullptr, *keys2 = nullptr;
+    int *idx = nullptr, *order = nullptr, *queue = nullptr;
+    if ((e = sa.get((void **)&keys, sizeof(float) * n)) != cudaSuccess || (e = sa.get((void **)&keys2, sizeof(float) * n)) != cudaSuccess ||
+        (e = sa.get((void **)&idx, sizeof(int) * n)) != cudaSuccess || (e = sa.get((void **)&order, sizeof(int) * n)) != cudaSuccess ||
+        (e = sa.get((void **)&queue, sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync");
+    k_order_keys<<<(n + 255) / 256, 256, 0, st>>>(dsys, n_systems, dtr, n, keys, idx);
+    size_t tmp_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, order, n, 0, 32, st);
+    void *tmp = nullptr;
+    if ((e = sa.get(&tmp, tmp_bytes)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    if ((e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, idx, order, n, 0, 32, st)) != cudaSuccess)
+        return cuda_fail(e, "cub::DeviceRadixSort");
+    if ((e = cudaMemsetAsync(queue, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+
+    // launch shape: one warp per 32-row slice (balanced), persistent grid
+    const int maxw = kPropThreads / 32;
+    int per = (max_slices + maxw - 1) / maxw;
+    int nwarps = std::max(4, std::min(maxw, (max_slices + per - 1) / per));
+    int threads = nwarps * 32;
+    size_t smem = sizeof(double2) * (6 * (size_t)nmax + 2 * (size_t)maxlev);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaFuncSetAttribute(k_propagate_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute (basis too large for shared memory)");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate_fp64, threads, smem)) != cudaSuccess)
+        return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: kernel does not fit on an SM");
+    int grid = std::min(n, sms * per_sm);
+    PropArgs pa;
+    pa.sys = dsys; pa.trajs = dtr; pa.order = order; pa.n = n; pa.n_systems = n_systems; pa.queue = queue;
+    pa.pop = dpop; pa.amp = damp; pa.diag = ddiag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
+    k_propagate_fp64<<<grid, threads, smem, st>>>(pa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");
+
+    if (!any_host) return MQCT_OK;
+    if (final_pop && !pop_dev &&
+        (e = cudaMemcpyAsync(final_pop, dpop, sizeof(double) * (size_t)n * nmax, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync");
+    if (final_amp && !amp_dev &&
+        (e = cudaMemcpyAsync(final_amp, damp, sizeof(double) * 2 * (size_t)n * nmax, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync");
+    std::vector<mqct_diag> hd(n);
+    mqct_diag *dst = (diag && !diag_dev) ? diag : hd.data();
+    if ((e = cudaMemcpyAsync(dst, ddiag, sizeof(mqct_diag) * (size_t)n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    for (int i = 0; i < n; ++i)
+        if (dst[i].status != 0) return fail(MQCT_ERR_TRAJ, "at least one trajectory ended with a non-zero status");
+    return MQCT_OK;
+}

@@ -1,0 +1,458 @@
+// mqct_create_system: validation, internal state order, spline tables and coupling
+// layouts (host), then upload to device memory.
+//
+// Spline (Sec. III): clamped cubic on the uniform grid, solved here in the slope form
+//   d_{i-1} + 4 d_i + d_{i+1} = 3 (y_{i+1} - y_{i-1}) / h,  d_0, d_{n-1} given,
+// whose piecewise cubics are the same clamped spline as any other construction.
+// Because the spline is linear in the data, the table of M_nm(R) = sum_l G^l_nm v_l(R)
+// is sum_l G^l_nm (coefficients of v_l): the PLAIN and FACTORISED paths evaluate the same
+// function (Eq. 12).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace mqct {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string &msg) { g_err = msg; }
+const char *last_error_cstr() { return g_err.c_str(); }
+mqct_status fail(mqct_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+mqct_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MQCT_ERR_OOM : MQCT_ERR_CUDA;
+}
+
+namespace {
+
+// clamped cubic spline in slope form; coef[i] = (c0, c1, c2, c3) on [R_i, R_i+1]
+void clamped_spline(int n, double h, const double *y, double d0, double dn, std::vector<dbl4> &coef)
+{
+    std::vector<double> d(n), cp(n), rp(n);
+    d[0] = d0;
+    d[n - 1] = dn;
+    int m = n - 2;  // interior unknowns d_1..d_{n-2}
+    if (m > 0) {
+        // forward sweep: rows i = 1..n-2, diag 4, off-diagonals 1
+        for (int i = 1; i <= m; ++i) {
+            double rhs = 3.0 * (y[i + 1] - y[i - 1]) / h;
+            if (i == 1) rhs -= d0;
+            if (i == m) rhs -= dn;
+            double diag = 4.0;
+            if (i > 1) {
+                diag -= cp[i - 1];
+                rhs -= rp[i - 1];
+            }
+            cp[i] = 1.0 / diag;
+            rp[i] = rhs / diag;
+        }
+        d[m] = rp[m];
+        for (int i = m - 1; i >= 1; --i) d[i] = rp[i] - cp[i] * d[i + 1];
+    }
+    coef.resize(n - 1);
+    for (int i = 0; i < n - 1; ++i) {
+        double del = (y[i + 1] - y[i]) / h;
+        coef[i] = make_dbl4(y[i], d[i], (3.0 * del - 2.0 * d[i] - d[i + 1]) / h, (d[i] + d[i + 1] - 2.0 * del) / (h * h));
+    }
+}
+
+struct Entry {
+    int r, c;
+    double v;
+};
+
+template <class T>
+mqct_status upload(System &S, const std::vector<T> &v, const T **dst)
+{
+    *dst = nullptr;
+    if (v.empty()) return MQCT_OK;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * v.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    S.allocs.push_back(p);
+    e = cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    *dst = static_cast<const T *>(p);
+    S.info.device_bytes += (int64_t)(sizeof(T) * v.size());
+    return MQCT_OK;
+}
+
+void release(System &S)
+{
+    for (void *p : S.allocs) cudaFree(p);
+    S.allocs.clear();
+    if (S.d) cudaFree(S.d);
+    S.d = nullptr;
+}
+
+// sliced-ELL layout of per-row entry lists: slices of kSlice consecutive rows, width = max
+// row length in the slice, entry (slice, k, lane) at off[slice] + k * kSlice + lane.
+struct Sell {
+    std::vector<int> off;   // [n_slices + 1]
+    std::vector<int> cols;  // [nnz_pad]
+    std::vector<int> src;   // [nnz_pad] index into the row's entry list, -1 for padding
+    std::vector<int> row_of;
+};
+
+Sell make_sell(int n, const std::vector<std::vector<Entry>> &rows)
+{
+    Sell S;
+    int ns = (n + kSlice - 1) / kSlice;
+    S.off.assign(ns + 1, 0);
+    for (int s = 0; s < ns; ++s) {
+        int w = 0;
+        for (int l = 0; l < kSlice; ++l) {
+            int r = s * kSlice + l;
+            if (r < n) w = std::max<int>(w, (int)rows[r].size());
+        }
+        S.off[s + 1] = S.off[s] + w * kSlice;
+    }
+    S.cols.assign(S.off[ns], 0);
+    S.src.assign(S.off[ns], -1);
+    S.row_of.assign(S.off[ns], 0);
+    for (int s = 0; s < ns; ++s) {
+        int w = (S.off[s + 1] - S.off[s]) / kSlice;
+        for (int l = 0; l < kSlice; ++l) {
+            int r = s * kSlice + l;
+            for (int k = 0; k < w; ++k) {
+                int e = S.off[s] + k * kSlice + l;
+                S.row_of[e] = r;
+                if (r < n && k < (int)rows[r].size()) {
+                    S.cols[e] = rows[r][k].c;
+                    S.src[e] = k;
+                } else {
+                    S.cols[e] = r < n ? r : 0;  // in-bounds dummy column, zero coefficient
+                }
+            }
+        }
+    }
+    return S;
+}
+
+}  // namespace
+}  // namespace mqct
+
+using namespace mqct;
+
+extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system *out)
+{
+    if (!d || !out) return fail(MQCT_ERR_INVALID_ARG, "mqct_create_system: NULL argument");
+    *out = nullptr;
+    const int n = d->n_states, L = d->n_terms, ng = d->n_grid, P = d->n_params;
+    if (n < 1) return fail(MQCT_ERR_INVALID_ARG, "n_states < 1");
+    if (L < 1 || L > kMaxTerms) return fail(MQCT_ERR_INVALID_ARG, "n_terms outside [1, 64]");
+    if (ng < 4) return fail(MQCT_ERR_INVALID_ARG, "n_grid < 4");
+    if (!(d->r_max > d->r_min) || !std::isfinite(d->r_min) || !std::isfinite(d->r_max))
+        return fail(MQCT_ERR_INVALID_ARG, "r_max must exceed r_min (finite)");
+    if (!(d->mu > 0) || !std::isfinite(d->mu)) return fail(MQCT_ERR_INVALID_ARG, "mu must be finite and > 0");
+    if (!d->energy || !d->level || !d->j || !d->m || !d->v || !d->dv_ends)
+        return fail(MQCT_ERR_INVALID_ARG, "NULL array in system description");
+    if (d->path != MQCT_PATH_PLAIN && d->path != MQCT_PATH_FACTORISED) return fail(MQCT_ERR_INVALID_ARG, "unknown path");
+    if (d->precision != MQCT_FP64 && d->precision != MQCT_FP32 && d->precision != MQCT_BF16X3)
+        return fail(MQCT_ERR_INVALID_ARG, "unknown precision");
+    if (d->precision == MQCT_BF16X3) return fail(MQCT_ERR_UNSUPPORTED, "BF16X3 precision is not available in this build");
+    if (d->flags != 0) return fail(MQCT_ERR_INVALID_ARG, "flags must be 0");
+    if (P < 0 || (P > 0 && (!d->dv_dparam || !d->ddv_ends))) return fail(MQCT_ERR_INVALID_ARG, "bad parameter tables");
+    if (!d->G && d->g_nnz > 0 && (!d->g_term || !d->g_row || !d->g_col || !d->g_val))
+        return fail(MQCT_ERR_INVALID_ARG, "NULL triplet array");
+    if (!d->G && d->g_nnz < 0) return fail(MQCT_ERR_INVALID_ARG, "g_nnz < 0");
+
+    // ---- labels and levels
+    int n_levels = 0;
+    for (int s = 0; s < n; ++s) {
+        if (!std::isfinite(d->energy[s])) return fail(MQCT_ERR_INVALID_ARG, "non-finite energy");
+        if (d->level[s] < 0 || d->level[s] >= n) return fail(MQCT_ERR_INVALID_ARG, "level id outside [0, N)");
+        if (d->j[s] >= 0 && std::abs(d->m[s]) > d->j[s]) return fail(MQCT_ERR_INVALID_ARG, "|m| > j");
+        n_levels = std::max(n_levels, d->level[s] + 1);
+    }
+    std::vector<double> lev_e(n_levels, NAN);
+    for (int s = 0; s < n; ++s) {
+        double &e = lev_e[d->level[s]];
+        if (std::isnan(e)) e = d->energy[s];
+        else if (e != d->energy[s]) return fail(MQCT_ERR_INVALID_ARG, "states of one level have different energies");
+    }
+    for (auto &e : lev_e)
+        if (std::isnan(e)) e = 0.0;  // unused level id
+
+    // ---- coupling entries per term (caller indices), duplicates summed
+    std::vector<std::map<std::pair<int, int>, double>> G(L);
+    double gmax = 0.0;
+    if (d->G) {
+        for (int l = 0; l < L; ++l)
+            for (int r = 0; r < n; ++r)
+                for (int c = 0; c < n; ++c) {
+                    double v = d->G[((size_t)l * n + r) * n + c];
+                    if (!std::isfinite(v)) return fail(MQCT_ERR_INVALID_ARG, "non-finite G");
+                    if (v != 0.0) G[l][{r, c}] += v;
+                }
+    } else {
+        for (int64_t i = 0; i < d->g_nnz; ++i) {
+            int l = d->g_term[i], r = d->g_row[i], c = d->g_col[i];
+            double v = d->g_val[i];
+            if (l < 0 || l >= L || r < 0 || r >= n || c < 0 || c >= n) return fail(MQCT_ERR_INVALID_ARG, "G triplet out of range");
+            if (!std::isfinite(v)) return fail(MQCT_ERR_INVALID_ARG, "non-finite G");
+            G[l][{r, c}] += v;
+        }
+    }
+    for (int l = 0; l < L; ++l)
+        for (auto &kv : G[l]) gmax = std::max(gmax, std::fabs(kv.second));
+    for (int l = 0; l < L; ++l)
+        for (auto &kv : G[l]) {
+            int r = kv.first.first, c = kv.first.second;
+            if (d->m[r] != d->m[c]) return fail(MQCT_ERR_INVALID_ARG, "G couples states of different m (Eq. 6)");
+            auto it = G[l].find({c, r});
+            double vt = it == G[l].end() ? 0.0 : it->second;
+            if (std::fabs(vt - kv.second) > 1e-12 * gmax) return fail(MQCT_ERR_INVALID_ARG, "G is not symmetric");
+        }
+
+    // ---- grid data
+    for (size_t i = 0; i < (size_t)L * ng; ++i)
+        if (!std::isfinite(d->v[i])) return fail(MQCT_ERR_INVALID_ARG, "non-finite v");
+    for (int i = 0; i < 2 * L; ++i)
+        if (!std::isfinite(d->dv_ends[i])) return fail(MQCT_ERR_INVALID_ARG, "non-finite dv_ends");
+
+    mqct_system_s *hs = new (std::nothrow) mqct_system_s();
+    if (!hs) return fail(MQCT_ERR_OOM, "host allocation failed");
+    System &S = hs->s;
+
+    // ---- internal order: blocks of equal m, largest block first, caller order inside
+    std::map<int, std::vector<int>> blocks;
+    for (int s = 0; s < n; ++s) blocks[d->m[s]].push_back(s);
+    std::vector<std::vector<int>> bl;
+    for (auto &kv : blocks) bl.push_back(kv.second);
+    std::stable_sort(bl.begin(), bl.end(), [](const std::vector<int> &a, const std::vector<int> &b) { return a.size() > b.size(); });
+    S.perm.clear();
+    for (auto &b : bl) {
+        S.max_block = std::max<int>(S.max_block, (int)b.size());
+        for (int s : b) S.perm.push_back(s);
+    }
+    S.inv.assign(n, 0);
+    for (int i = 0; i < n; ++i) S.inv[S.perm[i]] = i;
+    S.lev.resize(n);
+    for (int i = 0; i < n; ++i) S.lev[i] = d->level[S.perm[i]];
+
+    // ---- Coriolis partners (same level and j, m +- 1), internal indices
+    std::map<std::tuple<int, int, int>, int> where;
+    for (int i = 0; i < n; ++i) where[{d->level[S.perm[i]], d->j[S.perm[i]], d->m[S.perm[i]]}] = i;
+    std::vector<int> up(n), dn(n);
+    std::vector<double> aup(n, 0.0), adn(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        int s = S.perm[i], j = d->j[s], m = d->m[s], lv = d->level[s];
+        up[i] = dn[i] = i;
+        if (j < 0) continue;
+        auto iu = where.find({lv, j, m + 1}), id = where.find({lv, j, m - 1});
+        double jj = (double)j * (j + 1);
+        if (iu != where.end()) { up[i] = iu->second; aup[i] = std::sqrt(jj - (double)m * (m + 1)); }
+        if (id != where.end()) { dn[i] = id->second; adn[i] = std::sqrt(jj - (double)m * (m - 1)); }
+    }
+
+    // ---- splines of v_lambda and of the parameter derivatives
+    const int n_int = ng - 1;
+    const double h = (d->r_max - d->r_min) / (ng - 1);
+    std::vector<std::vector<dbl4>> vc(L);
+    std::vector<dbl4> vcoef((size_t)L * n_int);
+    for (int l = 0; l < L; ++l) {
+        clamped_spline(ng, h, d->v + (size_t)l * ng, d->dv_ends[2 * l], d->dv_ends[2 * l + 1], vc[l]);
+        std::copy(vc[l].begin(), vc[l].end(), vcoef.begin() + (size_t)l * n_int);
+    }
+    std::vector<dbl4> dvcoef;
+    if (P > 0) {
+        dvcoef.resize((size_t)P * L * n_int);
+        std::vector<dbl4> tmp;
+        for (int p = 0; p < P; ++p)
+            for (int l = 0; l < L; ++l) {
+                size_t o = (size_t)p * L + l;
+                for (int k = 0; k < ng; ++k)
+                    if (!std::isfinite(d->dv_dparam[o * ng + k])) { delete hs; return fail(MQCT_ERR_INVALID_ARG, "non-finite dv_dparam"); }
+                clamped_spline(ng, h, d->dv_dparam + o * ng, d->ddv_ends[2 * o], d->ddv_ends[2 * o + 1], tmp);
+                std::copy(tmp.begin(), tmp.end(), dvcoef.begin() + o * n_int);
+            }
+    }
+
+    // ---- G in internal indices, per term row lists; diagonal
+    std::vector<double> diag_g((size_t)L * n, 0.0);
+    std::vector<std::vector<std::vector<Entry>>> grows(L, std::vector<std::vector<Entry>>(n));
+    for (int l = 0; l < L; ++l)
+        for (auto &kv : G[l]) {
+            int r = S.inv[kv.first.first], c = S.inv[kv.first.second];
+            if (kv.second == 0.0) continue;
+            grows[l][r].push_back({r, c, kv.second});
+            if (r == c) diag_g[(size_t)l * n + r] = kv.second;
+        }
+    for (int l = 0; l < L; ++l)
+        for (auto &row : grows[l]) std::sort(row.begin(), row.end(), [](const Entry &a, const Entry &b) { return a.c < b.c; });
+
+    const int n_slices = (n + kSlice - 1) / kSlice;
+    DevSys &D = S.h;
+    std::memset(&D, 0, sizeof(D));
+    D.n = n; D.n_levels = n_levels; D.L = L; D.n_int = n_int; D.n_slices = n_slices; D.P = P;
+    D.path = d->path; D.precision = d->precision;
+    D.mu = d->mu; D.r_min = d->r_min; D.h = h; D.inv_h = 1.0 / h;
+
+    mqct_status st = MQCT_OK;
+    auto up_ = [&](auto &v, auto **dst) { if (st == MQCT_OK) st = upload(S, v, dst); };
+    up_(lev_e, &D.lev_energy);
+    up_(S.lev, &D.lev);
+    up_(S.perm, &D.perm);
+    up_(S.inv, &D.inv);
+    up_(up, &D.up);
+    up_(dn, &D.dn);
+    up_(aup, &D.aup);
+    up_(adn, &D.adn);
+    up_(diag_g, &D.diag_g);
+    up_(vcoef, &D.vcoef);
+    if (P > 0) up_(dvcoef, &D.dvcoef);
+
+    S.info.n_states = n;
+    S.info.n_levels = n_levels;
+    S.info.n_terms = L;
+    S.info.n_grid = ng;
+    S.info.n_blocks = (int)bl.size();
+    S.info.max_block = S.max_block;
+    S.info.path = d->path;
+    S.info.precision = d->precision;
+
+    if (d->path == MQCT_PATH_PLAIN) {
+        // union pattern of all terms, coefficients sum_l G^l_rc coef_l[k]
+        std::vector<std::vector<Entry>> rows(n);
+        for (int r = 0; r < n; ++r) {
+            std::map<int, int> cs;
+            for (int l = 0; l < L; ++l)
+                for (auto &e : grows[l][r]) cs[e.c] = 0;
+            for (auto &kv : cs) rows[r].push_back({r, kv.first, 0.0});
+        }
+        Sell sl = make_sell(n, rows);
+        const size_t nnz_pad = sl.cols.size();
+        // per row: map column -> position, and per term the G values in that order
+        std::vector<std::vector<std::vector<double>>> gv(n);
+        for (int r = 0; r < n; ++r) {
+            gv[r].assign(rows[r].size(), std::vector<double>(L, 0.0));
+            for (int l = 0; l < L; ++l)
+                for (auto &e : grows[l][r]) {
+                    auto it = std::lower_bound(rows[r].begin(), rows[r].end(), e.c, [](const Entry &a, int c) { return a.c < c; });
+                    gv[r][it - rows[r].begin()][l] = e.v;
+                }
+        }
+        std::vector<double2> T01(nnz_pad * n_int), T23(nnz_pad * n_int);
+        for (size_t e = 0; e < nnz_pad; ++e) {
+            int r = sl.row_of[e], k0 = sl.src[e];
+            for (int k = 0; k < n_int; ++k) {
+                double c[4] = {0, 0, 0, 0};
+                if (k0 >= 0)
+                    for (int l = 0; l < L; ++l) {
+                        double g = gv[r][k0][l];
+                        if (g == 0.0) continue;
+                        const dbl4 &q = vc[l][k];
+                        c[0] += g * q.x; c[1] += g * q.y; c[2] += g * q.z; c[3] += g * q.w;
+                    }
+                T01[(size_t)k * nnz_pad + e] = make_double2(c[0], c[1]);
+                T23[(size_t)k * nnz_pad + e] = make_double2(c[2], c[3]);
+            }
+        }
+        int64_t nnz = 0;
+        for (auto &r : rows) nnz += (int64_t)r.size();
+        D.nnz_pad = (long long)nnz_pad;
+        up_(sl.off, &D.sl_off);
+        up_(sl.cols, &D.cols);
+        up_(T01, &D.T01);
+        up_(T23, &D.T23);
+        if (d->precision != MQCT_FP64) {
+            std::vector<float2> f01(T01.size()), f23(T23.size());
+            for (size_t i = 0; i < T01.size(); ++i) {
+                f01[i] = make_float2((float)T01[i].x, (float)T01[i].y);
+                f23[i] = make_float2((float)T23[i].x, (float)T23[i].y);
+            }
+            up_(f01, &D.T01f);
+            up_(f23, &D.T23f);
+        }
+        S.info.table_nnz = nnz;
+        S.info.table_bytes = (int64_t)nnz_pad * n_int * 32;
+    } else {
+        // identity terms are applied directly; others get one sliced-ELL matrix each
+        std::vector<int> fterm, foff, fcols;
+        std::vector<double> fval;
+        unsigned long long idm = 0;
+        int64_t gnnz = 0;
+        for (int l = 0; l < L; ++l) {
+            bool ident = true;
+            for (int r = 0; r < n && ident; ++r) {
+                if (grows[l][r].size() != 1 || grows[l][r][0].c != r || grows[l][r][0].v != 1.0) ident = false;
+            }
+            bool empty = true;
+            for (int r = 0; r < n; ++r) if (!grows[l][r].empty()) empty = false;
+            if (ident) { idm |= 1ull << l; continue; }
+            if (empty) continue;
+            Sell sl = make_sell(n, grows[l]);
+            fterm.push_back(l);
+            int base = (int)fcols.size();
+            for (int s2 = 0; s2 <= n_slices; ++s2) foff.push_back(base + sl.off[s2]);
+            for (size_t e = 0; e < sl.cols.size(); ++e) {
+                fcols.push_back(sl.cols[e]);
+                int r = sl.row_of[e], k0 = sl.src[e];
+                fval.push_back(k0 >= 0 ? grows[l][r][k0].v : 0.0);
+            }
+            for (int r = 0; r < n; ++r) gnnz += (int64_t)grows[l][r].size();
+        }
+        D.n_f = (int)fterm.size();
+        D.id_mask = idm;
+        up_(fterm, &D.f_term);
+        up_(foff, &D.f_sl_off);
+        up_(fcols, &D.f_cols);
+        up_(fval, &D.f_val);
+        if (d->precision != MQCT_FP64) {
+            std::vector<float> ff(fval.begin(), fval.end());
+            up_(ff, &D.f_valf);
+        }
+        S.info.glambda_nnz = gnnz;
+    }
+    if (st == MQCT_OK) {
+        cudaError_t e = cudaMalloc(&S.d, sizeof(DevSys));
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
+        else {
+            S.info.device_bytes += sizeof(DevSys);
+            e = cudaMemcpy(S.d, &D, sizeof(DevSys), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy");
+        }
+    }
+    if (st != MQCT_OK) {
+        release(S);
+        delete hs;
+        return st;
+    }
+    *out = hs;
+    return MQCT_OK;
+}
+
+extern "C" mqct_status mqct_destroy_system(mqct_system sys)
+{
+    if (!sys) return MQCT_OK;
+    release(sys->s);
+    delete sys;
+    return MQCT_OK;
+}
+
+extern "C" mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out)
+{
+    if (!sys || !out) return fail(MQCT_ERR_INVALID_ARG, "mqct_system_info: NULL argument");
+    *out = sys->s.info;
+    return MQCT_OK;
+}
+
+extern "C" const char *mqct_last_error(void) { return last_error_cstr(); }
+
+extern "C" const char *mqct_version(void) { return "mqct-gb300 0.1 (sm_103a)"; }

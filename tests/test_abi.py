@@ -1,0 +1,178 @@
+"""C-ABI library checks that need no GPU: it loads, exports every declared symbol, its
+structs match the binding, and its host-side logic (the built-in system builder, input
+validation) behaves.  No compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2312_02322_gb300 import api, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2312_02322_gb300 import build
+
+    build.build()
+    return api.lib()
+
+
+def declared_functions():
+    inc = os.path.join(ROOT, "include")
+    names = set()
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(mqct_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "mqct_propagate" in names and "mqct_adjoint" in names and "mqct_cross_sections" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_version_and_last_error(L):
+    assert "sm_103a" in api.version()
+    d = api.Desc()
+    h = C.c_void_p()
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == api.ERR_INVALID_ARG
+    assert b"n_states" in L.mqct_last_error()
+
+
+def build_desc(jmax=3, path="plain", with_params=False, n_grid=40):
+    p = inputs.diatom_pes_params(jmax=jmax, n_grid=n_grid)
+    dp = api.DiatomParams()
+    dp.jmax, dp.bconst, dp.mu, dp.n_terms = p.jmax, p.bconst, p.mu, p.n_terms
+    for i in range(p.n_terms):
+        dp.A[i], dp.beta[i] = p.A[i], p.beta[i]
+    dp.c6, dp.rd, dp.n_grid, dp.r_min, dp.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
+    dp.with_params = int(with_params)
+    dp.path = api._PATHS[path]
+    d = api.Desc()
+    assert api.lib().mqct_build_diatom(C.byref(dp), C.byref(d)) == 0
+    return d, p
+
+
+def dense_G(d):
+    n, L = d.n_states, d.n_terms
+    G = np.zeros((L, n, n))
+    t = np.ctypeslib.as_array(C.cast(d.g_term, C.POINTER(C.c_int32)), (d.g_nnz,))
+    r = np.ctypeslib.as_array(C.cast(d.g_row, C.POINTER(C.c_int32)), (d.g_nnz,))
+    c = np.ctypeslib.as_array(C.cast(d.g_col, C.POINTER(C.c_int32)), (d.g_nnz,))
+    v = np.ctypeslib.as_array(C.cast(d.g_val, C.POINTER(C.c_double)), (d.g_nnz,))
+    np.add.at(G, (t, r, c), v)
+    return G
+
+
+def test_builder_coupling_matches_oracle(L, ora):
+    """The library's quadrature-built G^lambda (Eq. 15) agrees with the oracle's Racah-formula G."""
+    for jmax in (3, 12, 39):
+        d, p = build_desc(jmax)
+        G = dense_G(d)
+        for lam in range(5):
+            assert np.max(np.abs(G[lam] - ora.diatom_G(jmax, lam))) < 1e-13
+        e = np.ctypeslib.as_array(C.cast(d.energy, C.POINTER(C.c_double)), (d.n_states,))
+        e2, lev, jq, mq = ora.diatom_basis(jmax, p.bconst)
+        assert np.array_equal(e, e2)
+        api.lib().mqct_free_desc(C.byref(d))
+
+
+def test_builder_pes_matches_oracle(L, ora):
+    d, p = build_desc(4, with_params=True, n_grid=60)
+    v = np.ctypeslib.as_array(C.cast(d.v, C.POINTER(C.c_double)), (5, 60))
+    ends = np.ctypeslib.as_array(C.cast(d.dv_ends, C.POINTER(C.c_double)), (5, 2))
+    dvp = np.ctypeslib.as_array(C.cast(d.dv_dparam, C.POINTER(C.c_double)), (10, 5, 60))
+    dvpe = np.ctypeslib.as_array(C.cast(d.ddv_ends, C.POINTER(C.c_double)), (10, 5, 2))
+    v2, e2, dvp2, dvpe2 = ora.diatom_pes(p.A, p.beta, p.c6, p.rd, 60, p.r_min, p.r_max, with_params=True)
+    assert np.allclose(v, v2, rtol=1e-14, atol=0)
+    assert np.allclose(ends, e2, rtol=1e-12, atol=1e-30)
+    assert np.allclose(dvp, dvp2, rtol=1e-14, atol=0)
+    assert np.allclose(dvpe, dvpe2, rtol=1e-12, atol=1e-30)
+    api.lib().mqct_free_desc(C.byref(d))
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("n_grid", 3, b"n_grid"),
+    ("mu", -1.0, b"mu"),
+    ("n_terms", 0, b"n_terms"),
+    ("path", 7, b"path"),
+    ("flags", 1, b"flags"),
+])
+def test_create_validation_rejects_before_gpu(L, field, value, needle):
+    d, _ = build_desc(2)
+    setattr(d, field, value)
+    h = C.c_void_p()
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == api.ERR_INVALID_ARG
+    assert needle in L.mqct_last_error()
+    assert not h.value
+    setattr(d, "n_grid", 40)
+    api.lib().mqct_free_desc(C.byref(d))
+
+
+def test_create_rejects_coupling_across_m(L):
+    n = 2
+    e = np.zeros(n)
+    lev = np.array([0, 1], np.int32)
+    j = np.array([1, 1], np.int32)
+    m = np.array([0, 1], np.int32)
+    G = np.array([[[0.0, 1.0], [1.0, 0.0]]])
+    v = np.zeros((1, 8))
+    ends = np.zeros((1, 2))
+    d = api.Desc()
+    d.n_states, d.energy, d.level, d.j, d.m = n, e.ctypes.data, lev.ctypes.data, j.ctypes.data, m.ctypes.data
+    d.mu, d.n_terms, d.G = 100.0, 1, G.ctypes.data
+    d.n_grid, d.r_min, d.r_max, d.v, d.dv_ends = 8, 2.0, 30.0, v.ctypes.data, ends.ctypes.data
+    h = C.c_void_p()
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == api.ERR_INVALID_ARG
+    assert b"different m" in L.mqct_last_error()
+    m[1] = 0
+    G[0, 0, 1] = 0.5  # not symmetric
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == api.ERR_INVALID_ARG
+    assert b"symmetric" in L.mqct_last_error()
+
+
+def test_struct_layouts_match_header(L, tmp_path):
+    """Compile a probe against include/mqct.h with gcc and compare sizes and offsets with the binding."""
+    import subprocess
+
+    src = tmp_path / "layout.c"
+    checks = {
+        "mqct_system_desc": (api.Desc, ["n_states", "energy", "mu", "n_terms", "G", "g_nnz", "g_val", "n_grid",
+                                        "r_min", "v", "n_params", "ddv_ends", "path", "flags"]),
+        "mqct_system_info_t": (api.Info, ["n_states", "table_nnz", "device_bytes"]),
+        "mqct_diatom_params": (api.DiatomParams, ["jmax", "bconst", "mu", "n_terms", "A", "beta", "c6", "rd",
+                                                  "n_grid", "r_min", "with_params", "path", "precision"]),
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mqct.h"', "int main(void) {"]
+    for st, (_, fields) in checks.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines.append('printf("mqct_traj %zu\\n", sizeof(mqct_traj));')
+    for f in api.TRAJ_DTYPE.names[:-1]:
+        lines.append(f'printf("mqct_traj.{f} %zu\\n", offsetof(mqct_traj, {f}));')
+    lines.append('printf("mqct_diag %zu\\n", sizeof(mqct_diag));')
+    for f in api.DIAG_DTYPE.names:
+        lines.append(f'printf("mqct_diag.{f} %zu\\n", offsetof(mqct_diag, {f}));')
+    lines.append("return 0; }")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)]).decode().split("\n") if l)
+    for st, (cls, fields) in checks.items():
+        assert int(out[st]) == C.sizeof(cls), st
+        for f in fields:
+            assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+    assert int(out["mqct_traj"]) == api.TRAJ_DTYPE.itemsize
+    for f in api.TRAJ_DTYPE.names[:-1]:
+        assert int(out[f"mqct_traj.{f}"]) == api.TRAJ_DTYPE.fields[f][1], f
+    assert int(out["mqct_diag"]) == api.DIAG_DTYPE.itemsize
+    for f in api.DIAG_DTYPE.names:
+        assert int(out[f"mqct_diag.{f}"]) == api.DIAG_DTYPE.fields[f][1], f

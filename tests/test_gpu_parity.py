@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on the same
+seeded inputs.  FP64 paths: 1e-8 absolute on every final population and on the cross
+sections relative to pi b_max^2; identical step counts and statuses."""
+import numpy as np
+import pytest
+
+from paper_2312_02322_gb300 import inputs as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-8
+
+
+@pytest.fixture(scope="module")
+def mq():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_02322_gb300 import api, build
+
+    build.build()
+    return api
+
+
+def oracle_system(ora, p, with_params=False):
+    return ora.diatom_system(p.jmax, p.bconst, p.mu, p.A, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max,
+                             with_params=with_params)
+
+
+def oracle_run(ora, osys, ts):
+    init = [j * j + j + m for j, m in zip(ts.init_j, ts.init_m)]
+    amp, res = ora.propagate(osys, ts.e_coll, ts.b, init, r0=ts.r0, r_end=ts.r_end, dt=ts.dt,
+                             max_steps=ts.max_steps)
+    return np.abs(amp) ** 2, res
+
+
+def gpu_run(mq, sys, ts, device=False):
+    tr = mq.make_trajs(ts, sys)
+    if device:
+        import torch
+
+        trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+        pop, _, diag = mq.propagate(sys, trd, device=True)
+        torch.cuda.synchronize()
+        return pop.cpu().numpy(), mq.diag_to_numpy(diag)
+    pop, _, diag = mq.propagate(sys, tr, device=False)
+    return pop, diag
+
+
+def compare(pop_g, diag_g, pop_o, res_o, tol=TOL_FP64):
+    assert np.array_equal(diag_g["steps"], res_o["steps"])
+    assert np.array_equal(diag_g["status"], res_o["status"])
+    err = np.max(np.abs(pop_g - pop_o))
+    assert err < tol, err
+    assert np.allclose(diag_g["t_final"], res_o["t_final"], rtol=0, atol=0)
+    return err
+
+
+@pytest.mark.parametrize("path", ["plain", "factorised"])
+def test_small_full_m_average(mq, ora, path):
+    """j <= 3 (N = 16), two initial levels with every m', six b: populations, diagnostics and sigma."""
+    p, ts = W.small_workload(jmax=3, n_b=6, energies=(500.0, 2000.0), init_js=(0, 1), b_max=8.0, n_grid=120)
+    sys = mq.System.diatom(p, path=path)
+    pop_g, diag_g = gpu_run(mq, sys, ts)
+    osys = oracle_system(ora, p)
+    pop_o, res_o = oracle_run(ora, osys, ts)
+    compare(pop_g, diag_g, pop_o, res_o)
+    # diagnostics agree with the oracle's to well within their own size
+    assert np.allclose(diag_g["norm_dev"], res_o["norm_dev"], rtol=0, atol=1e-12)
+    assert np.allclose(diag_g["energy_dev"], res_o["energy_dev"], rtol=0, atol=1e-12)
+    assert np.allclose(diag_g["angmom_dev"], res_o["angmom_dev"], rtol=0, atol=1e-9)
+    w = mq.sigma_weights(ts, diag_g["status"])
+    sig_g = mq.cross_sections(sys, pop_g, w, ts.group, ts.n_groups)
+    sig_o = ora.cross_sections(osys, pop_o, w, ts.group, ts.n_groups)
+    assert np.max(np.abs(sig_g - sig_o)) < TOL_FP64 * np.pi * ts.b_max ** 2
+    assert np.allclose(sig_g.sum(axis=1), np.pi * ts.b_max ** 2, rtol=1e-9)
+
+
+def test_workload1_full(mq, ora):
+    """N = 49 workload (E = 500 cm^-1, j' = 0, 32 b on 0-12 bohr): every trajectory, plain FP64."""
+    p, ts = W.workload1()
+    sys = mq.System.diatom(p, path="plain")
+    pop_g, diag_g = gpu_run(mq, sys, ts, device=True)
+    pop_o, res_o = oracle_run(ora, oracle_system(ora, p), ts)
+    compare(pop_g, diag_g, pop_o, res_o)
+    assert np.max(diag_g["norm_dev"]) < 1e-10
+
+
+def test_paths_agree(mq):
+    """PLAIN (spline of M) and FACTORISED (sum of v_l G^l) are the same function: agree to 1e-12."""
+    p, ts = W.small_workload(jmax=5, n_b=5, energies=(800.0,), init_js=(1, 2), b_max=9.0, n_grid=150)
+    a = mq.System.diatom(p, path="plain")
+    b = mq.System.diatom(p, path="factorised")
+    pa, da = gpu_run(mq, a, ts)
+    pb, db = gpu_run(mq, b, ts)
+    assert np.array_equal(da["steps"], db["steps"])
+    assert np.max(np.abs(pa - pb)) < 1e-12
+
+
+def test_host_and_device_pointers_agree(mq):
+    p, ts = W.small_workload(jmax=2, n_b=4, energies=(600.0,), init_js=(1,), b_max=7.0, n_grid=80)
+    sys = mq.System.diatom(p)
+    ph, dh = gpu_run(mq, sys, ts, device=False)
+    pd, dd = gpu_run(mq, sys, ts, device=True)
+    assert np.array_equal(ph, pd)
+    assert np.array_equal(dh["steps"], dd["steps"])
+
+
+def test_workload2_sampled_at_full_size(mq, ora):
+    """N = 441 workload: the full 3072-trajectory batch in the bench launch configuration;
+    a seeded sample of its trajectories is recomputed one by one by the oracle."""
+    import torch
+
+    p, ts = W.workload2()
+    sys = mq.System.diatom(p, path="plain")
+    tr = mq.make_trajs(ts, sys)
+    trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+    pop, _, diag = mq.propagate(sys, trd, device=True)
+    torch.cuda.synchronize()
+    pop = pop.cpu().numpy()
+    diag = mq.diag_to_numpy(diag)
+    assert np.all(diag["status"] == 0)
+    # RK4 at dt = 5 is not exactly unitary: for this basis (couplings up to ~3000 cm^-1 at the
+    # turning point, gaps up to 1480 cm^-1) the norm drifts by up to ~2e-7; the oracle shows the
+    # same drift on the sampled trajectories below
+    assert np.max(diag["norm_dev"]) < 1e-6
+    assert np.max(np.abs(pop.sum(axis=1) - 1.0)) <= np.max(diag["norm_dev"]) * 1.0001
+    rng = np.random.default_rng(7)
+    # short trajectories (E = 3000 cm^-1) keep the oracle within seconds; one per initial level,
+    # plus the trajectory with the largest norm drift
+    cand = np.flatnonzero(ts.e_coll == ts.e_coll.max())
+    pick = np.concatenate([rng.choice(cand[ts.init_j[cand] == j], 1) for j in (0, 1, 2)])
+    pick = np.unique(np.append(pick, np.argmax(diag["norm_dev"])))
+    pop_o, res_o = oracle_run(ora, oracle_system(ora, p), ts.subset(pick))
+    sub = {k: diag[k][pick] for k in diag.dtype.names}
+    compare(pop[pick], sub, pop_o, res_o)
+    assert np.allclose(sub["norm_dev"], res_o["norm_dev"], rtol=1e-3, atol=1e-12)
+
+
+def test_edge_cases(mq, ora):
+    import torch
+
+    p, ts = W.small_workload(jmax=2, n_b=2, energies=(500.0,), init_js=(0,), b_max=6.0, n_grid=60)
+    sys = mq.System.diatom(p)
+    # no trajectories
+    pop, _, diag = mq.propagate(sys, np.zeros(0, mq.TRAJ_DTYPE), device=False)
+    assert pop.shape == (0, sys.n)
+    # max_steps = 0: initial state returned, status MAX_STEPS
+    tr = mq.make_trajs(ts, sys)
+    tr["max_steps"] = 0
+    pop, _, diag = mq.propagate(sys, tr, device=False)
+    assert np.all(diag["status"] == mq.TRAJ_MAX_STEPS) and np.all(diag["steps"] == 0)
+    assert np.allclose(pop[:, 0], 1.0) and np.allclose(pop[:, 1:], 0.0)
+    # invalid host trajectory -> INVALID_ARG, nothing launched
+    tr = mq.make_trajs(ts, sys)
+    tr["init_state"][0] = sys.n
+    with pytest.raises(mq.MQCTError) as ei:
+        mq.propagate(sys, tr, device=False)
+    assert ei.value.status == mq.ERR_INVALID_ARG
+    # invalid device trajectory -> status INVALID for it, others run
+    trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+    _, _, diag = mq.propagate(sys, trd, device=True)
+    d = mq.diag_to_numpy(diag)
+    assert d["status"][0] == mq.TRAJ_INVALID and d["status"][1] == 0
+    # head-on at high energy reaches below the grid: TABLE_RANGE reported, same as the oracle
+    p2 = W.diatom_pes_params(jmax=1, n_grid=60)
+    p2.r_min = 3.0
+    sys2 = mq.System.diatom(p2)
+    ts2 = W.regular_set([20000.0], [0], n_b=1, b_max=0.2)
+    pg, dg = gpu_run(mq, sys2, ts2)
+    po, ro = oracle_run(ora, oracle_system(ora, p2), ts2)
+    assert dg["status"][0] & mq.TRAJ_TABLE_RANGE
+    compare(pg, dg, po, ro)
+
+
+def test_two_level_custom_system(mq, ora):
+    """A caller-described system (dense G, Coriolis off via j = -1, single state per block of m)
+    against the oracle: Rabi-type two-level problem with an R-dependent coupling."""
+    import ctypes as C
+
+    n, L, ng = 2, 2, 30
+    e = np.array([0.0, 2e-3])
+    lev = np.array([0, 1], np.int32)
+    jj = np.array([-1, -1], np.int32)
+    mm = np.array([0, 0], np.int32)
+    G = np.zeros((L, n, n))
+    G[0] = np.eye(2)
+    G[1] = [[0.0, 1.0], [1.0, 0.0]]
+    R = np.linspace(2.0, 30.0, ng)
+    v = np.stack([0.5 * np.exp(-1.5 * R), 0.05 * np.exp(-1.2 * R)])
+    ends = np.array([[-0.75 * np.exp(-3.0), -0.75 * np.exp(-45.0)], [-0.06 * np.exp(-2.4), -0.06 * np.exp(-36.0)]])
+    d = mq.Desc()
+    d.n_states, d.energy, d.level, d.j, d.m = n, e.ctypes.data, lev.ctypes.data, jj.ctypes.data, mm.ctypes.data
+    d.mu, d.n_terms, d.G = 3000.0, L, G.ctypes.data
+    d.n_grid, d.r_min, d.r_max, d.v, d.dv_ends = ng, 2.0, 30.0, v.ctypes.data, ends.ctypes.data
+    sys = mq.System(d)
+    tr = np.zeros(3, mq.TRAJ_DTYPE)
+    tr["e_coll"] = [5e-3, 1e-2, 2e-2]
+    tr["b"] = [0.0, 1.0, 3.0]
+    tr["r0"], tr["r_end"], tr["dt"], tr["max_steps"] = 30.0, 30.0, 4.0, 100000
+    pop, _, diag = mq.propagate(sys, tr, device=False)
+    osys = ora.System(e, lev, jj, mm, G, v, ends, 3000.0, 2.0, 30.0)
+    amp, res = ora.propagate(osys, tr["e_coll"], tr["b"], [0, 0, 0], dt=4.0, max_steps=100000)
+    compare(pop, diag, np.abs(amp) ** 2, res)
+    assert np.min(pop[:, 1]) > 1e-4
