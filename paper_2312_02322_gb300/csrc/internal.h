@@ -56,6 +56,13 @@ struct DevSys {
     const int *f_cols;
     const double *f_val;
     const float *f_valf;
+    // Batched mixed-precision path: CSR of each stored term (rows in internal order) and
+    // FP32 spline coefficients of v_lambda.
+    const int *csr_ptr;        // [n_f][n+1] offsets into csr_col / csr_val
+    const int *csr_col;
+    const float *csr_val;
+    const float4 *vcoef_f;     // [L][n_int]
+    int max_row_nnz;           // max over rows of the summed CSR row lengths
 };
 
 struct System {
@@ -70,6 +77,23 @@ struct System {
 
 void set_error(const std::string &msg);
 const char *last_error_cstr();
+
+// arguments of the batched mixed-precision launch (batched.cu)
+struct BatchArgs {
+    const DevSys *sys;
+    const mqct_traj *trajs;
+    const int *order;
+    int n;
+    int *queue;
+    double *pop;
+    double *amp;
+    mqct_diag *diag;
+    int nmax;
+    int sys_idx;  // trajectories must name this system
+};
+cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width);
+int batched_width(const DevSys &h);
+
 mqct_status fail(mqct_status st, const std::string &msg);
 mqct_status cuda_fail(cudaError_t e, const char *what);
 

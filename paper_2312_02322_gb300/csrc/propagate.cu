@@ -454,7 +454,11 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
         if (h.path != path || h.precision != prec)
             return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: systems differ in path or precision");
     }
-    if (prec != MQCT_FP64) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: only FP64 systems in this build");
+    if (prec != MQCT_FP64) {
+        if (n_systems != 1) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: mixed precision takes one system per call");
+        if (batched_width(systems[0]->s.h) == 0)
+            return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: basis too large for the batched kernel");
+    }
     if (n == 0) return MQCT_OK;
 
     const bool trajs_dev = is_device_ptr(trajs);
@@ -519,6 +523,12 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
         return cuda_fail(e, "cub::DeviceRadixSort");
     if ((e = cudaMemsetAsync(queue, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
+    if (prec != MQCT_FP64) {
+        BatchArgs ba;
+        ba.sys = systems[0]->s.d; ba.trajs = dtr; ba.order = order; ba.n = n; ba.queue = queue;
+        ba.pop = dpop; ba.amp = damp; ba.diag = ddiag; ba.nmax = nmax; ba.sys_idx = 0;
+        if ((e = run_batched(ba, systems[0]->s.h, st, nullptr)) != cudaSuccess) return cuda_fail(e, "batched launch");
+    } else {
     // launch shape: one warp per 32-row slice (balanced), persistent grid
     const int maxw = kPropThreads / 32;
     int per = (max_slices + maxw - 1) / maxw;
@@ -539,6 +549,7 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
     pa.pop = dpop; pa.amp = damp; pa.diag = ddiag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
     k_propagate_fp64<<<grid, threads, smem, st>>>(pa);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");
+    }
 
     if (!any_host) return MQCT_OK;
     if (final_pop && !pop_dev &&

@@ -166,6 +166,8 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     if (d->precision != MQCT_FP64 && d->precision != MQCT_FP32 && d->precision != MQCT_BF16X3)
         return fail(MQCT_ERR_INVALID_ARG, "unknown precision");
     if (d->precision == MQCT_BF16X3) return fail(MQCT_ERR_UNSUPPORTED, "BF16X3 precision is not available in this build");
+    if (d->precision != MQCT_FP64 && d->path != MQCT_PATH_FACTORISED)
+        return fail(MQCT_ERR_UNSUPPORTED, "mixed precision runs on the factorised (batched) path only");
     if (d->flags != 0) return fail(MQCT_ERR_INVALID_ARG, "flags must be 0");
     if (P < 0 || (P > 0 && (!d->dv_dparam || !d->ddv_ends))) return fail(MQCT_ERR_INVALID_ARG, "bad parameter tables");
     if (!d->G && d->g_nnz > 0 && (!d->g_term || !d->g_row || !d->g_col || !d->g_val))
@@ -371,15 +373,6 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         up_(sl.cols, &D.cols);
         up_(T01, &D.T01);
         up_(T23, &D.T23);
-        if (d->precision != MQCT_FP64) {
-            std::vector<float2> f01(T01.size()), f23(T23.size());
-            for (size_t i = 0; i < T01.size(); ++i) {
-                f01[i] = make_float2((float)T01[i].x, (float)T01[i].y);
-                f23[i] = make_float2((float)T23[i].x, (float)T23[i].y);
-            }
-            up_(f01, &D.T01f);
-            up_(f23, &D.T23f);
-        }
         S.info.table_nnz = nnz;
         S.info.table_bytes = (int64_t)nnz_pad * n_int * 32;
     } else {
@@ -415,8 +408,31 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         up_(fcols, &D.f_cols);
         up_(fval, &D.f_val);
         if (d->precision != MQCT_FP64) {
-            std::vector<float> ff(fval.begin(), fval.end());
-            up_(ff, &D.f_valf);
+            // CSR per stored term for the batched kernel, FP32 values and spline coefficients
+            std::vector<int> cptr, ccol;
+            std::vector<float> cval;
+            int max_row = 0;
+            std::vector<int> row_tot(n, 0);
+            for (int l : fterm) {
+                for (int r = 0; r < n; ++r) {
+                    cptr.push_back((int)ccol.size());
+                    for (auto &e : grows[l][r]) {
+                        ccol.push_back(e.c);
+                        cval.push_back((float)e.v);
+                    }
+                    row_tot[r] += (int)grows[l][r].size();
+                }
+                cptr.push_back((int)ccol.size());
+            }
+            for (int r = 0; r < n; ++r) max_row = std::max(max_row, row_tot[r]);
+            std::vector<float4> vf(vcoef.size());
+            for (size_t i = 0; i < vcoef.size(); ++i)
+                vf[i] = make_float4((float)vcoef[i].x, (float)vcoef[i].y, (float)vcoef[i].z, (float)vcoef[i].w);
+            up_(cptr, &D.csr_ptr);
+            up_(ccol, &D.csr_col);
+            up_(cval, &D.csr_val);
+            up_(vf, &D.vcoef_f);
+            D.max_row_nnz = max_row;
         }
         S.info.glambda_nnz = gnnz;
     }
