@@ -246,7 +246,7 @@ def gpu_arm(args):
     achieved = flops_stage * stages / (k_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
                 "frac": achieved * 1e3 / fp64_peak, "traffic": None,
-                "kernel": "k_propagate_fp64", "peak_source": f"measured {args.precision.upper()} FMA probe (mqct_probe_fma_rate)",
+                "kernel": "k_propagate_fp64" if args.precision == "fp64" else "k_batched_f32", "peak_source": f"measured {args.precision.upper()} FMA probe (mqct_probe_fma_rate)",
                 "algorithmic_flops_per_traj_stage": flops_stage, "traj_stages_per_launch": stages,
                 "kernel_ms": k_ms}
     try:

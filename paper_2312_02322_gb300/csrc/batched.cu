@@ -256,15 +256,26 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
                         if (a.amp) { a.amp[2 * o] = a0.x; a.amp[2 * o + 1] = a0.y; }
                         continue;
                     }
-                    ACC[e] = kk;
+                    // the accumulator enters the step holding the rounding error of the last update
+                    const float2 cmp = ACC[e];
+                    ACC[e] = make_float2(kk.x + cmp.x, kk.y + cmp.y);
                 } else {
                     float2 acc = ACC[e];
                     acc.x = fmaf(wgt, kk.x, acc.x);
                     acc.y = fmaf(wgt, kk.y, acc.y);
                     if (s == 3) {
-                        const float h6 = dtf / 6.0f;
-                        const float2 an = make_float2(fmaf(h6, acc.x, a0.x), fmaf(h6, acc.y, a0.y));
+                        // compensated update a + (dt/6) acc (two-sum): in the interaction picture a
+                        // changes by tiny increments far from the collision, which a plain FP32 add
+                        // would round away; the error is carried to the next step's accumulator
+                        const float h6 = dtf / 6.0f, ih6 = 6.0f / dtf;
+                        const float ix = h6 * acc.x, iy = h6 * acc.y;
+                        const float sx = __fadd_rn(a0.x, ix), sy = __fadd_rn(a0.y, iy);
+                        const float bx = __fsub_rn(sx, a0.x), by = __fsub_rn(sy, a0.y);
+                        const float ex = __fadd_rn(__fsub_rn(a0.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
+                        const float ey = __fadd_rn(__fsub_rn(a0.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
+                        const float2 an = make_float2(sx, sy);
                         A[e] = an;
+                        ACC[e] = make_float2(ex * ih6, ey * ih6);
                         const float2 pn = PHn[lev * B + b];
                         C[e] = make_float2(pn.x * an.x - pn.y * an.y, pn.x * an.y + pn.y * an.x);
                         continue;
