@@ -197,6 +197,27 @@ mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out);
 mqct_status mqct_propagate(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
                            double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream);
 
+/* mqct_propagate without any memory allocation.  The paper has no counterpart: this call
+ * exists for callers that may not allocate GPU memory while they run it -- frameworks that
+ * own a fixed device pool and forbid cudaMalloc / cudaFree after start-up, real-time loops
+ * that cannot afford allocation latency, processes that must not grow the driver's pool.
+ * It runs the same FP64 persistent kernel as mqct_propagate (FP64 systems, plain or
+ * factorised) and allocates nothing: its scratch (work-queue counter, system views) is a
+ * file-scope device array of 256 + 16 * sizeof(system view) bytes that every GPU loading
+ * the library holds until the process exits.
+ *   - at most 16 systems per call (the size of that array); more -> MQCT_ERR_INVALID_ARG;
+ *   - trajs, final_pop, final_amp and diag must be DEVICE pointers (outputs may be NULL);
+ *     layouts as for mqct_propagate; trajectories are claimed in the caller's order;
+ *   - the call only enqueues work on `cuda_stream` and returns MQCT_OK; per-trajectory
+ *     status is in diag;
+ *   - all calls share the one scratch array: two calls whose work overlaps on the GPU (on
+ *     different streams, or from different threads without ordering) race on it;
+ *   - the first call on a device looks up the array's device address on that device (with
+ *     it current); make that first call before any stream capture.
+ * Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_CUDA. */
+mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
+                                   double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream);
+
 /* Cross sections (Sec. II):
  *   sigma_out[g][l''] = sum_{t : group[t] = g} weight[t] * sum_{s in level l''} final_pop[t][s]
  * final_pop [n][N] (row stride N of `sys`), weight [n], group [n] (entries outside

@@ -78,6 +78,25 @@ struct System {
 void set_error(const std::string &msg);
 const char *last_error_cstr();
 
+// arguments of the persistent FP64 launch (propagate.cu)
+constexpr int kPropThreads = 512;  // upper bound of the block size (register budget)
+struct PropArgs {
+    const DevSys *sys;
+    const mqct_traj *trajs;
+    const int *order;  // work order (trajectory indices), or nullptr for the caller's order
+    int n, n_systems;
+    int *queue;        // work counter, zero at launch
+    double *pop;
+    double *amp;
+    mqct_diag *diag;
+    int nmax;      // row stride of pop / amp
+    int smem_n;    // shared-memory vector length (max n over systems)
+    int smem_lev;  // max n_levels over systems
+};
+#ifdef __CUDACC__
+__global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a);
+#endif
+
 // arguments of the batched mixed-precision launch (batched.cu)
 struct BatchArgs {
     const DevSys *sys;

@@ -25,22 +25,6 @@
 
 namespace mqct {
 
-constexpr int kPropThreads = 512;  // upper bound of the block size (register budget)
-
-struct PropArgs {
-    const DevSys *sys;
-    const mqct_traj *trajs;
-    const int *order;
-    int n, n_systems;
-    int *queue;
-    double *pop;
-    double *amp;
-    mqct_diag *diag;
-    int nmax;      // row stride of pop / amp
-    int smem_n;    // shared-memory vector length (max n over systems)
-    int smem_lev;  // max n_levels over systems
-};
-
 struct Ctl {
     double q[4], qs[4], lacc[4];
     double phidot, x, dt, r_end;
