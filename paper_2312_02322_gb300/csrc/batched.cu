@@ -1,14 +1,18 @@
 // Batched mixed-precision trajectory kernel (factorised path, FP32 amplitudes).
 //
 // One CTA integrates B trajectories at once: their phase-rotated stage amplitudes form the
-// N x B block C (one column per trajectory, FP32 complex, shared memory).  Per RK4 stage:
-//   P3  contraction: for every stored term lambda, Y_lambda = G^lambda C (sparse G, the same
-//       row entries applied to all B columns), combined per column with the FP32 spline
-//       values v_lambda(R_b), v_lambda'(R_b):  w = M(R_b) c_b, u = M'(R_b) c_b   (Eq. 12);
-//       Coriolis stencil Dc_b = (J+ - J-) c_b; partial sums of the force -Re(c^dag u), the
-//       torque Re(c^dag D w) = -Re((Dc)^dag w) and (stage 0) Re(c^dag w);
+// N x B block C (one column per trajectory, FP32 complex, shared memory, row-major so that a
+// row of four columns is 32 contiguous bytes).  A thread owns units (row r, 4 columns); the
+// sparse G entries of a row are loaded once and applied to the four columns.  Per RK4 stage:
+//   P3  contraction: for every stored term lambda, Y_lambda = G^lambda C, combined per column
+//       with the FP32 spline values v_lambda(R_b), v_lambda'(R_b):  w = M(R_b) c_b and
+//       u = M'(R_b) c_b   (Eq. 12); Coriolis stencil Dc_b = (J+ - J-) c_b; partial sums of
+//       the force -Re(c^dag u), the torque Re(c^dag D w) = -Re((Dc)^dag w) and (stage 0)
+//       Re(c^dag w);
 //   P4  derivative assembly da/dt = -i exp(iEt) w + (dPhi/dt/2) exp(iEt) Dc   (Eq. 5, using
 //       that Coriolis partners share the level energy), RK4 accumulation and next stage input;
+//       the step update a + (dt/6) acc is compensated (two-sum), its rounding error carried
+//       into the next step's accumulator;
 //   C   one lane per trajectory: FP64 classical stage update (Eqs. 7-10), FP64 bookkeeping of
 //       norm, total energy and P_Phi + <J_y>, termination, and refill of the slot from the
 //       device work queue (trajectories of uneven length share a CTA).
@@ -17,20 +21,18 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "internal.h"
 
 namespace mqct {
 
-constexpr int kBThreads = 512;
-constexpr int kEptMax = 16;  // elements (row, column) owned by one thread
+constexpr int kUpt = 4;  // (row, 4-column) units per thread
 
 enum { SLOT_IDLE = 0, SLOT_ACTIVE = 1, SLOT_FINAL = 2, SLOT_WAIT = 3 };
 
 struct Slot {
     double q[4], qs[4], lacc[4];
-    double dt, r_end, e0, j0, ndev, edev, jdev, x, phidot;
+    double dt, r_end, e0, j0, ndev, edev, jdev, x, phidot, inv_mu;
     int kint, status, steps, max_steps, traj, state, s0;
 };
 
@@ -46,20 +48,32 @@ __device__ __forceinline__ float2 phase_of(double e, double t)
     return make_float2(c, -s);
 }
 
-// slot thread: claim the next valid trajectory for slot b (FP64 initial conditions)
+__device__ __forceinline__ void locate_slot(const DevSys &S, Slot &sl)
+{
+    const double R = sl.qs[0];
+    int k = (int)floor((R - S.r_min) * S.inv_h);
+    k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
+    sl.kint = k;
+    sl.x = R - (S.r_min + k * S.h);
+    const double ir = 1.0 / R;
+    sl.phidot = sl.qs[3] * sl.inv_mu * ir * ir;
+    if (R < S.r_min) sl.status |= MQCT_TRAJ_TABLE_RANGE;
+}
+
+// slot lane: claim the next valid trajectory (FP64 initial conditions)
 __device__ void claim(const BatchArgs &a, const DevSys &S, Slot &sl)
 {
     for (;;) {
-        int item = atomicAdd(a.queue, 1);
+        const int item = atomicAdd(a.queue, 1);
         if (item >= a.n) {
             sl.state = SLOT_IDLE;
             return;
         }
         const int t = a.order ? a.order[item] : item;
         const mqct_traj tr = a.trajs[t];
-        bool ok = tr.system_idx == a.sys_idx && tr.dt > 0.0 && tr.e_coll > 0.0 && tr.b >= 0.0 && tr.r0 > 0.0 &&
-                  tr.b < tr.r0 && isfinite(tr.r_end) && tr.max_steps >= 0 && tr.init_state >= 0 &&
-                  tr.init_state < S.n;
+        const bool ok = tr.system_idx == a.sys_idx && tr.dt > 0.0 && tr.e_coll > 0.0 && tr.b >= 0.0 && tr.r0 > 0.0 &&
+                        tr.b < tr.r0 && isfinite(tr.r_end) && tr.max_steps >= 0 && tr.init_state >= 0 &&
+                        tr.init_state < S.n;
         if (!ok) {
             if (a.diag) {
                 mqct_diag d = {0, MQCT_TRAJ_INVALID, 0.0, 0.0, 0.0, 0.0};
@@ -82,6 +96,7 @@ __device__ void claim(const BatchArgs &a, const DevSys &S, Slot &sl)
         for (int i = 0; i < 4; ++i) sl.qs[i] = sl.q[i];
         sl.dt = tr.dt; sl.r_end = tr.r_end; sl.max_steps = tr.max_steps;
         sl.ndev = sl.edev = sl.jdev = 0.0;
+        sl.inv_mu = 1.0 / S.mu;
         sl.status = 0; sl.steps = 0; sl.traj = t; sl.s0 = s0;
         sl.state = SLOT_WAIT;
         sl.kint = k; sl.x = x; sl.phidot = 0.0;
@@ -89,28 +104,43 @@ __device__ void claim(const BatchArgs &a, const DevSys &S, Slot &sl)
     }
 }
 
-__device__ __forceinline__ void locate_slot(const DevSys &S, Slot &sl)
+struct F4x2 {  // four complex FP32 values (one unit row of four columns)
+    float2 v[4];
+};
+
+__device__ __forceinline__ F4x2 ld4(const float2 *p)
 {
-    const double R = sl.qs[0];
-    int k = (int)floor((R - S.r_min) * S.inv_h);
-    k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
-    sl.kint = k;
-    sl.x = R - (S.r_min + k * S.h);
-    sl.phidot = sl.qs[3] / (S.mu * R * R);
-    if (R < S.r_min) sl.status |= MQCT_TRAJ_TABLE_RANGE;
+    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    F4x2 r;
+    r.v[0] = make_float2(a.x, a.y); r.v[1] = make_float2(a.z, a.w);
+    r.v[2] = make_float2(b.x, b.y); r.v[3] = make_float2(b.z, b.w);
+    return r;
 }
 
-template <int B>
-__global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
+__device__ __forceinline__ void st4(float2 *p, const F4x2 &r)
 {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(r.v[0].x, r.v[0].y, r.v[1].x, r.v[1].y);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(r.v[2].x, r.v[2].y, r.v[3].x, r.v[3].y);
+}
+
+template <int B, int T>
+__global__ void __launch_bounds__(T, 512 / T) k_batched_f32(BatchArgs a)
+{
+    static_assert(B % 4 == 0 && B <= 32, "batch width");
+    constexpr int G4 = B / 4;  // four-column groups per row
+    constexpr int NW = T / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ DevSys S;
     __shared__ Slot sl[B];
-    __shared__ float vid[B], dvid[B];
+    __shared__ __align__(16) float vid[B];
+    __shared__ __align__(16) float dvid[B];
+    __shared__ __align__(16) float s_hp[B];
+    __shared__ __align__(16) float s_dt[B];
+    __shared__ int s_state[B], s_traj[B], s_s0[B];
+    __shared__ double red2[B][6];
     __shared__ int s_live;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = kBThreads / 32;
-    const int b = tid & (B - 1);
+    const int g = tid % G4;
     if (tid == 0) S = *a.sys;
     __syncthreads();
     const int n = S.n, NL = S.n_levels, L = S.L;
@@ -118,15 +148,24 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
     float2 *A = C + (size_t)n * B, *ACC = A + (size_t)n * B;
     float2 *PHa = ACC + (size_t)n * B, *PHb = PHa + (size_t)NL * B;
     float *vv = reinterpret_cast<float *>(PHb + (size_t)NL * B), *dvv = vv + (size_t)L * B;
-    double *red = reinterpret_cast<double *>(dvv + (size_t)L * B);  // [NW][B][6], 8-byte aligned (B >= 4)
-    const int ept = (n * B + kBThreads - 1) / kBThreads;
+    double *red = reinterpret_cast<double *>(dvv + (size_t)L * B);  // [NW][B][6]
+    const int upt = (n * G4 + T - 1) / T;
 
-    // v_lambda, v_lambda' at every slot's stage R (FP32 spline of the FP64-located interval)
+    // per-column views written by the slot lanes after every update
+    auto publish = [&](int b) {
+        const Slot &m = sl[b];
+        s_hp[b] = (float)(0.5 * m.phidot);
+        s_dt[b] = (float)m.dt;
+        s_state[b] = m.state;
+        s_traj[b] = m.traj;
+        s_s0[b] = m.s0;
+    };
+    // v_lambda, v_lambda' at every running slot's stage R (FP32 spline, FP64-located interval)
     auto terms = [&]() {
-        for (int i = tid; i < L * B; i += kBThreads) {
+        for (int i = tid; i < L * B; i += T) {
             const int l = i / B, bb = i % B;
             const Slot &s = sl[bb];
-            if (s.state == SLOT_IDLE || s.state == SLOT_WAIT) continue;
+            if (s.state == SLOT_IDLE || s.state == SLOT_WAIT) { vv[i] = 0.f; dvv[i] = 0.f; continue; }
             const float4 c = S.vcoef_f[(size_t)l * S.n_int + s.kint];
             const float x = (float)s.x;
             vv[i] = fmaf(x, fmaf(x, fmaf(x, c.w, c.z), c.y), c.x);
@@ -141,26 +180,29 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
             dvid[tid] = d0;
         }
     };
-    // column initialisation of slots waiting to start (A = e_s0, ACC = 0, C = A, phases 1)
-    auto init_columns = [&]() {
-        for (int k = 0; k < ept; ++k) {
-            const int e = tid + k * kBThreads, r = e / B;
-            if (r >= n || sl[b].state != SLOT_WAIT) continue;
-            const float2 v = make_float2(r == sl[b].s0 ? 1.0f : 0.0f, 0.0f);
-            A[e] = v; ACC[e] = make_float2(0.f, 0.f); C[e] = v;
-        }
-        for (int i = tid; i < NL * B; i += kBThreads)
-            if (sl[i % B].state == SLOT_WAIT) PHa[i] = make_float2(1.f, 0.f);
-    };
 
-    if (tid < B) claim(a, S, sl[tid]);
+    // ---- start: every slot claims a trajectory; columns e_s0, accumulators 0, phases 1
+    if (tid < B) {
+        claim(a, S, sl[tid]);
+        publish(tid);
+    }
     __syncthreads();
-    init_columns();
+    for (int i = tid; i < n * B; i += T) {
+        const int r = i / B, bb = i % B;
+        if (s_state[bb] != SLOT_WAIT) continue;
+        const float2 v = make_float2(r == s_s0[bb] ? 1.0f : 0.0f, 0.0f);
+        A[i] = v; ACC[i] = make_float2(0.f, 0.f); C[i] = v;
+    }
+    for (int i = tid; i < NL * B; i += T) PHa[i] = make_float2(1.f, 0.f);
     __syncthreads();
-    if (tid < B && sl[tid].state == SLOT_WAIT) {
-        sl[tid].state = sl[tid].max_steps > 0 ? SLOT_ACTIVE : SLOT_FINAL;
-        if (sl[tid].max_steps <= 0) sl[tid].status |= MQCT_TRAJ_MAX_STEPS;
-        locate_slot(S, sl[tid]);
+    if (tid < B) {
+        Slot &m = sl[tid];
+        if (m.state == SLOT_WAIT) {
+            m.state = m.max_steps > 0 ? SLOT_ACTIVE : SLOT_FINAL;
+            if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
+            locate_slot(S, m);
+        }
+        publish(tid);
     }
     if (tid == 0) s_live = 1;
     __syncthreads();
@@ -171,147 +213,197 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
         for (int s = 0; s < 4; ++s) {
             const float2 *PHc = (s == 0 || s == 3) ? PHa : PHb;
             const float2 *PHn = (s == 0 || s == 1) ? PHb : PHa;
-            // phases of the next distinct stage time for the running slots
             if (s == 0 || s == 2) {
                 float2 *dst = s == 0 ? PHb : PHa;
-                for (int i = tid; i < NL * B; i += kBThreads) {
+                for (int i = tid; i < NL * B; i += T) {
                     const Slot &q = sl[i % B];
                     if (q.state != SLOT_ACTIVE) continue;
                     const double t = q.steps * q.dt + (s == 0 ? 0.5 * q.dt : q.dt);
                     dst[i] = phase_of(S.lev_energy[i / B], t);
                 }
             }
-            // ---- P3: contraction, Coriolis stencil, partial sums
-            const int st_b = sl[b].state;
-            const bool live = st_b == SLOT_ACTIVE || st_b == SLOT_FINAL;
-            float2 wk[kEptMax], dck[kEptMax];
-            float fpart = 0.f, tpart = 0.f, vpart = 0.f;
+            // column states of my group
+            int cst[4];
+            bool any = false;
 #pragma unroll
-            for (int k = 0; k < kEptMax; ++k) {
-                wk[k] = make_float2(0.f, 0.f);
-                dck[k] = make_float2(0.f, 0.f);
-                const int e = tid + k * kBThreads, r = e / B;
-                if (k >= ept || r >= n || !live) continue;
-                const float2 c = C[e];
-                float2 w = make_float2(vid[b] * c.x, vid[b] * c.y);
-                float2 u = make_float2(dvid[b] * c.x, dvid[b] * c.y);
+            for (int j = 0; j < 4; ++j) {
+                cst[j] = s_state[4 * g + j];
+                any |= cst[j] == SLOT_ACTIVE || cst[j] == SLOT_FINAL;
+            }
+            // ---- P3
+            F4x2 kq[kUpt];  // derivative da/dt of the unit's four columns (Eq. 5)
+            float fp[4] = {0, 0, 0, 0}, tp[4] = {0, 0, 0, 0}, vp[4] = {0, 0, 0, 0};
+            float np_[4] = {0, 0, 0, 0}, ep[4] = {0, 0, 0, 0}, jp[4] = {0, 0, 0, 0};
+            const float4 hp4 = reinterpret_cast<const float4 *>(s_hp)[g];
+            const float hp[4] = {hp4.x, hp4.y, hp4.z, hp4.w};
+#pragma unroll
+            for (int k = 0; k < kUpt; ++k) {
+                const int r = (tid + k * T) / G4;
+                if (k >= upt || r >= n || !any) continue;
+                const F4x2 c = ld4(C + (size_t)r * B + 4 * g);
+                const float4 vi = reinterpret_cast<const float4 *>(vid)[g], dvi = reinterpret_cast<const float4 *>(dvid)[g];
+                const float vi_[4] = {vi.x, vi.y, vi.z, vi.w}, dvi_[4] = {dvi.x, dvi.y, dvi.z, dvi.w};
+                F4x2 w, u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    w.v[j] = make_float2(vi_[j] * c.v[j].x, vi_[j] * c.v[j].y);
+                    u.v[j] = make_float2(dvi_[j] * c.v[j].x, dvi_[j] * c.v[j].y);
+                }
                 for (int f = 0; f < S.n_f; ++f) {
                     const int *ptr = S.csr_ptr + (size_t)f * (n + 1);
-                    const int e0 = __ldg(ptr + r), e1 = __ldg(ptr + r + 1);
-                    float2 y = make_float2(0.f, 0.f);
-                    for (int q = e0; q < e1; ++q) {
-                        const float g = __ldg(S.csr_val + q);
-                        const float2 z = C[__ldg(S.csr_col + q) * B + b];
-                        y.x = fmaf(g, z.x, y.x);
-                        y.y = fmaf(g, z.y, y.y);
+                    const int q0 = __ldg(ptr + r), q1 = __ldg(ptr + r + 1);
+                    float2 y[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+                    for (int q = q0; q < q1; ++q) {
+                        const int col = __ldg(S.csr_col + q);
+                        const float gv = __ldg(S.csr_val + q);
+                        const F4x2 z = ld4(C + (size_t)col * B + 4 * g);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            y[j].x = fmaf(gv, z.v[j].x, y[j].x);
+                            y[j].y = fmaf(gv, z.v[j].y, y[j].y);
+                        }
                     }
                     const int l = S.f_term[f];
-                    const float v = vv[l * B + b], dv = dvv[l * B + b];
-                    w.x = fmaf(v, y.x, w.x); w.y = fmaf(v, y.y, w.y);
-                    u.x = fmaf(dv, y.x, u.x); u.y = fmaf(dv, y.y, u.y);
+                    const float4 v4 = reinterpret_cast<const float4 *>(vv + l * B)[g];
+                    const float4 d4 = reinterpret_cast<const float4 *>(dvv + l * B)[g];
+                    const float vl[4] = {v4.x, v4.y, v4.z, v4.w}, dl[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        w.v[j].x = fmaf(vl[j], y[j].x, w.v[j].x); w.v[j].y = fmaf(vl[j], y[j].y, w.v[j].y);
+                        u.v[j].x = fmaf(dl[j], y[j].x, u.v[j].x); u.v[j].y = fmaf(dl[j], y[j].y, u.v[j].y);
+                    }
                 }
-                const float au = (float)S.aup[r], ad = (float)S.adn[r];
-                const float2 cu = C[S.up[r] * B + b], cd = C[S.dn[r] * B + b];
-                const float2 dc = make_float2(ad * cd.x - au * cu.x, ad * cd.y - au * cu.y);
-                fpart -= c.x * u.x + c.y * u.y;
-                tpart -= dc.x * w.x + dc.y * w.y;
-                vpart += c.x * w.x + c.y * w.y;
-                wk[k] = w;
-                dck[k] = dc;
+                const float au = __ldg(S.aupf + r), ad = __ldg(S.adnf + r);
+                const F4x2 cu = ld4(C + (size_t)__ldg(S.up + r) * B + 4 * g);
+                const F4x2 cd = ld4(C + (size_t)__ldg(S.dn + r) * B + 4 * g);
+                const int lev = S.lev[r];
+                const F4x2 p = ld4(PHc + (size_t)lev * B + 4 * g);
+                F4x2 a0;
+                if (s == 0) a0 = ld4(A + (size_t)r * B + 4 * g);
+                const float elev = (float)S.lev_energy[lev];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 dc = make_float2(ad * cd.v[j].x - au * cu.v[j].x, ad * cd.v[j].y - au * cu.v[j].y);
+                    const float2 wj = w.v[j], pj = p.v[j];
+                    fp[j] -= c.v[j].x * u.v[j].x + c.v[j].y * u.v[j].y;
+                    tp[j] -= dc.x * wj.x + dc.y * wj.y;
+                    vp[j] += c.v[j].x * wj.x + c.v[j].y * wj.y;
+                    // conj(p) Dc = (J+ - J-) a at this stage (partners share the level energy)
+                    const float2 da = make_float2(pj.x * dc.x + pj.y * dc.y, pj.x * dc.y - pj.y * dc.x);
+                    kq[k].v[j].x = fmaf(hp[j], da.x, pj.x * wj.y - pj.y * wj.x);
+                    kq[k].v[j].y = fmaf(hp[j], da.y, -(pj.x * wj.x + pj.y * wj.y));
+                    if (s == 0) {
+                        const float2 aj = a0.v[j];
+                        const float pp = aj.x * aj.x + aj.y * aj.y;
+                        np_[j] += pp;
+                        ep[j] += elev * pp;
+                        jp[j] += aj.x * da.y - aj.y * da.x;
+                    }
+                }
             }
             __syncthreads();
-            // ---- P4: derivatives, RK4 accumulation, next stage input (own elements only)
-            const Slot &me = sl[b];
-            const float hp = 0.5f * (float)me.phidot;
-            const float dtf = (float)me.dt;
+            // ---- P4 (own units only)
+            const float4 dt4 = reinterpret_cast<const float4 *>(s_dt)[g];
+            const float dtj[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
             const float wgt = (s == 1 || s == 2) ? 2.0f : 1.0f;
-            const float bn = s == 2 ? dtf : 0.5f * dtf;
-            float npart = 0.f, epart = 0.f, jpart = 0.f;
 #pragma unroll
-            for (int k = 0; k < kEptMax; ++k) {
-                const int e = tid + k * kBThreads, r = e / B;
-                if (k >= ept || r >= n) continue;
-                if (st_b == SLOT_WAIT && s == 3) {
-                    const float2 v = make_float2(r == me.s0 ? 1.0f : 0.0f, 0.0f);
-                    A[e] = v; ACC[e] = make_float2(0.f, 0.f); C[e] = v;
-                    continue;
-                }
-                if (!live) continue;
+            for (int k = 0; k < kUpt; ++k) {
+                const int r = (tid + k * T) / G4;
+                if (k >= upt || r >= n) continue;
+                const size_t o = (size_t)r * B + 4 * g;
                 const int lev = S.lev[r];
-                const float2 p = PHc[lev * B + b], w = wk[k], dc = dck[k];
-                // conj(p) Dc = (J+ - J-) a at this stage (partners share the level energy)
-                const float2 da = make_float2(p.x * dc.x + p.y * dc.y, p.x * dc.y - p.y * dc.x);
-                float2 kk;
-                kk.x = fmaf(hp, da.x, p.x * w.y - p.y * w.x);
-                kk.y = fmaf(hp, da.y, -(p.x * w.x + p.y * w.y));
-                const float2 a0 = A[e];
-                if (s == 0) {
-                    const float pp = a0.x * a0.x + a0.y * a0.y;
-                    npart += pp;
-                    epart += (float)S.lev_energy[lev] * pp;
-                    jpart += a0.x * da.y - a0.y * da.x;
-                    if (st_b == SLOT_FINAL) {
-                        const size_t o = (size_t)me.traj * a.nmax + S.perm[r];
-                        if (a.pop) a.pop[o] = (double)pp;
-                        if (a.amp) { a.amp[2 * o] = a0.x; a.amp[2 * o + 1] = a0.y; }
+                F4x2 a0 = ld4(A + o), acc = ld4(ACC + o), cn = ld4(C + o);
+                const F4x2 pn = ld4(PHn + (size_t)lev * B + 4 * g);
+                bool wr_a = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int stj = cst[j];
+                    if (stj == SLOT_WAIT) {
+                        if (s == 3) {
+                            const float2 v = make_float2(r == s_s0[4 * g + j] ? 1.0f : 0.0f, 0.0f);
+                            a0.v[j] = v; acc.v[j] = make_float2(0.f, 0.f); cn.v[j] = v;
+                            wr_a = true;
+                        }
                         continue;
                     }
-                    // the accumulator enters the step holding the rounding error of the last update
-                    const float2 cmp = ACC[e];
-                    ACC[e] = make_float2(kk.x + cmp.x, kk.y + cmp.y);
-                } else {
-                    float2 acc = ACC[e];
-                    acc.x = fmaf(wgt, kk.x, acc.x);
-                    acc.y = fmaf(wgt, kk.y, acc.y);
-                    if (s == 3) {
-                        // compensated update a + (dt/6) acc (two-sum): in the interaction picture a
-                        // changes by tiny increments far from the collision, which a plain FP32 add
-                        // would round away; the error is carried to the next step's accumulator
-                        const float h6 = dtf / 6.0f, ih6 = 6.0f / dtf;
-                        const float ix = h6 * acc.x, iy = h6 * acc.y;
-                        const float sx = __fadd_rn(a0.x, ix), sy = __fadd_rn(a0.y, iy);
-                        const float bx = __fsub_rn(sx, a0.x), by = __fsub_rn(sy, a0.y);
-                        const float ex = __fadd_rn(__fsub_rn(a0.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
-                        const float ey = __fadd_rn(__fsub_rn(a0.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
-                        const float2 an = make_float2(sx, sy);
-                        A[e] = an;
-                        ACC[e] = make_float2(ex * ih6, ey * ih6);
-                        const float2 pn = PHn[lev * B + b];
-                        C[e] = make_float2(pn.x * an.x - pn.y * an.y, pn.x * an.y + pn.y * an.x);
-                        continue;
+                    if (stj != SLOT_ACTIVE && stj != SLOT_FINAL) continue;
+                    const float2 kk = kq[k].v[j];
+                    const float2 aj = a0.v[j];
+                    if (s == 0) {
+                        if (stj == SLOT_FINAL) {
+                            const float pp = aj.x * aj.x + aj.y * aj.y;
+                            const size_t oo = (size_t)s_traj[4 * g + j] * a.nmax + S.perm[r];
+                            if (a.pop) a.pop[oo] = (double)pp;
+                            if (a.amp) { a.amp[2 * oo] = aj.x; a.amp[2 * oo + 1] = aj.y; }
+                            continue;
+                        }
+                        // the accumulator enters the step holding the rounding error of the last update
+                        acc.v[j] = make_float2(kk.x + acc.v[j].x, kk.y + acc.v[j].y);
+                    } else {
+                        acc.v[j].x = fmaf(wgt, kk.x, acc.v[j].x);
+                        acc.v[j].y = fmaf(wgt, kk.y, acc.v[j].y);
+                        if (s == 3) {
+                            // compensated a + (dt/6) acc (two-sum): far from the collision the
+                            // interaction-picture amplitudes change by increments a plain FP32 add
+                            // would round away; the error is carried to the next accumulator
+                            const float h6 = dtj[j] * (1.0f / 6.0f), ih6 = 6.0f / dtj[j];
+                            const float ix = h6 * acc.v[j].x, iy = h6 * acc.v[j].y;
+                            const float sx = __fadd_rn(aj.x, ix), sy = __fadd_rn(aj.y, iy);
+                            const float bx = __fsub_rn(sx, aj.x), by = __fsub_rn(sy, aj.y);
+                            const float ex = __fadd_rn(__fsub_rn(aj.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
+                            const float ey = __fadd_rn(__fsub_rn(aj.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
+                            a0.v[j] = make_float2(sx, sy);
+                            acc.v[j] = make_float2(ex * ih6, ey * ih6);
+                            const float2 q = pn.v[j];
+                            cn.v[j] = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
+                            wr_a = true;
+                            continue;
+                        }
                     }
-                    ACC[e] = acc;
+                    const float bn = s == 2 ? dtj[j] : 0.5f * dtj[j];
+                    const float2 yn = make_float2(fmaf(bn, kk.x, aj.x), fmaf(bn, kk.y, aj.y));
+                    const float2 q = pn.v[j];
+                    cn.v[j] = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
                 }
-                const float2 yn = make_float2(fmaf(bn, kk.x, a0.x), fmaf(bn, kk.y, a0.y));
-                const float2 pn = PHn[lev * B + b];
-                C[e] = make_float2(pn.x * yn.x - pn.y * yn.y, pn.x * yn.y + pn.y * yn.x);
+                if (wr_a) st4(A + o, a0);
+                st4(ACC + o, acc);
+                st4(C + o, cn);
             }
-            // per-column reduction: lanes of one column inside the warp, then warps in FP64
-            float part[6] = {fpart, tpart, vpart, npart, epart, jpart};
+            // ---- per-column reduction: lanes of one group inside the warp, then warps in FP64
+            const int nq = s == 0 ? 6 : 2;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                float v = part[q];
-                for (int o = B; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                part[q] = v;
+            for (int j = 0; j < 4; ++j) {
+                float part[6] = {fp[j], tp[j], vp[j], np_[j], ep[j], jp[j]};
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    if (q >= nq) break;
+                    float v = part[q];
+#pragma unroll
+                    for (int off = G4; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                    part[q] = v;
+                }
+                if (lane < G4)
+                    for (int q = 0; q < nq; ++q) red[((size_t)warp * B + 4 * lane + j) * 6 + q] = (double)part[q];
             }
-            if (lane < B) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) red[((size_t)warp * B + lane) * 6 + q] = (double)part[q];
+            __syncthreads();
+            if (tid < B * 6) {
+                const int bb = tid / 6, q = tid % 6;
+                double sum = 0.0;
+                if (q < nq)
+                    for (int w2 = 0; w2 < NW; ++w2) sum += red[((size_t)w2 * B + bb) * 6 + q];
+                red2[bb][q] = sum;
             }
             __syncthreads();
             // ---- C: one lane per slot, FP64
             if (tid < B) {
                 Slot &m = sl[tid];
-                double F = 0, T = 0, V = 0, NR = 0, ER = 0, JY = 0;
-                for (int w2 = 0; w2 < NW; ++w2) {
-                    const double *r6 = red + ((size_t)w2 * B + tid) * 6;
-                    F += r6[0]; T += r6[1]; V += r6[2]; NR += r6[3]; ER += r6[4]; JY += r6[5];
-                }
-                const double mu = S.mu;
+                const double F = red2[tid][0], Tq = red2[tid][1];
                 if (m.state == SLOT_ACTIVE || m.state == SLOT_FINAL) {
-                    const double R = m.qs[0], PR = m.qs[1], PP = m.qs[3];
+                    const double R = m.qs[0], PR = m.qs[1], PP = m.qs[3], imu = m.inv_mu;
+                    const double ir = 1.0 / R, ir2 = ir * ir;
                     if (s == 0) {
-                        const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + ER + V;
+                        const double V = red2[tid][2], NR = red2[tid][3], ER = red2[tid][4], JY = red2[tid][5];
+                        const double et = 0.5 * imu * (PR * PR + PP * PP * ir2) + ER + V;
                         const double jt = PP + 0.5 * JY;
                         if (m.steps == 0) { m.e0 = et; m.j0 = jt; }
                         m.ndev = fmax(m.ndev, fabs(NR - 1.0));
@@ -330,7 +422,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
                             claim(a, S, m);
                         }
                     } else {
-                        const double l4[4] = {PR / mu, F + PP * PP / (mu * R * R * R), m.phidot, T};
+                        const double l4[4] = {PR * imu, F + PP * PP * imu * ir2 * ir, m.phidot, Tq};
                         const double wg = (s == 1 || s == 2) ? 2.0 : 1.0;
                         for (int i = 0; i < 4; ++i) m.lacc[i] = s == 0 ? l4[i] : fma(wg, l4[i], m.lacc[i]);
                         if (s < 3) {
@@ -351,57 +443,68 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batched_f32(BatchArgs a)
                     if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
                     locate_slot(S, m);
                 }
+                publish(tid);
             }
             __syncthreads();
-            if (tid == 0 && s == 3) {
-                int live_n = 0;
-                for (int q = 0; q < B; ++q) live_n += sl[q].state != SLOT_IDLE;
-                s_live = live_n;
-            }
-            // phases of slots that start a trajectory at the next stage (t = 0); their columns were
-            // initialised in P4 of this stage
-            if (s == 3)
-                for (int i = tid; i < NL * B; i += kBThreads) {
+            if (s == 3) {
+                if (tid == 0) {
+                    int live_n = 0;
+                    for (int q = 0; q < B; ++q) live_n += sl[q].state != SLOT_IDLE;
+                    s_live = live_n;
+                }
+                // slots that start a trajectory at the next stage: phases of t = 0 (their columns
+                // were initialised in P4 of this stage)
+                for (int i = tid; i < NL * B; i += T) {
                     const Slot &q = sl[i % B];
                     if ((q.state == SLOT_ACTIVE || q.state == SLOT_FINAL) && q.steps == 0) PHa[i] = make_float2(1.f, 0.f);
                 }
+            }
             terms();
             __syncthreads();
         }
     }
 }
 
-template <int B>
+template <int B, int T>
 size_t batched_smem(const DevSys &h)
 {
     return sizeof(float2) * (3 * (size_t)h.n * B + 2 * (size_t)h.n_levels * B) + sizeof(float) * 2 * (size_t)h.L * B +
-           sizeof(double) * (kBThreads / 32) * B * 6;
+           sizeof(double) * (T / 32) * B * 6;
 }
 
-template <int B>
+template <int B, int T>
+bool batched_fits(const DevSys &h, size_t cap)
+{
+    return (size_t)h.n * (B / 4) <= (size_t)kUpt * T && batched_smem<B, T>(h) <= cap;
+}
+
+template <int B, int T>
 cudaError_t launch_batched(const BatchArgs &a, const DevSys &h, int sms, cudaStream_t st)
 {
-    const size_t smem = batched_smem<B>(h);
-    cudaError_t e = cudaFuncSetAttribute(k_batched_f32<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = batched_smem<B, T>(h);
+    cudaError_t e = cudaFuncSetAttribute(k_batched_f32<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_f32<B>, kBThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_f32<B, T>, T, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = std::min(sms * per_sm, (a.n + B - 1) / B);
     grid = std::max(grid, 1);
-    k_batched_f32<B><<<grid, kBThreads, smem, st>>>(a);
+    k_batched_f32<B, T><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// pick the widest batch whose shared-memory block and per-thread element count fit
+// Batch shape: 256-thread CTAs, two per SM, when a CTA's block fits in half the shared
+// memory; otherwise 512-thread CTAs, one per SM.  Widest batch first.
 int batched_width(const DevSys &h)
 {
-    const size_t cap = 220 * 1024;
-    if ((size_t)h.n * 32 <= (size_t)kEptMax * kBThreads && batched_smem<32>(h) <= cap) return 32;
-    if ((size_t)h.n * 16 <= (size_t)kEptMax * kBThreads && batched_smem<16>(h) <= cap) return 16;
-    if ((size_t)h.n * 8 <= (size_t)kEptMax * kBThreads && batched_smem<8>(h) <= cap) return 8;
-    if ((size_t)h.n * 4 <= (size_t)kEptMax * kBThreads && batched_smem<4>(h) <= cap) return 4;
+    const size_t half = 110 * 1024, full = 220 * 1024;
+    if (batched_fits<32, 256>(h, half)) return 32 * 1000 + 256;
+    if (batched_fits<16, 256>(h, half)) return 16 * 1000 + 256;
+    if (batched_fits<8, 256>(h, half)) return 8 * 1000 + 256;
+    if (batched_fits<16, 512>(h, full)) return 16 * 1000 + 512;
+    if (batched_fits<8, 512>(h, full)) return 8 * 1000 + 512;
+    if (batched_fits<4, 512>(h, full)) return 4 * 1000 + 512;
     return 0;
 }
 
@@ -410,13 +513,15 @@ cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, in
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int B = batched_width(h);
-    if (width) *width = B;
-    switch (B) {
-        case 32: return launch_batched<32>(a, h, sms, st);
-        case 16: return launch_batched<16>(a, h, sms, st);
-        case 8: return launch_batched<8>(a, h, sms, st);
-        case 4: return launch_batched<4>(a, h, sms, st);
+    const int shape = batched_width(h);
+    if (width) *width = shape / 1000;
+    switch (shape) {
+        case 32256: return launch_batched<32, 256>(a, h, sms, st);
+        case 16256: return launch_batched<16, 256>(a, h, sms, st);
+        case 8256: return launch_batched<8, 256>(a, h, sms, st);
+        case 16512: return launch_batched<16, 512>(a, h, sms, st);
+        case 8512: return launch_batched<8, 512>(a, h, sms, st);
+        case 4512: return launch_batched<4, 512>(a, h, sms, st);
         default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -62,6 +62,7 @@ struct DevSys {
     const int *csr_col;
     const float *csr_val;
     const float4 *vcoef_f;     // [L][n_int]
+    const float *aupf, *adnf;  // [n] FP32 ladder factors
     int max_row_nnz;           // max over rows of the summed CSR row lengths
 };
 

@@ -428,6 +428,9 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
             std::vector<float4> vf(vcoef.size());
             for (size_t i = 0; i < vcoef.size(); ++i)
                 vf[i] = make_float4((float)vcoef[i].x, (float)vcoef[i].y, (float)vcoef[i].z, (float)vcoef[i].w);
+            std::vector<float> aupf(aup.begin(), aup.end()), adnf(adn.begin(), adn.end());
+            up_(aupf, &D.aupf);
+            up_(adnf, &D.adnf);
             up_(cptr, &D.csr_ptr);
             up_(ccol, &D.csr_col);
             up_(cval, &D.csr_val);
