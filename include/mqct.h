@@ -78,6 +78,7 @@ typedef enum { MQCT_FP64 = 0, MQCT_FP32 = 1, MQCT_BF16X3 = 2 } mqct_precision;
 #define MQCT_TRAJ_NONFINITE 4   /* a non-finite value appeared; the trajectory was stopped  */
 #define MQCT_TRAJ_TIMEOUT 8     /* a bounded device wait ran out while running it           */
 #define MQCT_TRAJ_INVALID 16    /* device-resident trajectory failed validation; not run    */
+#define MQCT_TRAJ_CKPT 32       /* adjoint: the forward pass outran its checkpoint storage  */
 
 /* Description of one atom + rotor system.  All pointers are HOST pointers, read and
  * copied during mqct_create_system only. */

@@ -288,6 +288,59 @@ def sigma_weights(ts: "_inputs.TrajSet", status=None) -> np.ndarray:
     return w
 
 
+def adjoint(system: System, trajs: np.ndarray, weight, group, n_groups: int, dL_dsigma, ckpt: int = 64,
+            stream=None) -> np.ndarray:
+    """dL/dtheta for L = sum dL_dsigma[g][l] sigma[g][l] by the discrete adjoint of the RK4 map
+    (mqct_adjoint); theta are the parameters whose tables the system was built with."""
+    weight = np.ascontiguousarray(weight, np.float64)
+    group = np.ascontiguousarray(group, np.int32)
+    dls = np.ascontiguousarray(dL_dsigma, np.float64)
+    out = np.zeros(system.n_params)
+    _check(lib().mqct_adjoint(system.handle, _ptr(trajs), trajs.shape[0], _ptr(weight), _ptr(group), n_groups,
+                              _ptr(dls), int(ckpt), _ptr(out), _stream(stream)), allow=(ERR_TRAJ,))
+    return out
+
+
+def _diatom_with(p, theta):
+    """Copy of a DiatomParams with theta = (A_0..A_{L-1}, beta_0..beta_{L-1})."""
+    import copy
+
+    q = copy.copy(p)
+    L = p.n_terms
+    th = np.asarray(theta, np.float64)
+    q.A = th[:L].copy()
+    q.beta = th[L:2 * L].copy()
+    return q
+
+
+def cross_section_fn():
+    """torch.autograd.Function computing the cross sections of a diatom workload as a function
+    of theta = (A, beta); backward runs the adjoint kernel (FP64).
+
+        sigma = CrossSection.apply(theta, params, trajset, ckpt)
+    theta: float64 CPU tensor [2L]; returns sigma [n_groups][n_levels] (float64, CPU)."""
+    import torch
+
+    class CrossSection(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, params, ts, ckpt=64):
+            p = _diatom_with(params, theta.detach().cpu().numpy())
+            sys_ = System.diatom(p, path="factorised", precision="fp64", with_params=True)
+            tr = make_trajs(ts, sys_)
+            pop, _, diag = propagate(sys_, tr, device=False)
+            w = sigma_weights(ts, diag["status"])
+            sig = cross_sections(sys_, pop, w, ts.group, ts.n_groups)
+            ctx.sys, ctx.tr, ctx.w, ctx.ts, ctx.ckpt = sys_, tr, w, ts, ckpt
+            return torch.from_numpy(sig)
+
+        @staticmethod
+        def backward(ctx, g):
+            d = adjoint(ctx.sys, ctx.tr, ctx.w, ctx.ts.group, ctx.ts.n_groups, g.detach().cpu().numpy(), ctx.ckpt)
+            return torch.from_numpy(d), None, None, None
+
+    return CrossSection
+
+
 def fma_rate(kind: str = "fp64", stream=None) -> float:
     """Measured FMA throughput of the current GPU in GFLOP/s ("fp64" or "fp32")."""
     out = C.c_double()

@@ -375,8 +375,10 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         up_(T23, &D.T23);
         S.info.table_nnz = nnz;
         S.info.table_bytes = (int64_t)nnz_pad * n_int * 32;
-    } else {
-        // identity terms are applied directly; others get one sliced-ELL matrix each
+    }
+    if (d->path == MQCT_PATH_FACTORISED || P > 0) {
+        // identity terms are applied directly; others get one sliced-ELL matrix each (the
+        // adjoint always works on the per-term form, so it is built whenever P > 0)
         std::vector<int> fterm, foff, fcols;
         std::vector<double> fval;
         unsigned long long idm = 0;
