@@ -38,8 +38,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--path", default="plain", choices=["plain", "factorised"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--path", default="factorised", choices=["plain", "factorised"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain-FP64 comparison run (throughput and max |dP| against it)")
+    ap.add_argument("--adjoint", type=int, default=0,
+                    help="also time the adjoint on this many trajectories of the gradient workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-traj", type=int, default=0,
@@ -278,6 +282,48 @@ def gpu_arm(args):
         e2e = {"value": traj_steps * ws / (e_ms_step * 1e-3), "unit": "traj-steps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms_step}
 
+    # the same batch through the plain FP64 path: its throughput, and the largest population
+    # difference of the measured path against it over every trajectory ("same error")
+    compare = None
+    if not args.no_compare and not (args.path == "plain" and args.precision == "fp64"):
+        pop_m = pop.cpu().numpy()
+        s64 = api.System.diatom(p, path="plain", precision="fp64")
+        flush.zero_()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        pop64, _, d64 = api.propagate(s64, trd, device=True, stream=stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a_.elapsed_time(b_)
+        d64 = api.diag_to_numpy(d64)
+        same = d64["steps"] == dg["steps"]
+        dp = np.abs(pop_m - pop64.cpu().numpy()[:, :pop_m.shape[1]])
+        compare = {"path": "plain", "precision": "fp64", "value": float(d64["steps"].sum()) * ws / (ms64 * 1e-3),
+                   "unit": "traj-steps/s", "ms": ms64, "timed_runs": 1,
+                   "max_abs_dP_vs_fp64": float(dp.max()), "max_abs_dP_same_steps": float(dp[same].max()),
+                   "trajectories_same_steps": int(same.sum()),
+                   "speedup": value / (float(d64["steps"].sum()) * ws / (ms64 * 1e-3))}
+        del s64
+
+    adj = None
+    if args.adjoint:
+        pa, ta = W.workload5()
+        ta = ta.subset(np.linspace(0, ta.n - 1, args.adjoint).astype(int))
+        sa = api.System.diatom(pa, path="factorised", precision="fp64", with_params=True)
+        tra = api.make_trajs(ta, sa)
+        _, _, dga = api.propagate(sa, tra, device=False)
+        wa = api.sigma_weights(ta, dga["status"])
+        dls = np.ones((ta.n_groups, sa.n_levels))
+        api.adjoint(sa, tra, wa, ta.group, ta.n_groups, dls, ckpt=64)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grad = api.adjoint(sa, tra, wa, ta.group, ta.n_groups, dls, ckpt=64)
+        t_adj = time.perf_counter() - t0
+        adj = {"workload": f"{ta.n} of the 1024 trajectories of the N=441, E=1000 cm^-1 gradient workload",
+               "params": int(sa.n_params), "ckpt": 64, "seconds": t_adj,
+               "traj_steps_per_s": float(dga["steps"].sum()) / t_adj,
+               "gradients_per_s": 1.0 / t_adj, "dL_dtheta_norm": float(np.linalg.norm(grad))}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         sub = oracle_sample(p, ts, 16)
@@ -298,7 +344,7 @@ def gpu_arm(args):
                    "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,
                    "l2": "flushed (256 MB write) before every timed step", "seed": W.DEFAULT_SEED},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step * args.steps, "comparison": compare, "adjoint": adj,
     }))
 
 
