@@ -30,6 +30,7 @@ from paper_2312_02322_gb300 import inputs as W  # noqa: E402
 
 METRIC = "MQCT trajectory-steps/s at N=441/1600, batched mixed vs plain FP64, same error"
 WORKLOAD = "diatom j<=20 (N=441), 3072 trajectories: E in {100,300,1000,3000} cm^-1 x j' in {0,1,2} x 256 b on 0-15 bohr"
+WORKLOAD_1600 = "diatom j<=39 (N=1600), 768 trajectories: E in {1000,3000} cm^-1 x j' in {0,1,2} x 128 b on 0-15 bohr"
 
 
 def parse():
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-traj", type=int, default=0,
                     help="run a seeded subset of this many trajectories (profiling of a small case)")
+    ap.add_argument("--workload", default="n441", choices=["n441", "n1600"],
+                    help="n441: the 3072-trajectory N = 441 workload; n1600: 768 trajectories with N = 1600")
     ap.add_argument("--energy", type=float, default=0.0,
                     help="keep only the trajectories at this collision energy (cm^-1)")
     return ap.parse_args()
@@ -186,8 +189,8 @@ def gpu_arm(args):
     build.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    p, ts = W.workload2()
-    workload = WORKLOAD
+    p, ts = W.workload2() if args.workload == "n441" else W.workload2_n1600()
+    workload = WORKLOAD if args.workload == "n441" else WORKLOAD_1600
     if args.energy:
         ts = ts.subset(np.flatnonzero(np.isclose(ts.e_coll, float(W.cm(args.energy)))))
         workload = f"E = {args.energy} cm^-1 part of: {WORKLOAD}"

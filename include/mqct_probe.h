@@ -20,6 +20,14 @@ extern "C" {
 
 mqct_status mqct_probe_fma_rate(int32_t kind, double *gflops, void *cuda_stream);
 
+/* Check of the library's 5th-generation tensor-core path (tcgen05 MMA, tensor-memory
+ * accumulator, shared-memory operand descriptors): D = A * B^T on one CTA.
+ *   a [128][k] BF16, b [n][k] BF16, d [128][n] FP32 -- all DEVICE pointers, row-major;
+ *   16 <= n, k <= 256, multiples of 16.  Synchronises `cuda_stream`.
+ * Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_TIMEOUT (the bounded completion wait ran out),
+ * MQCT_ERR_CUDA.  No counterpart in the paper (a building-block check). */
+mqct_status mqct_probe_tc_gemm(int32_t n, int32_t k, const void *a, const void *b, float *d, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

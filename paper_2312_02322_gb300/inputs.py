@@ -143,6 +143,13 @@ def workload2():
             regular_set([100.0, 300.0, 1000.0, 3000.0], [0, 1, 2], n_b=256, b_max=15.0))
 
 
+def workload2_n1600():
+    """N = 1600 (j <= 39): E in {1000, 3000} cm^-1, j' in {0, 1, 2}, 128 midpoint b on 0-15 bohr
+    per (E, j'): 768 trajectories; 400-point grid."""
+    return (diatom_pes_params(jmax=39, n_grid=400),
+            regular_set([1000.0, 3000.0], [0, 1, 2], n_b=128, b_max=15.0))
+
+
 def workload5():
     """N = 441, E = 1000 cm^-1, j' = 0, 1024 midpoint b on 0-15 bohr (gradient workload)."""
     return diatom_pes_params(jmax=20, n_grid=400), regular_set([1000.0], [0], n_b=1024, b_max=15.0)

@@ -143,6 +143,27 @@ def test_mixed_workload2_sampled_at_full_size(mq, ora):
     compare(pop[pick], sub, pop_o, res_o, tol=TOL_MIXED)
 
 
+def test_n1600_sampled(mq, ora):
+    """N = 1600 (j <= 39): 24 trajectories of the N = 1600 workload through the plain FP64 and
+    the batched mixed paths; two of them recomputed by the oracle."""
+    import torch
+
+    p, ts = W.workload2_n1600()
+    rng = np.random.default_rng(9)
+    cand = np.flatnonzero(ts.e_coll == ts.e_coll.max())
+    sub = ts.subset(np.sort(rng.choice(cand, 24, replace=False)))
+    s64 = mq.System.diatom(p, path="plain")
+    s32 = mq.System.diatom(p, path="factorised", precision="fp32")
+    p64, d64 = gpu_run(mq, s64, sub, device=True)
+    p32, d32 = gpu_run(mq, s32, sub, device=True)
+    assert np.all(d64["status"] == 0) and np.all(d32["status"] == 0)
+    assert np.max(np.abs(p32 - p64)) < TOL_MIXED
+    pick = [0, 13]
+    pop_o, res_o = oracle_run(ora, oracle_system(ora, p), sub.subset(pick))
+    compare(p64[pick], {k: d64[k][pick] for k in d64.dtype.names}, pop_o, res_o)
+    compare(p32[pick], {k: d32[k][pick] for k in d32.dtype.names}, pop_o, res_o, tol=TOL_MIXED)
+
+
 def test_paths_agree(mq):
     """PLAIN (spline of M) and FACTORISED (sum of v_l G^l) are the same function: agree to 1e-12."""
     p, ts = W.small_workload(jmax=5, n_b=5, energies=(800.0,), init_js=(1, 2), b_max=9.0, n_grid=150)
