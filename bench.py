@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--path", default="factorised", choices=["plain", "factorised"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16x3"])
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP64 comparison run (throughput and max |dP| against it)")
     ap.add_argument("--adjoint", type=int, default=0,
@@ -260,7 +260,22 @@ def gpu_arm(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = peaks.get("hbm_gbs")
     except Exception:
-        hbm = None
+        peaks, hbm = {}, None
+    if args.precision == "bf16x3":
+        # executed tensor work: per stage, per row tile and 64-slot tile, (w, u) x stored terms x
+        # 3 split products x 8 K steps of a 128 x 128 x 16 MMA; time = the whole propagate call
+        # (contraction, element update and slot kernels), so the fraction is a lower bound
+        n_f = sum(1 for l in range(p.n_terms) if l > 0)
+        tiles = int(np.ceil(n / 128.0))
+        exec_stage = tiles * n_f * 2 * 3 * 8 * (2.0 * 128 * 128 * 16) / 64.0
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        ach = exec_stage * stages / (k_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                    "traffic": None, "kernel": "k_tc_contract (timed with the whole propagate call)",
+                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
+                    "executed_flops_per_traj_stage": exec_stage, "useful_flops_per_traj_stage": flops_stage,
+                    "useful_over_executed": flops_stage / exec_stage, "traj_stages_per_launch": stages,
+                    "kernel_ms": k_ms}
     if bytes_stage and hbm:
         gbs = bytes_stage * stages / (k_ms * 1e-3) / 1e9
         roofline["hbm_view"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
@@ -342,7 +357,8 @@ def gpu_arm(args):
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": workload, "path": args.path, "precision": args.precision, "n_states": n,
                    "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,
                    "l2": "flushed (256 MB write) before every timed step", "seed": W.DEFAULT_SEED},

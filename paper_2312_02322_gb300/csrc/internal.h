@@ -64,6 +64,12 @@ struct DevSys {
     const float4 *vcoef_f;     // [L][n_int]
     const float *aupf, *adnf;  // [n] FP32 ladder factors
     int max_row_nnz;           // max over rows of the summed CSR row lengths
+    // Tensor-core path (BF16X3): m-blocks packed into row tiles of <= 128 rows; for every
+    // stored term f and tile t the 128 x 128 block-diagonal G^f tile as BF16 hi and lo parts in
+    // the canonical K-major layout of the MMA A operand (tile-major: [f][t][hi,lo][16384]).
+    int n_tiles;
+    const int *tile_r0;        // [n_tiles + 1] first row of each tile
+    const uint16_t *g_tiles;   // [n_f][n_tiles][2][128 * 128]
 };
 
 struct System {
@@ -112,6 +118,9 @@ struct BatchArgs {
     int sys_idx;  // trajectories must name this system
 };
 cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width);
+// stage-synchronous tensor-core launch sequence (tc_batched.cu); allocates its scratch with
+// stream-ordered allocation and synchronises `st` between chunks of steps
+mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st);
 int batched_width(const DevSys &h);
 
 mqct_status fail(mqct_status st, const std::string &msg);

@@ -440,7 +440,7 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
     }
     if (prec != MQCT_FP64) {
         if (n_systems != 1) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: mixed precision takes one system per call");
-        if (batched_width(systems[0]->s.h) == 0)
+        if (prec == MQCT_FP32 && batched_width(systems[0]->s.h) == 0)
             return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: basis too large for the batched kernel");
     }
     if (n == 0) return MQCT_OK;
@@ -511,7 +511,12 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
         BatchArgs ba;
         ba.sys = systems[0]->s.d; ba.trajs = dtr; ba.order = order; ba.n = n; ba.queue = queue;
         ba.pop = dpop; ba.amp = damp; ba.diag = ddiag; ba.nmax = nmax; ba.sys_idx = 0;
-        if ((e = run_batched(ba, systems[0]->s.h, st, nullptr)) != cudaSuccess) return cuda_fail(e, "batched launch");
+        if (prec == MQCT_BF16X3) {
+            const mqct_status ts = run_tc_batched(ba, systems[0]->s.h, st);
+            if (ts != MQCT_OK) return ts;
+        } else if ((e = run_batched(ba, systems[0]->s.h, st, nullptr)) != cudaSuccess) {
+            return cuda_fail(e, "batched launch");
+        }
     } else {
     // launch shape: one warp per 32-row slice (balanced), persistent grid
     const int maxw = kPropThreads / 32;

@@ -165,7 +165,6 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     if (d->path != MQCT_PATH_PLAIN && d->path != MQCT_PATH_FACTORISED) return fail(MQCT_ERR_INVALID_ARG, "unknown path");
     if (d->precision != MQCT_FP64 && d->precision != MQCT_FP32 && d->precision != MQCT_BF16X3)
         return fail(MQCT_ERR_INVALID_ARG, "unknown precision");
-    if (d->precision == MQCT_BF16X3) return fail(MQCT_ERR_UNSUPPORTED, "BF16X3 precision is not available in this build");
     if (d->precision != MQCT_FP64 && d->path != MQCT_PATH_FACTORISED)
         return fail(MQCT_ERR_UNSUPPORTED, "mixed precision runs on the factorised (batched) path only");
     if (d->flags != 0) return fail(MQCT_ERR_INVALID_ARG, "flags must be 0");
@@ -438,6 +437,56 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
             up_(cval, &D.csr_val);
             up_(vf, &D.vcoef_f);
             D.max_row_nnz = max_row;
+        }
+        if (d->precision == MQCT_BF16X3) {
+            // pack whole m-blocks (contiguous in the internal order) into row tiles of <= 128 rows
+            std::vector<int> t0{0};
+            int rows = 0;
+            for (auto &b : bl) {
+                const int sz = (int)b.size();
+                if (sz > 128) {
+                    release(S);
+                    delete hs;
+                    return fail(MQCT_ERR_UNSUPPORTED, "BF16X3: an m-block has more than 128 states");
+                }
+                if (rows + sz > 128) { t0.push_back(t0.back() + rows); rows = 0; }
+                rows += sz;
+            }
+            t0.push_back(t0.back() + rows);
+            const int nt = (int)t0.size() - 1;
+            // block-diagonal 128 x 128 tiles, BF16 hi/lo split, canonical K-major MMA layout:
+            // element (r, k) at byte (r/8)*2048 + (k/8)*128 + (r%8)*16 + (k%8)*2
+            auto bf16_bits = [](float x) -> uint16_t {
+                uint32_t u;
+                std::memcpy(&u, &x, 4);
+                u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+                return (uint16_t)(u >> 16);
+            };
+            auto bf16_val = [](uint16_t h) -> float {
+                uint32_t u = (uint32_t)h << 16;
+                float x;
+                std::memcpy(&x, &u, 4);
+                return x;
+            };
+            std::vector<uint16_t> tiles((size_t)fterm.size() * nt * 2 * 16384, 0);
+            for (size_t f = 0; f < fterm.size(); ++f) {
+                const int l = fterm[f];
+                for (int t = 0; t < nt; ++t) {
+                    uint16_t *hi = tiles.data() + (((size_t)f * nt + t) * 2) * 16384, *lo = hi + 16384;
+                    for (int r = t0[t]; r < t0[t + 1]; ++r)
+                        for (auto &e : grows[l][r]) {
+                            const int rr = r - t0[t], kk = e.c - t0[t];
+                            const float v = (float)e.v;
+                            const uint16_t h = bf16_bits(v);
+                            const size_t off = ((size_t)(rr >> 3) * 2048 + (size_t)(kk >> 3) * 128 + (rr & 7) * 16 + (kk & 7) * 2) / 2;
+                            hi[off] = h;
+                            lo[off] = bf16_bits(v - bf16_val(h));
+                        }
+                }
+            }
+            D.n_tiles = nt;
+            up_(t0, &D.tile_r0);
+            up_(tiles, &D.g_tiles);
         }
         S.info.glambda_nnz = gnnz;
     }
