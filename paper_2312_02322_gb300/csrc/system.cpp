@@ -383,9 +383,11 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         unsigned long long idm = 0;
         int64_t gnnz = 0;
         for (int l = 0; l < L; ++l) {
+            // the identity (e.g. G^0 of a Legendre expansion) up to rounding of its construction
             bool ident = true;
             for (int r = 0; r < n && ident; ++r) {
-                if (grows[l][r].size() != 1 || grows[l][r][0].c != r || grows[l][r][0].v != 1.0) ident = false;
+                if (grows[l][r].size() != 1 || grows[l][r][0].c != r || std::fabs(grows[l][r][0].v - 1.0) > 1e-13)
+                    ident = false;
             }
             bool empty = true;
             for (int r = 0; r < n; ++r) if (!grows[l][r].empty()) empty = false;

@@ -210,84 +210,94 @@ __global__ void k_tc_identity(TcState T, int cur)
 }
 
 // ---------------------------------------------------------------------------------------------
-// element update: block = kTcRows rows x 32 slots
+// the update of one element (row r, slot sl) from w = M c and u = M' c (Eq. 5, RK4); adds its
+// force, torque and (stage 0) diagnostic contributions to part[6]
+__device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s, int cur, int r, int sl, int st,
+                                        float2 w, float2 u, double *part)
+{
+    const int nxt = cur ^ 1;
+    const size_t e = (size_t)r * T.S + sl;
+    const float2 *PHc = (s == 0 || s == 3) ? T.PHa : T.PHb;
+    const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
+    if (st == TS_WAIT && s == 3) {
+        const float2 v = make_float2(r == T.slot[sl].s0 ? 1.0f : 0.0f, 0.0f);
+        T.A[e] = v;
+        T.ACC[e] = make_float2(0.f, 0.f);
+        T.C[nxt][e] = v;
+        return;
+    }
+    if (st != TS_ACTIVE && st != TS_FINAL) return;
+    const float2 *Cc = T.C[cur];
+    const float2 c = Cc[e];
+    const float au = S.aupf[r], ad = S.adnf[r];
+    const float2 cu = Cc[(size_t)S.up[r] * T.S + sl], cd = Cc[(size_t)S.dn[r] * T.S + sl];
+    const float2 dc = make_float2(ad * cd.x - au * cu.x, ad * cd.y - au * cu.y);
+    const int lev = S.lev[r];
+    const float2 p = PHc[(size_t)lev * T.S + sl];
+    const float2 da = make_float2(p.x * dc.x + p.y * dc.y, p.x * dc.y - p.y * dc.x);
+    const float hp = T.hp[sl];
+    float2 kk;
+    kk.x = fmaf(hp, da.x, p.x * w.y - p.y * w.x);
+    kk.y = fmaf(hp, da.y, -(p.x * w.x + p.y * w.y));
+    part[0] -= (double)(c.x * u.x + c.y * u.y);
+    part[1] -= (double)(dc.x * w.x + dc.y * w.y);
+    const float2 a0 = T.A[e];
+    if (s == 0) {
+        const float pp = a0.x * a0.x + a0.y * a0.y;
+        part[2] += (double)(c.x * w.x + c.y * w.y);
+        part[3] += (double)pp;
+        part[4] += S.lev_energy[lev] * (double)pp;
+        part[5] += (double)(a0.x * da.y - a0.y * da.x);
+    }
+    if (st == TS_FINAL) {
+        if (s == 0) {
+            const size_t oo = (size_t)T.slot[sl].traj * T.nmax + S.perm[r];
+            if (T.pop) T.pop[oo] = (double)(a0.x * a0.x + a0.y * a0.y);
+            if (T.amp) { T.amp[2 * oo] = a0.x; T.amp[2 * oo + 1] = a0.y; }
+        }
+        return;
+    }
+    const float dtj = T.dtf[sl];
+    float2 acc = T.ACC[e];
+    if (s == 0) {
+        acc = make_float2(kk.x + acc.x, kk.y + acc.y);  // acc holds the last rounding error
+    } else {
+        const float wg = (s == 1 || s == 2) ? 2.0f : 1.0f;
+        acc.x = fmaf(wg, kk.x, acc.x);
+        acc.y = fmaf(wg, kk.y, acc.y);
+    }
+    if (s == 3) {
+        // compensated a + (dt/6) acc (two-sum); the rounding error goes to the accumulator
+        const float h6 = dtj * (1.0f / 6.0f), ih6 = 6.0f / dtj;
+        const float ix = h6 * acc.x, iy = h6 * acc.y;
+        const float sx = __fadd_rn(a0.x, ix), sy = __fadd_rn(a0.y, iy);
+        const float bx = __fsub_rn(sx, a0.x), by = __fsub_rn(sy, a0.y);
+        const float ex = __fadd_rn(__fsub_rn(a0.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
+        const float ey = __fadd_rn(__fsub_rn(a0.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
+        T.A[e] = make_float2(sx, sy);
+        T.ACC[e] = make_float2(ex * ih6, ey * ih6);
+        const float2 q = PHn[(size_t)lev * T.S + sl];
+        T.C[nxt][e] = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
+    } else {
+        T.ACC[e] = acc;
+        const float bn = s == 2 ? dtj : 0.5f * dtj;
+        const float2 yn = make_float2(fmaf(bn, kk.x, a0.x), fmaf(bn, kk.y, a0.y));
+        const float2 q = PHn[(size_t)lev * T.S + sl];
+        T.C[nxt][e] = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
+    }
+}
+
+// element update after k_tc_contract: block = kTcRows rows x 32 slots
 __global__ void __launch_bounds__(256) k_tc_update(TcState T, int s, int cur)
 {
     __shared__ double red[kTcRows][32][6];
     const DevSys &S = *T.sys;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int sl = blockIdx.x * 32 + tx, r = blockIdx.y * kTcRows + ty;
-    const int nxt = cur ^ 1;
     double part[6] = {0, 0, 0, 0, 0, 0};
     if (sl < T.S && r < S.n) {
-        const int st = T.state[sl];
         const size_t e = (size_t)r * T.S + sl;
-        const float2 *PHc = (s == 0 || s == 3) ? T.PHa : T.PHb;
-        const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
-        if (st == TS_WAIT && s == 3) {
-            const float2 v = make_float2(r == T.slot[sl].s0 ? 1.0f : 0.0f, 0.0f);
-            T.A[e] = v;
-            T.ACC[e] = make_float2(0.f, 0.f);
-            T.C[nxt][e] = v;
-        } else if (st == TS_ACTIVE || st == TS_FINAL) {
-            const float2 *Cc = T.C[cur];
-            const float2 c = Cc[e], w = T.W[e], u = T.U[e];
-            const float au = S.aupf[r], ad = S.adnf[r];
-            const float2 cu = Cc[(size_t)S.up[r] * T.S + sl], cd = Cc[(size_t)S.dn[r] * T.S + sl];
-            const float2 dc = make_float2(ad * cd.x - au * cu.x, ad * cd.y - au * cu.y);
-            const int lev = S.lev[r];
-            const float2 p = PHc[(size_t)lev * T.S + sl];
-            const float2 da = make_float2(p.x * dc.x + p.y * dc.y, p.x * dc.y - p.y * dc.x);
-            const float hp = T.hp[sl];
-            float2 kk;
-            kk.x = fmaf(hp, da.x, p.x * w.y - p.y * w.x);
-            kk.y = fmaf(hp, da.y, -(p.x * w.x + p.y * w.y));
-            part[0] = -(double)(c.x * u.x + c.y * u.y);
-            part[1] = -(double)(dc.x * w.x + dc.y * w.y);
-            const float2 a0 = T.A[e];
-            if (s == 0) {
-                const float pp = a0.x * a0.x + a0.y * a0.y;
-                part[2] = (double)(c.x * w.x + c.y * w.y);
-                part[3] = (double)pp;
-                part[4] = S.lev_energy[lev] * (double)pp;
-                part[5] = (double)(a0.x * da.y - a0.y * da.x);
-            }
-            if (st == TS_FINAL) {
-                if (s == 0) {
-                    const size_t oo = (size_t)T.slot[sl].traj * T.nmax + S.perm[r];
-                    if (T.pop) T.pop[oo] = (double)(a0.x * a0.x + a0.y * a0.y);
-                    if (T.amp) { T.amp[2 * oo] = a0.x; T.amp[2 * oo + 1] = a0.y; }
-                }
-            } else {
-                const float dtj = T.dtf[sl];
-                float2 acc = T.ACC[e];
-                if (s == 0) {
-                    acc = make_float2(kk.x + acc.x, kk.y + acc.y);  // acc holds the last rounding error
-                } else {
-                    const float wg = (s == 1 || s == 2) ? 2.0f : 1.0f;
-                    acc.x = fmaf(wg, kk.x, acc.x);
-                    acc.y = fmaf(wg, kk.y, acc.y);
-                }
-                if (s == 3) {
-                    const float h6 = dtj * (1.0f / 6.0f), ih6 = 6.0f / dtj;
-                    const float ix = h6 * acc.x, iy = h6 * acc.y;
-                    const float sx = __fadd_rn(a0.x, ix), sy = __fadd_rn(a0.y, iy);
-                    const float bx = __fsub_rn(sx, a0.x), by = __fsub_rn(sy, a0.y);
-                    const float ex = __fadd_rn(__fsub_rn(a0.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
-                    const float ey = __fadd_rn(__fsub_rn(a0.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
-                    T.A[e] = make_float2(sx, sy);
-                    T.ACC[e] = make_float2(ex * ih6, ey * ih6);
-                    const float2 q = PHn[(size_t)lev * T.S + sl];
-                    T.C[nxt][e] = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
-                } else {
-                    T.ACC[e] = acc;
-                    const float bn = s == 2 ? dtj : 0.5f * dtj;
-                    const float2 yn = make_float2(fmaf(bn, kk.x, a0.x), fmaf(bn, kk.y, a0.y));
-                    const float2 q = PHn[(size_t)lev * T.S + sl];
-                    T.C[nxt][e] = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
-                }
-            }
-        }
+        tc_elem(T, S, s, cur, r, sl, T.state[sl], T.W[e], T.U[e], part);
     }
     for (int q = 0; q < 6; ++q) red[ty][tx][q] = part[q];
     __syncthreads();
