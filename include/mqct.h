@@ -169,7 +169,46 @@ typedef struct {
  * Host-only: needs no GPU.  Errors: MQCT_ERR_INVALID_ARG (jmax < 0, n_terms outside
  * [1, 16], n_grid < 4, r_max <= r_min, mu <= 0), MQCT_ERR_OOM. */
 mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_system_desc *out);
-/* Free the arrays allocated by mqct_build_diatom and zero *desc. */
+/* Parameters of the built-in atom + rigid asymmetric top system (helper for users and tests).
+ * Rotor states (Eq. 1): psi_{J tau M} = sum_K b_K sqrt((2J+1)/(8 pi^2)) D^{J*}_{MK}, the b_K
+ * diagonalising A Ja^2 + B Jb^2 + C Jc^2 (K = projection on the a axis); within one J the
+ * 2J+1 levels are labelled tau = -J..J in ascending energy.  The basis keeps whole levels (all
+ * 2J+1 values of M) for J <= jmax in ascending energy (ties: smaller J first) while the number
+ * of states stays <= max_states; states are level-major, M = -J..J within a level, and each
+ * level's eigenvector has its largest component in Wang's symmetrised functions positive.
+ * PES: V = sum_t v_t(R) f_t with v_t = coef_t exp(-beta_t R) (plus the damped dispersion
+ * -C6 R^-6 (1 - exp(-(R/Rd)^6)) on term 0) and the real angular functions
+ *   f_t = (D^{lam*}_{0 mu} + (-1)^mu D^{lam*}_{0,-mu}) / (1 + delta_{mu 0}),  0 <= mu <= lam,
+ * i.e. P_lam(cos beta) for mu = 0 and 2 d^lam_{0 mu}(beta) cos(mu gamma) otherwise (the +-mu
+ * combination of Eq. 14 for an atom partner).  G^t = <J'' tau'' M | f_t | J' tau' M> (the Eq. 16
+ * integrals) is real symmetric and block-diagonal in M.  With with_params != 0 the derivative
+ * tables for theta = (coef_0..coef_{L-1}, beta_0..beta_{L-1}) are filled (P = 2L). */
+typedef struct {
+    int32_t jmax;        /* 0..20                                                  */
+    double A, B, C;      /* rotational constants (hartree), A >= B >= C > 0, A > C */
+    int32_t max_states;  /* >= 1                                                    */
+    double mu;           /* reduced mass (electron masses)                         */
+    int32_t n_terms;     /* L in [1, 64]                                           */
+    int32_t lam[64];     /* lambda_t in [0, 8]                                     */
+    int32_t mproj[64];   /* mu_t in [0, lambda_t]                                  */
+    double coef[64];     /* hartree                                                */
+    double beta[64];     /* 1/bohr                                                 */
+    double c6;           /* hartree bohr^6                                         */
+    double rd;           /* bohr                                                   */
+    int32_t n_grid;
+    double r_min, r_max;
+    int32_t with_params;
+    int32_t path, precision;
+    int32_t *tau_out;    /* optional HOST array of (jmax+1)^2 entries: tau of each kept level */
+} mqct_asym_params;
+
+/* Build the description of the atom + asymmetric top system above (host only, no GPU).
+ * Allocates the host arrays of *out (released by mqct_free_desc); G in triplet form.
+ * Errors: MQCT_ERR_INVALID_ARG (a bound above violated, or max_states below the first
+ * level), MQCT_ERR_OOM. */
+mqct_status mqct_build_asym_top(const mqct_asym_params *p, mqct_system_desc *out);
+
+/* Free the arrays allocated by mqct_build_diatom / mqct_build_asym_top and zero *desc. */
 void mqct_free_desc(mqct_system_desc *desc);
 
 /* Validate `desc`, build the spline tables (Sec. III) and coupling layouts of Eq. 12 in

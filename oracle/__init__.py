@@ -8,7 +8,8 @@ this module only marshals numpy arrays through ctypes.  Every quantity is in
 atomic units (hartree, bohr, electron masses, atomic units of time).
 
 Paper passages followed (arXiv 2312.02322): Eq. 4-10 (equations of motion), Eq. 12
-(factorised PES), Eq. 15 (Gaunt integral), Sec. III (cubic spline of the coupling),
+(factorised PES), Eq. 15 (Gaunt integral), Eq. 1 and Eq. 16 (asymmetric-top states and
+their coupling), Sec. III (cubic spline of the coupling),
 Sec. II (cross sections from final populations).
 """
 from __future__ import annotations
@@ -80,6 +81,8 @@ def lib():
             L.ora_propagate.restype = C.c_int
             L.ora_tangent.restype = C.c_int
             L.ora_num_threads.restype = C.c_int
+            L.ora_asym_levels.restype = C.c_int
+            L.ora_asym_basis.restype = C.c_int
             _lib = L
     return _lib
 
@@ -152,6 +155,8 @@ def diatom_G(jmax: int, lam: int) -> np.ndarray:
 
 
 def diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params=False):
+    """Grid tables of v_l(R) = A_l exp(-beta_l R) (+ damped -C6 R^-6 on term 0), end slopes and,
+    with with_params, their derivatives with respect to (A_0.., beta_0..)."""
     A = np.ascontiguousarray(A, np.float64)
     beta = np.ascontiguousarray(beta, np.float64)
     L = A.shape[0]
@@ -172,6 +177,60 @@ def diatom_system(jmax, bconst, mu, A, beta, c6, rd, n_grid, r_min, r_max, with_
     G = np.stack([diatom_G(jmax, l) for l in range(L)])
     v, ends, dvp, dvpe = diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params)
     return System(e, lev, jq, mq, G, v, ends, mu, r_min, r_max, dvp, dvpe)
+
+
+def asym_levels(J: int, A: float, B: float, Cc: float):
+    """Eigenstates of the rigid asymmetric top for one J (Eq. 1): energies ascending (tau = -J..J)
+    and b[e][K + J]."""
+    n = 2 * J + 1
+    E = np.zeros(n)
+    b = np.zeros((n, n))
+    if lib().ora_asym_levels(C.c_int(J), C.c_double(A), C.c_double(B), C.c_double(Cc), _p(E), _p(b)):
+        raise MemoryError("ora_asym_levels")
+    return E, b
+
+
+def asym_basis(jmax: int, A: float, B: float, Cc: float, max_states: int):
+    """Levels kept for the asymmetric-top basis: (J, tau, E, b[l][K + jmax]) in ascending energy."""
+    nall = (jmax + 1) ** 2
+    lj, lt = np.zeros(nall, np.int32), np.zeros(nall, np.int32)
+    le, lb = np.zeros(nall), np.zeros((nall, 2 * jmax + 1))
+    nl = lib().ora_asym_basis(C.c_int(jmax), C.c_double(A), C.c_double(B), C.c_double(Cc), C.c_int(max_states),
+                              _p(lj), _p(lt), _p(le), _p(lb))
+    if nl < 0:
+        raise MemoryError("ora_asym_basis")
+    return lj[:nl].copy(), lt[:nl].copy(), le[:nl].copy(), lb[:nl].copy()
+
+
+def asym_states(lev_J, lev_E):
+    """State labels of the level-major asymmetric-top basis (M = -J..J inside each level)."""
+    e, lev, jq, mq = [], [], [], []
+    for l, (J, E) in enumerate(zip(lev_J, lev_E)):
+        for M in range(-J, J + 1):
+            e.append(E); lev.append(l); jq.append(J); mq.append(M)
+    return np.array(e), np.array(lev, np.int32), np.array(jq, np.int32), np.array(mq, np.int32)
+
+
+def asym_G(lev_J, lev_b, jmax: int, lam: int, mu: int) -> np.ndarray:
+    """<J'' tau'' M | f_{lam mu} | J' tau' M> over the level-major states (Eq. 16)."""
+    lev_J = np.ascontiguousarray(lev_J, np.int32)
+    lev_b = np.ascontiguousarray(lev_b, np.float64)
+    n = int(np.sum(2 * lev_J + 1))
+    G = np.zeros((n, n))
+    lib().ora_asym_G(C.c_int(len(lev_J)), _p(lev_J), _p(lev_b), C.c_int(jmax), C.c_int(lam), C.c_int(mu), C.c_int(n),
+                     _p(G))
+    return G
+
+
+def asym_system(p, with_params=False) -> System:
+    """Atom + rigid asymmetric top from an AsymTopParams-like object (Eq. 1 basis, Eq. 16 coupling)."""
+    lj, lt, le, lb = asym_basis(p.jmax, p.A, p.B, p.C, p.max_states)
+    e, lev, jq, mq = asym_states(lj, le)
+    G = np.stack([asym_G(lj, lb, p.jmax, int(l), int(m)) for l, m in zip(p.lam, p.mproj)])
+    v, ends, dvp, dvpe = diatom_pes(p.coef, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max, with_params)
+    s = System(e, lev, jq, mq, G, v, ends, p.mu, p.r_min, p.r_max, dvp, dvpe)
+    s.tau = lt
+    return s
 
 
 def spline(y, h, d0, dn) -> np.ndarray:

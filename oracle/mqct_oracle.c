@@ -16,6 +16,9 @@
  *   Eqs. 7-10   classical R, Phi, P_R, P_Phi in the collision plane (Theta = pi/2)
  *   Eq. 12      V = sum_lambda v_lambda(R) tau_lambda, hence M(R) = sum_lambda v_lambda(R) G^lambda
  *   Eq. 15      integral of three spherical harmonics (G^lambda of a linear rotor)
+ *   Eq. 1       asymmetric-top eigenstates as sums of symmetric-top functions (Wang's
+ *               symmetrised functions, Jacobi rotations)
+ *   Eq. 16      integral of three Wigner D-functions (G^{lambda mu} of an asymmetric top)
  *   Sec. III    cubic-spline interpolation of the coupling along R
  *   Sec. II     final |a|^2 summed over final and averaged over initial degenerate states
  *
@@ -858,4 +861,210 @@ int ora_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Rigid asymmetric top (Eq. 1 basis) and its coupling to an atom      */
+/* (Eq. 16 integrals of three Wigner D-functions)                      */
+/* ------------------------------------------------------------------ */
+/* Rotor Hamiltonian A Ja^2 + B Jb^2 + C Jc^2 for one J in the symmetric-top functions
+ * |J K> (K = projection on the a axis, index K + J), with Jb, Jc taken as Jx, Jy:
+ *   <K|H|K>   = (B+C)/2 (J(J+1) - K^2) + A K^2
+ *   <K+2|H|K> = (B-C)/4 sqrt((J-K)(J-K-1)(J+K+1)(J+K+2)). */
+static void asym_h(int J, double A, double B, double C, double *H)
+{
+    int n = 2 * J + 1;
+    memset(H, 0, sizeof(double) * n * n);
+    for (int K = -J; K <= J; ++K) {
+        H[(K + J) * n + (K + J)] = 0.5 * (B + C) * ((double)J * (J + 1) - (double)K * K) + A * (double)K * K;
+        if (K + 2 <= J) {
+            double x = 0.25 * (B - C) * sqrt((double)(J - K) * (J - K - 1) * (J + K + 1) * (J + K + 2));
+            H[(K + 2 + J) * n + (K + J)] = x;
+            H[(K + J) * n + (K + 2 + J)] = x;
+        }
+    }
+}
+
+/* Wang's symmetrised functions, column w of U (|K> rows): w = 0 is |0>, then for
+ * K = 1..J the pair (|K> + |-K>)/sqrt2, (|K> - |-K>)/sqrt2.  H is invariant under K -> -K,
+ * so U^T H U has no element between the + and - combinations (nor between even and odd K):
+ * every eigenvector stays inside one symmetry class, also for near-degenerate pairs. */
+static void wang_basis(int J, double *U)
+{
+    int n = 2 * J + 1;
+    double r = sqrt(0.5);
+    memset(U, 0, sizeof(double) * n * n);
+    U[J * n + 0] = 1.0;
+    for (int K = 1; K <= J; ++K) {
+        int wp = 2 * K - 1, wm = 2 * K;
+        U[(K + J) * n + wp] = r;  U[(-K + J) * n + wp] = r;
+        U[(K + J) * n + wm] = r;  U[(-K + J) * n + wm] = -r;
+    }
+}
+
+/* cyclic Jacobi rotations on the symmetric matrix a (destroyed); v = eigenvectors (columns), w = eigenvalues */
+static void jacobi_eigen(int n, double *a, double *v, double *w)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) v[i * n + j] = (i == j);
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += a[p * n + p] * a[p * n + p];
+            for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+        }
+        if (off <= 1e-34 * diag || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = a[p * n + q];
+                if (apq == 0.0) continue;
+                double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = c * akp - s * akq;
+                    a[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = c * apk - s * aqk;
+                    a[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = v[k * n + p], vkq = v[k * n + q];
+                    v[k * n + p] = c * vkp - s * vkq;
+                    v[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) w[i] = a[i * n + i];
+}
+
+/* Eigenstates of one J (Eq. 1): E[e] ascending (e = 0..2J, tau = e - J), b[e][K + J] the expansion
+ * coefficients b_K.  Sign: the largest-magnitude Wang component of each eigenvector is positive
+ * (first such component on a tie). */
+int ora_asym_levels(int J, double A, double B, double C, double *E, double *b)
+{
+    int n = 2 * J + 1;
+    double *H = malloc(sizeof(double) * n * n), *U = malloc(sizeof(double) * n * n);
+    double *Hw = malloc(sizeof(double) * n * n), *V = malloc(sizeof(double) * n * n);
+    double *w = malloc(sizeof(double) * n);
+    int *idx = malloc(sizeof(int) * n);
+    if (!H || !U || !Hw || !V || !w || !idx) {
+        free(H); free(U); free(Hw); free(V); free(w); free(idx);
+        return ORA_ENOMEM;
+    }
+    asym_h(J, A, B, C, H);
+    wang_basis(J, U);
+    for (int p = 0; p < n; ++p)          /* Hw = U^T H U, zero between classes (exactly, not to rounding) */
+        for (int q = 0; q < n; ++q) {
+            int Kp = (p + 1) / 2, Kq = (q + 1) / 2;
+            int sp = p > 0 && p % 2 == 0, sq = q > 0 && q % 2 == 0;  /* 1 for the (|K> - |-K>) combination */
+            double s = 0.0;
+            if ((Kp - Kq) % 2 == 0 && sp == sq)
+                for (int k = 0; k < n; ++k)
+                    for (int l = 0; l < n; ++l) s += U[k * n + p] * H[k * n + l] * U[l * n + q];
+            Hw[p * n + q] = s;
+        }
+    jacobi_eigen(n, Hw, V, w);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    for (int i = 0; i < n; ++i)          /* ascending energy */
+        for (int j = i + 1; j < n; ++j)
+            if (w[idx[j]] < w[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+    for (int e = 0; e < n; ++e) {
+        int src = idx[e], big = 0;
+        for (int k = 1; k < n; ++k)
+            if (fabs(V[k * n + src]) > fabs(V[big * n + src])) big = k;
+        double sg = V[big * n + src] < 0 ? -1.0 : 1.0;
+        E[e] = w[src];
+        for (int K = 0; K < n; ++K) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += U[K * n + k] * V[k * n + src];
+            b[e * n + K] = sg * s;
+        }
+    }
+    free(H); free(U); free(Hw); free(V); free(w); free(idx);
+    return ORA_OK;
+}
+
+/* Levels (J, tau) for J <= jmax in ascending energy (ties: smaller J first), keeping whole
+ * multiplets (all 2J+1 values of M) while the total number of states stays <= max_states.
+ * Output arrays hold (jmax+1)^2 levels; lev_b[l][K + jmax] (row length 2 jmax + 1).
+ * Returns the number of levels kept, or -1 on allocation failure. */
+int ora_asym_basis(int jmax, double A, double B, double C, int max_states, int *lev_J, int *lev_tau,
+                   double *lev_E, double *lev_b)
+{
+    int nall = (jmax + 1) * (jmax + 1), w = 2 * jmax + 1;
+    int *aJ = malloc(sizeof(int) * nall), *at = malloc(sizeof(int) * nall), *ord = malloc(sizeof(int) * nall);
+    double *aE = malloc(sizeof(double) * nall), *ab = calloc((size_t)nall * w, sizeof(double));
+    double *E = malloc(sizeof(double) * w), *b = malloc(sizeof(double) * w * w);
+    if (!aJ || !at || !ord || !aE || !ab || !E || !b) {
+        free(aJ); free(at); free(ord); free(aE); free(ab); free(E); free(b);
+        return -1;
+    }
+    int k = 0;
+    for (int J = 0; J <= jmax; ++J) {
+        int n = 2 * J + 1;
+        ora_asym_levels(J, A, B, C, E, b);
+        for (int e = 0; e < n; ++e, ++k) {
+            aJ[k] = J; at[k] = e - J; aE[k] = E[e];
+            for (int K = -J; K <= J; ++K) ab[(size_t)k * w + K + jmax] = b[e * n + K + J];
+        }
+    }
+    for (int i = 0; i < nall; ++i) ord[i] = i;
+    for (int i = 0; i < nall; ++i)       /* stable selection by (E, J) */
+        for (int j = i + 1; j < nall; ++j) {
+            int a = ord[i], c = ord[j];
+            if (aE[c] < aE[a] || (aE[c] == aE[a] && aJ[c] < aJ[a])) { ord[i] = c; ord[j] = a; }
+        }
+    int nl = 0, ns = 0;
+    for (int i = 0; i < nall; ++i) {
+        int s = ord[i];
+        if (ns + 2 * aJ[s] + 1 > max_states) break;
+        ns += 2 * aJ[s] + 1;
+        lev_J[nl] = aJ[s]; lev_tau[nl] = at[s]; lev_E[nl] = aE[s];
+        memcpy(lev_b + (size_t)nl * w, ab + (size_t)s * w, sizeof(double) * w);
+        ++nl;
+    }
+    free(aJ); free(at); free(ord); free(aE); free(ab); free(E); free(b);
+    return nl;
+}
+
+/* Coupling matrix of one expansion term (Eq. 12) between the states (level, M), levels in the given
+ * order and M = -J..J inside each level.  The angular function is
+ *   f_{lam mu} = (D^{lam*}_{0 mu} + (-1)^mu D^{lam*}_{0,-mu}) / (1 + delta_{mu 0}),  0 <= mu <= lam,
+ * real (2 d^lam_{0 mu}(beta) cos(mu gamma), or P_lam(cos beta) for mu = 0).  With Eq. 16 and the
+ * normalisation sqrt((2J+1)/(8 pi^2)) of Eq. 1,
+ *   <J'' K'' M | D^{lam*}_{0 nu} | J' K' M> = sqrt((2J'+1)/(2J''+1)) C^{J''M}_{J'M lam 0} C^{J''K''}_{J'K' lam nu},
+ * and the eigenstates add these with weights b''_{K''} b'_{K'}.  G[n][n], row = final state. */
+void ora_asym_G(int n_lev, const int *lev_J, const double *lev_b, int jmax, int lam, int mu, int n, double *G)
+{
+    int w = 2 * jmax + 1;
+    int *first = malloc(sizeof(int) * (n_lev + 1));
+    first[0] = 0;
+    for (int l = 0; l < n_lev; ++l) first[l + 1] = first[l] + 2 * lev_J[l] + 1;
+    memset(G, 0, sizeof(double) * (size_t)n * n);
+    double sgn = (mu & 1) ? -1.0 : 1.0;
+#pragma omp parallel for schedule(dynamic)
+    for (int l2 = 0; l2 < n_lev; ++l2)
+        for (int l1 = 0; l1 < n_lev; ++l1) {
+            int J2 = lev_J[l2], J1 = lev_J[l1];
+            if (abs(J2 - J1) > lam || J2 + J1 < lam) continue;
+            const double *b2 = lev_b + (size_t)l2 * w + jmax, *b1 = lev_b + (size_t)l1 * w + jmax;
+            double S = 0.0;  /* the K sum: independent of M */
+            for (int K1 = -J1; K1 <= J1; ++K1) {
+                int Kp = K1 + mu, Km = K1 - mu;
+                if (Kp >= -J2 && Kp <= J2) S += b2[Kp] * b1[K1] * ora_cg(J1, K1, lam, mu, J2, Kp);
+                if (mu > 0 && Km >= -J2 && Km <= J2) S += sgn * b2[Km] * b1[K1] * ora_cg(J1, K1, lam, -mu, J2, Km);
+            }
+            if (S == 0.0) continue;
+            double pre = sqrt((2.0 * J1 + 1.0) / (2.0 * J2 + 1.0)) * S;
+            int Mmax = J1 < J2 ? J1 : J2;
+            for (int M = -Mmax; M <= Mmax; ++M) {
+                int r = first[l2] + M + J2, c = first[l1] + M + J1;
+                if (r < n && c < n) G[(size_t)r * n + c] = pre * ora_cg(J1, M, lam, 0, J2, M);
+            }
+        }
+    free(first);
 }

@@ -59,6 +59,15 @@ class DiatomParams(C.Structure):
                 ("path", C.c_int32), ("precision", C.c_int32)]
 
 
+class AsymParams(C.Structure):
+    _fields_ = [("jmax", C.c_int32), ("A", C.c_double), ("B", C.c_double), ("C", C.c_double),
+                ("max_states", C.c_int32), ("mu", C.c_double), ("n_terms", C.c_int32), ("lam", C.c_int32 * 64),
+                ("mproj", C.c_int32 * 64), ("coef", C.c_double * 64), ("beta", C.c_double * 64), ("c6", C.c_double),
+                ("rd", C.c_double), ("n_grid", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double),
+                ("with_params", C.c_int32), ("path", C.c_int32), ("precision", C.c_int32),
+                ("tau_out", C.c_void_p)]
+
+
 TRAJ_DTYPE = np.dtype([("e_coll", "<f8"), ("b", "<f8"), ("r0", "<f8"), ("r_end", "<f8"), ("dt", "<f8"),
                        ("init_state", "<i4"), ("max_steps", "<i4"), ("system_idx", "<i4"), ("_pad", "<i4")])
 DIAG_DTYPE = np.dtype([("steps", "<i4"), ("status", "<i4"), ("norm_dev", "<f8"), ("energy_dev", "<f8"),
@@ -79,6 +88,7 @@ def lib():
             L = C.CDLL(LIB_PATH)
             vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
             L.mqct_build_diatom.argtypes = [C.POINTER(DiatomParams), C.POINTER(Desc)]
+            L.mqct_build_asym_top.argtypes = [C.POINTER(AsymParams), C.POINTER(Desc)]
             L.mqct_free_desc.argtypes = [C.POINTER(Desc)]
             L.mqct_free_desc.restype = None
             L.mqct_create_system.argtypes = [C.POINTER(Desc), C.POINTER(vp)]
@@ -91,7 +101,7 @@ def lib():
             L.mqct_probe_fma_rate.restype = C.c_int
             L.mqct_last_error.restype = C.c_char_p
             L.mqct_version.restype = C.c_char_p
-            for f in ("mqct_build_diatom", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
+            for f in ("mqct_build_diatom", "mqct_build_asym_top", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
                       "mqct_propagate", "mqct_cross_sections", "mqct_adjoint"):
                 getattr(L, f).restype = C.c_int
             _lib = L
@@ -147,6 +157,8 @@ class System:
         self.n_params = desc.n_params
         self._keep = keep
         self._index = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(self.j, self.m))}
+        self._lindex = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(self.level, self.m))}
+        self.tau = None  # per-level tau label (asymmetric top only)
 
     @classmethod
     def diatom(cls, p: "_inputs.DiatomParams", path="plain", precision="fp64", with_params=False) -> "System":
@@ -165,8 +177,35 @@ class System:
         finally:
             lib().mqct_free_desc(C.byref(d))
 
+    @classmethod
+    def asym_top(cls, p: "_inputs.AsymTopParams", path="plain", precision="fp64", with_params=False) -> "System":
+        ap = AsymParams()
+        ap.jmax, ap.A, ap.B, ap.C, ap.max_states, ap.mu = p.jmax, p.A, p.B, p.C, p.max_states, p.mu
+        ap.n_terms = p.n_terms
+        for t in range(p.n_terms):
+            ap.lam[t], ap.mproj[t] = int(p.lam[t]), int(p.mproj[t])
+            ap.coef[t], ap.beta[t] = float(p.coef[t]), float(p.beta[t])
+        ap.c6, ap.rd, ap.n_grid, ap.r_min, ap.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
+        ap.with_params = int(bool(with_params))
+        ap.path, ap.precision = _PATHS[path], _PRECS[precision]
+        tau = np.zeros((p.jmax + 1) ** 2, np.int32)
+        ap.tau_out = tau.ctypes.data
+        d = Desc()
+        _check(lib().mqct_build_asym_top(C.byref(ap), C.byref(d)))
+        try:
+            s = cls(d)
+        finally:
+            lib().mqct_free_desc(C.byref(d))
+        s.tau = tau[: int(s.level.max()) + 1].copy()
+        return s
+
     def state(self, j, m) -> int:
+        """State index of the (j, m) label (unique for a linear rotor)."""
         return self._index[(int(j), int(m))]
+
+    def level_state(self, level, m) -> int:
+        """State index of projection m in the given level."""
+        return self._lindex[(int(level), int(m))]
 
     @property
     def info(self) -> dict:
@@ -195,14 +234,18 @@ class System:
 
 
 def make_trajs(ts: "_inputs.TrajSet", systems) -> np.ndarray:
-    """mqct_traj array for a TrajSet; initial states addressed by their (j, m) labels."""
+    """mqct_traj array for a TrajSet; initial states addressed by their (j, m) labels, or by
+    (level, m) when ts.init_by == "level"."""
     systems = systems if isinstance(systems, (list, tuple)) else [systems]
     tr = np.zeros(ts.n, TRAJ_DTYPE)
     tr["e_coll"], tr["b"] = ts.e_coll, ts.b
     tr["r0"], tr["r_end"], tr["dt"], tr["max_steps"] = ts.r0, ts.r_end, ts.dt, ts.max_steps
     sidx = ts.system if len(ts.system) else np.zeros(ts.n, np.int32)
     tr["system_idx"] = sidx
-    tr["init_state"] = [systems[s].state(j, m) for s, j, m in zip(sidx, ts.init_j, ts.init_m)]
+    if ts.init_by == "level":
+        tr["init_state"] = [systems[s].level_state(j, m) for s, j, m in zip(sidx, ts.init_j, ts.init_m)]
+    else:
+        tr["init_state"] = [systems[s].state(j, m) for s, j, m in zip(sidx, ts.init_j, ts.init_m)]
     return tr
 
 

@@ -16,7 +16,7 @@
 
 #include "internal.h"
 
-namespace {
+namespace mqct {
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
@@ -44,6 +44,10 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
         w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
 }
+
+}  // namespace mqct
+
+namespace {
 
 // theta[j] = normalised associated Legendre function of order m (int_{-1}^{1} theta^2 dx = 1)
 // at x for j = m..jmax (entries j < m are left at zero).
@@ -84,6 +88,91 @@ T *alloc_copy(const std::vector<T> &v)
 }
 
 }  // namespace
+
+namespace mqct {
+
+// Grid tables of the expansion coefficients v_l(R) = A_l exp(-beta_l R) (+ the damped -C6 R^-6
+// dispersion on term 0), their analytic end slopes for the clamped spline and, with
+// with_params, the derivative tables for theta = (A_0..A_{L-1}, beta_0..beta_{L-1}); then the
+// host arrays of *out (freed by mqct_free_desc).
+mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vector<double> &energy,
+                        const std::vector<int32_t> &level, const std::vector<int32_t> &jq,
+                        const std::vector<int32_t> &mq, double mu, int L, const std::vector<int32_t> &gt,
+                        const std::vector<int32_t> &gr, const std::vector<int32_t> &gc, const std::vector<double> &gv,
+                        const double *A, const double *beta, double c6, double rd, int ng, double r_min, double r_max,
+                        bool with_params, int path, int precision)
+{
+    const int n = (int)energy.size();
+    const double h = (r_max - r_min) / (ng - 1);
+    std::vector<double> v((size_t)L * ng), ends((size_t)L * 2);
+    auto c6term = [&](double R) { return -c6 * std::pow(R, -6.0) * (1.0 - std::exp(-std::pow(R / rd, 6.0))); };
+    auto c6slope = [&](double R) {
+        double u = std::pow(R / rd, 6.0);
+        return 6.0 * c6 * std::pow(R, -7.0) * (1.0 - std::exp(-u)) - 6.0 * c6 * u * std::exp(-u) * std::pow(R, -7.0);
+    };
+    for (int l = 0; l < L; ++l) {
+        for (int k = 0; k < ng; ++k) {
+            double R = r_min + k * h;
+            v[(size_t)l * ng + k] = A[l] * std::exp(-beta[l] * R) + (l == 0 ? c6term(R) : 0.0);
+        }
+        for (int e = 0; e < 2; ++e) {
+            double R = e ? r_max : r_min;
+            ends[2 * l + e] = -beta[l] * A[l] * std::exp(-beta[l] * R) + (l == 0 ? c6slope(R) : 0.0);
+        }
+    }
+    std::vector<double> dvp, dvpe;
+    int P = 0;
+    if (with_params) {
+        P = 2 * L;
+        dvp.assign((size_t)P * L * ng, 0.0);
+        dvpe.assign((size_t)P * L * 2, 0.0);
+        for (int l = 0; l < L; ++l) {
+            for (int k = 0; k < ng; ++k) {
+                double R = r_min + k * h, ex = std::exp(-beta[l] * R);
+                dvp[((size_t)l * L + l) * ng + k] = ex;                      // d/dA_l
+                dvp[((size_t)(L + l) * L + l) * ng + k] = -R * A[l] * ex;    // d/dbeta_l
+            }
+            for (int e = 0; e < 2; ++e) {
+                double R = e ? r_max : r_min, ex = std::exp(-beta[l] * R);
+                dvpe[((size_t)l * L + l) * 2 + e] = -beta[l] * ex;
+                dvpe[((size_t)(L + l) * L + l) * 2 + e] = A[l] * ex * (beta[l] * R - 1.0);
+            }
+        }
+    }
+
+    out->n_states = n;
+    out->energy = alloc_copy(energy);
+    out->level = alloc_copy(level);
+    out->j = alloc_copy(jq);
+    out->m = alloc_copy(mq);
+    out->mu = mu;
+    out->n_terms = L;
+    out->G = nullptr;
+    out->g_nnz = (int64_t)gv.size();
+    out->g_term = alloc_copy(gt);
+    out->g_row = alloc_copy(gr);
+    out->g_col = alloc_copy(gc);
+    out->g_val = alloc_copy(gv);
+    out->n_grid = ng;
+    out->r_min = r_min;
+    out->r_max = r_max;
+    out->v = alloc_copy(v);
+    out->dv_ends = alloc_copy(ends);
+    out->n_params = P;
+    out->dv_dparam = P ? alloc_copy(dvp) : nullptr;
+    out->ddv_ends = P ? alloc_copy(dvpe) : nullptr;
+    out->path = path;
+    out->precision = precision;
+    out->flags = 0;
+    if (!out->energy || !out->level || !out->j || !out->m || !out->g_term || !out->g_row || !out->g_col ||
+        !out->g_val || !out->v || !out->dv_ends || (P && (!out->dv_dparam || !out->ddv_ends))) {
+        mqct_free_desc(out);
+        return fail(MQCT_ERR_OOM, std::string(who) + ": host allocation failed");
+    }
+    return MQCT_OK;
+}
+
+}  // namespace mqct
 
 extern "C" mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_system_desc *out)
 {
@@ -138,74 +227,8 @@ extern "C" mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_syste
         }
     }
 
-    // PES on the grid, analytic end slopes, parameter derivatives
-    const double h = (p->r_max - p->r_min) / (ng - 1);
-    std::vector<double> v((size_t)L * ng), ends((size_t)L * 2);
-    auto c6term = [&](double R) { return -p->c6 * std::pow(R, -6.0) * (1.0 - std::exp(-std::pow(R / p->rd, 6.0))); };
-    auto c6slope = [&](double R) {
-        double u = std::pow(R / p->rd, 6.0);
-        return 6.0 * p->c6 * std::pow(R, -7.0) * (1.0 - std::exp(-u)) - 6.0 * p->c6 * u * std::exp(-u) * std::pow(R, -7.0);
-    };
-    for (int l = 0; l < L; ++l) {
-        for (int k = 0; k < ng; ++k) {
-            double R = p->r_min + k * h;
-            v[(size_t)l * ng + k] = p->A[l] * std::exp(-p->beta[l] * R) + (l == 0 ? c6term(R) : 0.0);
-        }
-        for (int e = 0; e < 2; ++e) {
-            double R = e ? p->r_max : p->r_min;
-            ends[2 * l + e] = -p->beta[l] * p->A[l] * std::exp(-p->beta[l] * R) + (l == 0 ? c6slope(R) : 0.0);
-        }
-    }
-    std::vector<double> dvp, dvpe;
-    int P = 0;
-    if (p->with_params) {
-        P = 2 * L;
-        dvp.assign((size_t)P * L * ng, 0.0);
-        dvpe.assign((size_t)P * L * 2, 0.0);
-        for (int l = 0; l < L; ++l) {
-            for (int k = 0; k < ng; ++k) {
-                double R = p->r_min + k * h, ex = std::exp(-p->beta[l] * R);
-                dvp[((size_t)l * L + l) * ng + k] = ex;                          // d/dA_l
-                dvp[((size_t)(L + l) * L + l) * ng + k] = -R * p->A[l] * ex;     // d/dbeta_l
-            }
-            for (int e = 0; e < 2; ++e) {
-                double R = e ? p->r_max : p->r_min, ex = std::exp(-p->beta[l] * R);
-                dvpe[((size_t)l * L + l) * 2 + e] = -p->beta[l] * ex;
-                dvpe[((size_t)(L + l) * L + l) * 2 + e] = p->A[l] * ex * (p->beta[l] * R - 1.0);
-            }
-        }
-    }
-
-    out->n_states = n;
-    out->energy = alloc_copy(energy);
-    out->level = alloc_copy(level);
-    out->j = alloc_copy(jq);
-    out->m = alloc_copy(mq);
-    out->mu = p->mu;
-    out->n_terms = L;
-    out->G = nullptr;
-    out->g_nnz = (int64_t)gv.size();
-    out->g_term = alloc_copy(gt);
-    out->g_row = alloc_copy(gr);
-    out->g_col = alloc_copy(gc);
-    out->g_val = alloc_copy(gv);
-    out->n_grid = ng;
-    out->r_min = p->r_min;
-    out->r_max = p->r_max;
-    out->v = alloc_copy(v);
-    out->dv_ends = alloc_copy(ends);
-    out->n_params = P;
-    out->dv_dparam = P ? alloc_copy(dvp) : nullptr;
-    out->ddv_ends = P ? alloc_copy(dvpe) : nullptr;
-    out->path = p->path;
-    out->precision = p->precision;
-    out->flags = 0;
-    if (!out->energy || !out->level || !out->j || !out->m || !out->g_term || !out->g_row || !out->g_col ||
-        !out->g_val || !out->v || !out->dv_ends || (P && (!out->dv_dparam || !out->ddv_ends))) {
-        mqct_free_desc(out);
-        return fail(MQCT_ERR_OOM, "mqct_build_diatom: host allocation failed");
-    }
-    return MQCT_OK;
+    return mqct::finish_desc(out, "mqct_build_diatom", energy, level, jq, mq, p->mu, L, gt, gr, gc, gv, p->A, p->beta,
+                             p->c6, p->rd, ng, p->r_min, p->r_max, p->with_params != 0, p->path, p->precision);
 }
 
 extern "C" void mqct_free_desc(mqct_system_desc *d)

@@ -126,6 +126,15 @@ int batched_width(const DevSys &h);
 mqct_status fail(mqct_status st, const std::string &msg);
 mqct_status cuda_fail(cudaError_t e, const char *what);
 
+// host helpers of the built-in system builders (diatom.cpp)
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
+mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vector<double> &energy,
+                        const std::vector<int32_t> &level, const std::vector<int32_t> &jq,
+                        const std::vector<int32_t> &mq, double mu, int L, const std::vector<int32_t> &gt,
+                        const std::vector<int32_t> &gr, const std::vector<int32_t> &gc, const std::vector<double> &gv,
+                        const double *A, const double *beta, double c6, double rd, int ng, double r_min, double r_max,
+                        bool with_params, int path, int precision);
+
 }  // namespace mqct
 
 struct mqct_system_s {

@@ -76,6 +76,7 @@ class TrajSet:
     system: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))  # system index per trajectory
     group_e: np.ndarray = field(default_factory=lambda: np.zeros(0))           # energy of each group
     group_j: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32)) # initial level of each group
+    init_by: str = "j"         # "j": init_j is the rotor j label; "level": init_j is a level index
 
     @property
     def n(self) -> int:
@@ -86,7 +87,8 @@ class TrajSet:
         return TrajSet(self.e_coll[idx], self.b[idx], self.init_j[idx], self.init_m[idx], self.group[idx],
                        self.n_groups, self.r0, self.r_end, self.dt, self.max_steps, self.sampling, self.b_max,
                        self.n_b, self.m_avg,
-                       self.system[idx] if len(self.system) else self.system, self.group_e, self.group_j)
+                       self.system[idx] if len(self.system) else self.system, self.group_e, self.group_j,
+                       self.init_by)
 
 
 def diatom_pes_params(jmax=6, n_grid=200, mu_amu=4.0):
@@ -128,8 +130,69 @@ def regular_set(energies_cm, init_js, n_b, b_max, m_avg="one", dt=5.0, r0=30.0) 
                    m_avg=m_avg, group_e=np.array(ge), group_j=np.array(gj, np.int32))
 
 
+@dataclass
+class AsymTopParams:
+    """Atom + rigid asymmetric top: rotor A Ja^2 + B Jb^2 + C Jc^2 (J <= jmax, whole levels kept in
+    ascending energy while N <= max_states); PES sum_t coef_t exp(-beta_t R) f_{lam_t mu_t} with the
+    real angular functions f_{lam mu} (P_lam(cos beta) for mu = 0, 2 d^lam_{0 mu}(beta) cos(mu gamma)
+    otherwise) and the damped -C6 R^-6 dispersion on term 0 = (0, 0)."""
+    jmax: int
+    A: float                 # hartree
+    B: float
+    C: float
+    max_states: int
+    mu: float                # electron masses
+    lam: np.ndarray
+    mproj: np.ndarray
+    coef: np.ndarray         # hartree
+    beta: np.ndarray         # 1/bohr
+    c6: float
+    rd: float = 3.0
+    n_grid: int = 400
+    r_min: float = 2.0
+    r_max: float = 30.0
+
+    @property
+    def n_terms(self) -> int:
+        return len(self.coef)
+
+
+def asym_pes_params(jmax=12, max_states=1600, lam_max=6, n_grid=400, mu_amu=3.3, seed=DEFAULT_SEED):
+    """Rigid asymmetric top with water-like constants A, B, C = 27.88, 14.51, 9.28 cm^-1 and all
+    cos-type terms 0 <= mu <= lam <= lam_max.  The isotropic term is the diatom workloads' repulsive
+    wall 2e5 exp(-1.8 R) cm^-1 with the damped C6 = 3e5 cm^-1 bohr^6 dispersion; the anisotropic
+    coefficients are drawn as coef ~ N(0, (2e4 / (1 + lam))^2) cm^-1 with beta = 1.8 + 0.1 lam."""
+    rng = np.random.default_rng(seed)
+    lam, mproj, coef, beta = [], [], [], []
+    for l in range(lam_max + 1):
+        for m in range(l + 1):
+            lam.append(l)
+            mproj.append(m)
+            coef.append(2e5 if l == 0 else rng.normal(0.0, 2e4 / (1.0 + l)))
+            beta.append(1.8 + 0.1 * l)
+    return AsymTopParams(jmax=jmax, A=float(cm(27.88)), B=float(cm(14.51)), C=float(cm(9.28)),
+                         max_states=max_states, mu=mu_amu * AMU_ME, lam=np.array(lam, np.int32),
+                         mproj=np.array(mproj, np.int32), coef=cm(coef), beta=np.array(beta), c6=float(cm(3e5)),
+                         rd=3.0, n_grid=n_grid, r_min=2.0, r_max=30.0)
+
+
+def mc_set(energies_cm, n_per_e, b_max, seed=DEFAULT_SEED, init_level=0, init_m=0, dt=5.0, r0=30.0) -> TrajSet:
+    """Monte-Carlo impact parameters b ~ U(0, b_max), n_per_e per energy, one group per energy,
+    initial state (level, m) addressed by level index."""
+    rng = np.random.default_rng(seed + 1)
+    ne = len(energies_cm)
+    e = np.repeat(cm(np.asarray(energies_cm, np.float64)), n_per_e)
+    b = rng.uniform(0.0, b_max, ne * n_per_e)
+    g = np.repeat(np.arange(ne, dtype=np.int32), n_per_e)
+    n = ne * n_per_e
+    return TrajSet(e, b, np.full(n, init_level, np.int32), np.full(n, init_m, np.int32), g, ne, r0=r0, r_end=r0,
+                   dt=dt, sampling="mc", b_max=b_max, n_b=n_per_e, m_avg="one",
+                   group_e=cm(np.asarray(energies_cm, np.float64)), group_j=np.full(ne, init_level, np.int32),
+                   init_by="level")
+
+
 # ----------------------------------------------------------------------------
-# The five workloads
+# The workloads
 # ----------------------------------------------------------------------------
 def workload1():
     """N = 49 (j <= 6), E = 500 cm^-1, j' = 0, 32 midpoint b on 0-12 bohr, 200-point grid."""
@@ -148,6 +211,20 @@ def workload2_n1600():
     per (E, j'): 768 trajectories; 400-point grid."""
     return (diatom_pes_params(jmax=39, n_grid=400),
             regular_set([1000.0, 3000.0], [0, 1, 2], n_b=128, b_max=15.0))
+
+
+def workload3(n_per_e=2500, seed=DEFAULT_SEED):
+    """Asymmetric top, J <= 12 truncated to whole levels with N <= 1600 (N = 1580, 110 levels),
+    28 cos-type terms lam <= 6, mu = 3.3 amu; 8 energies log-spaced on 10-2000 cm^-1, n_per_e
+    trajectories per energy with b ~ U(0, 15), initial state the ground level (J = 0)."""
+    energies = np.geomspace(10.0, 2000.0, 8)
+    return asym_pes_params(seed=seed), mc_set(energies, n_per_e, 15.0, seed=seed)
+
+
+def small_asym_workload(jmax=4, max_states=60, lam_max=3, energies=(300.0,), n_per_e=6, b_max=8.0, n_grid=120):
+    """A reduced asymmetric-top case that the oracle finishes in seconds (parity tests)."""
+    return (asym_pes_params(jmax=jmax, max_states=max_states, lam_max=lam_max, n_grid=n_grid),
+            mc_set(list(energies), n_per_e, b_max))
 
 
 def workload5():

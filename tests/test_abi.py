@@ -84,6 +84,64 @@ def test_builder_coupling_matches_oracle(L, ora):
         api.lib().mqct_free_desc(C.byref(d))
 
 
+def build_asym(p, with_params=False, tau=None):
+    ap = api.AsymParams()
+    ap.jmax, ap.A, ap.B, ap.C, ap.max_states, ap.mu = p.jmax, p.A, p.B, p.C, p.max_states, p.mu
+    ap.n_terms = p.n_terms
+    for t in range(p.n_terms):
+        ap.lam[t], ap.mproj[t], ap.coef[t], ap.beta[t] = int(p.lam[t]), int(p.mproj[t]), p.coef[t], p.beta[t]
+    ap.c6, ap.rd, ap.n_grid, ap.r_min, ap.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
+    ap.with_params = int(with_params)
+    ap.tau_out = None if tau is None else tau.ctypes.data
+    d = api.Desc()
+    st = api.lib().mqct_build_asym_top(C.byref(ap), C.byref(d))
+    return st, d, ap
+
+
+def test_asym_builder_matches_oracle_at_full_size(L, ora):
+    """Library: Wang classes by Sturm bisection + inverse iteration, G by quadrature of Wigner d
+    over beta.  Oracle: Jacobi rotations, G by the Eq. 16 closed form.  Same basis order, labels,
+    eigenvector signs and coupling matrices on the N = 1580 workload (28 terms)."""
+    p = inputs.asym_pes_params()
+    tau = np.zeros((p.jmax + 1) ** 2, np.int32)
+    st, d, _ = build_asym(p, tau=tau)
+    assert st == 0
+    lj, lt, le, lb = ora.asym_basis(p.jmax, p.A, p.B, p.C, p.max_states)
+    e2, lev2, jq2, mq2 = ora.asym_states(lj, le)
+    n = d.n_states
+    assert n == len(e2) == 1580
+    arr = lambda ptr, t: np.ctypeslib.as_array(C.cast(ptr, C.POINTER(t)), (n,))
+    assert np.allclose(arr(d.energy, C.c_double), e2, rtol=1e-13, atol=0)
+    assert np.array_equal(arr(d.level, C.c_int32), lev2)
+    assert np.array_equal(arr(d.j, C.c_int32), jq2)
+    assert np.array_equal(arr(d.m, C.c_int32), mq2)
+    assert np.array_equal(tau[: len(lt)], lt)
+    G = dense_G(d)
+    for t in range(p.n_terms):
+        Go = ora.asym_G(lj, lb, p.jmax, int(p.lam[t]), int(p.mproj[t]))
+        assert np.max(np.abs(G[t] - Go)) < 1e-12, (p.lam[t], p.mproj[t])
+    v = np.ctypeslib.as_array(C.cast(d.v, C.POINTER(C.c_double)), (p.n_terms, p.n_grid))
+    v2, _, _, _ = ora.diatom_pes(p.coef, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max)
+    assert np.allclose(v, v2, rtol=1e-14, atol=0)
+    api.lib().mqct_free_desc(C.byref(d))
+
+
+@pytest.mark.parametrize("field,value", [("jmax", 21), ("C", 1.0), ("max_states", 0), ("n_terms", 65)])
+def test_asym_builder_validation(L, field, value):
+    p = inputs.asym_pes_params(jmax=3, max_states=30, lam_max=2)
+    ap_ok = build_asym(p)
+    assert ap_ok[0] == 0
+    api.lib().mqct_free_desc(C.byref(ap_ok[1]))
+    st, d, ap = build_asym(p)
+    api.lib().mqct_free_desc(C.byref(d))
+    setattr(ap, field, value)
+    assert L.mqct_build_asym_top(C.byref(ap), C.byref(d)) == api.ERR_INVALID_ARG
+    ap.jmax, ap.C, ap.max_states, ap.n_terms = p.jmax, p.C, p.max_states, p.n_terms
+    ap.mproj[1] = 2  # mu > lambda = 1
+    assert L.mqct_build_asym_top(C.byref(ap), C.byref(d)) == api.ERR_INVALID_ARG
+    assert b"mu <= lambda" in L.mqct_last_error()
+
+
 def test_builder_pes_matches_oracle(L, ora):
     d, p = build_desc(4, with_params=True, n_grid=60)
     v = np.ctypeslib.as_array(C.cast(d.v, C.POINTER(C.c_double)), (5, 60))
@@ -149,6 +207,9 @@ def test_struct_layouts_match_header(L, tmp_path):
         "mqct_system_info_t": (api.Info, ["n_states", "table_nnz", "device_bytes"]),
         "mqct_diatom_params": (api.DiatomParams, ["jmax", "bconst", "mu", "n_terms", "A", "beta", "c6", "rd",
                                                   "n_grid", "r_min", "with_params", "path", "precision"]),
+        "mqct_asym_params": (api.AsymParams, ["jmax", "A", "B", "C", "max_states", "mu", "n_terms", "lam", "mproj",
+                                              "coef", "beta", "c6", "rd", "n_grid", "r_min", "r_max",
+                                              "with_params", "path", "precision", "tau_out"]),
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mqct.h"', "int main(void) {"]
     for st, (_, fields) in checks.items():
