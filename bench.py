@@ -31,6 +31,8 @@ from paper_2312_02322_gb300 import inputs as W  # noqa: E402
 METRIC = "MQCT trajectory-steps/s at N=441/1600, batched mixed vs plain FP64, same error"
 WORKLOAD = "diatom j<=20 (N=441), 3072 trajectories: E in {100,300,1000,3000} cm^-1 x j' in {0,1,2} x 256 b on 0-15 bohr"
 WORKLOAD_1600 = "diatom j<=39 (N=1600), 768 trajectories: E in {1000,3000} cm^-1 x j' in {0,1,2} x 128 b on 0-15 bohr"
+WORKLOAD_ASYM = ("asymmetric top A,B,C = 27.88,14.51,9.28 cm^-1, J<=12 truncated to N=1580 (110 levels), 28 terms "
+                 "lam<=6, 8 E log-spaced 10-2000 cm^-1, b ~ U(0,15), initial level J=0")
 
 
 def parse():
@@ -49,8 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-traj", type=int, default=0,
                     help="run a seeded subset of this many trajectories (profiling of a small case)")
-    ap.add_argument("--workload", default="n441", choices=["n441", "n1600"],
-                    help="n441: the 3072-trajectory N = 441 workload; n1600: 768 trajectories with N = 1600")
+    ap.add_argument("--workload", default="n441", choices=["n441", "n1600", "asym1580"],
+                    help="n441: the 3072-trajectory N = 441 workload; n1600: 768 trajectories with N = 1600; "
+                         "asym1580: the N = 1580 asymmetric-top workload (a seeded subset, --max-traj, default 1024)")
     ap.add_argument("--energy", type=float, default=0.0,
                     help="keep only the trajectories at this collision energy (cm^-1)")
     return ap.parse_args()
@@ -64,22 +67,38 @@ def dist_env():
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def oracle_sample(p, ts, n_sample, seed=11):
-    """Bounded, seeded sample of the workload: n_sample trajectories stratified over the
-    collision energies (the step count per trajectory depends mostly on E)."""
+def strat_idx(ts, n_sample, seed):
+    """Seeded indices of n_sample trajectories stratified over the collision energies (the step
+    count per trajectory depends mostly on E)."""
     rng = np.random.default_rng(seed)
     es = np.unique(ts.e_coll)
     per = max(1, n_sample // len(es))
-    pick = np.concatenate([rng.choice(np.flatnonzero(ts.e_coll == e), per, replace=False) for e in es])
-    return ts.subset(np.sort(pick))
+    return np.sort(np.concatenate([rng.choice(np.flatnonzero(ts.e_coll == e), min(per, int(np.sum(ts.e_coll == e))),
+                                              replace=False) for e in es]))
+
+
+def oracle_sample(p, ts, n_sample, seed=11):
+    """Bounded, seeded sample of the workload (see strat_idx)."""
+    return ts.subset(strat_idx(ts, n_sample, seed))
+
+
+def make_system(api, p, path, precision):
+    if isinstance(p, W.AsymTopParams):
+        return api.System.asym_top(p, path=path, precision=precision)
+    return api.System.diatom(p, path=path, precision=precision)
 
 
 def run_oracle(p, sub, threads):
     import oracle
 
     oracle.build()
-    osys = oracle.diatom_system(p.jmax, p.bconst, p.mu, p.A, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max)
-    init = [j * j + j + m for j, m in zip(sub.init_j, sub.init_m)]
+    if isinstance(p, W.AsymTopParams):
+        osys = oracle.asym_system(p)
+        lab = {(int(l), int(m)): i for i, (l, m) in enumerate(zip(osys.level, osys.mq))}
+        init = [lab[(int(l), int(m))] for l, m in zip(sub.init_j, sub.init_m)]
+    else:
+        osys = oracle.diatom_system(p.jmax, p.bconst, p.mu, p.A, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max)
+        init = [j * j + j + m for j, m in zip(sub.init_j, sub.init_m)]
     t0 = time.perf_counter()
     amp, res = oracle.propagate(osys, sub.e_coll, sub.b, init, r0=sub.r0, r_end=sub.r_end, dt=sub.dt,
                                 max_steps=sub.max_steps, n_threads=threads)
@@ -189,15 +208,21 @@ def gpu_arm(args):
     build.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    p, ts = W.workload2() if args.workload == "n441" else W.workload2_n1600()
-    workload = WORKLOAD if args.workload == "n441" else WORKLOAD_1600
+    if args.workload == "asym1580":
+        p, ts = W.workload3()
+        workload = WORKLOAD_ASYM
+        if not args.max_traj:
+            args.max_traj = 1024
+    else:
+        p, ts = W.workload2() if args.workload == "n441" else W.workload2_n1600()
+        workload = WORKLOAD if args.workload == "n441" else WORKLOAD_1600
     if args.energy:
         ts = ts.subset(np.flatnonzero(np.isclose(ts.e_coll, float(W.cm(args.energy)))))
-        workload = f"E = {args.energy} cm^-1 part of: {WORKLOAD}"
+        workload = f"E = {args.energy} cm^-1 part of: {workload}"
     if args.max_traj:
         ts = oracle_sample(p, ts, args.max_traj, seed=5)
         workload = f"seeded subset of {ts.n} trajectories of: {workload}"
-    sys_ = api.System.diatom(p, path=args.path, precision=args.precision)
+    sys_ = make_system(api, p, args.path, args.precision)
     info = sys_.info
     tr = api.make_trajs(ts, sys_)
     trd = torch.from_numpy(tr.view(np.uint8).copy()).to(dev)
@@ -247,7 +272,7 @@ def gpu_arm(args):
         flops_stage = 16.0 * info["table_nnz"] + 40.0 * n
         bytes_stage = 32.0 * info["table_nnz"] * (1.0 if args.precision == "fp64" else 0.5)
     else:
-        flops_stage = 4.0 * info["glambda_nnz"] + (8.0 * p.n_terms + 40.0) * n
+        flops_stage = 4.0 * info["glambda_nnz"] + (8.0 * info["n_terms"] + 40.0) * n
         bytes_stage = 0.0
     fp64_peak = api.fma_rate("fp64") if args.precision == "fp64" else api.fma_rate("fp32")
     achieved = flops_stage * stages / (k_ms * 1e-3) / 1e12
@@ -262,16 +287,14 @@ def gpu_arm(args):
     except Exception:
         peaks, hbm = {}, None
     if args.precision == "bf16x3":
-        # executed tensor work: per stage, per row tile and 64-slot tile, (w, u) x stored terms x
-        # 3 split products x 8 K steps of a 128 x 128 x 16 MMA; time = the whole propagate call
-        # (contraction, element update and slot kernels), so the fraction is a lower bound
-        n_f = sum(1 for l in range(p.n_terms) if l > 0)
-        tiles = int(np.ceil(n / 128.0))
-        exec_stage = tiles * n_f * 2 * 3 * 8 * (2.0 * 128 * 128 * 16) / 64.0
+        # executed tensor work: per stage, per 64-slot tile, for every stored term and row tile its
+        # non-zero 16-column K chunks x 3 split products of a 128 x 128 x 16 MMA; time = the whole
+        # propagate call (contraction, element update and slot kernels): a lower bound
+        exec_stage = info["tc_kchunks"] * 3 * (2.0 * 128 * 128 * 16) / 64.0
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         ach = exec_stage * stages / (k_ms * 1e-3) / 1e12
         roofline = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                    "traffic": None, "kernel": "k_tc_contract (timed with the whole propagate call)",
+                    "traffic": None, "kernel": "k_tc_stage (timed with the whole propagate call)",
                     "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
                     "executed_flops_per_traj_stage": exec_stage, "useful_flops_per_traj_stage": flops_stage,
                     "useful_over_executed": flops_stage / exec_stage, "traj_stages_per_launch": stages,
@@ -304,20 +327,24 @@ def gpu_arm(args):
     # difference of the measured path against it over every trajectory ("same error")
     compare = None
     if not args.no_compare and not (args.path == "plain" and args.precision == "fp64"):
-        pop_m = pop.cpu().numpy()
-        s64 = api.System.diatom(p, path="plain", precision="fp64")
+        # the asymmetric-top plain FP64 run is long (one CTA per trajectory at N = 1580): it is
+        # timed on a stratified 128-trajectory part of the batch
+        cidx = strat_idx(ts, 128, seed=9) if args.workload == "asym1580" else np.arange(ts.n)
+        pop_m = pop.cpu().numpy()[cidx]
+        s64 = make_system(api, p, "plain", "fp64")
+        trc = torch.from_numpy(tr[cidx].view(np.uint8).copy()).to(dev)
         flush.zero_()
         a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a_.record(stream)
-        pop64, _, d64 = api.propagate(s64, trd, device=True, stream=stream)
+        pop64, _, d64 = api.propagate(s64, trc, device=True, stream=stream)
         b_.record(stream)
         torch.cuda.synchronize()
         ms64 = a_.elapsed_time(b_)
         d64 = api.diag_to_numpy(d64)
-        same = d64["steps"] == dg["steps"]
+        same = d64["steps"] == dg["steps"][cidx]
         dp = np.abs(pop_m - pop64.cpu().numpy()[:, :pop_m.shape[1]])
         compare = {"path": "plain", "precision": "fp64", "value": float(d64["steps"].sum()) * ws / (ms64 * 1e-3),
-                   "unit": "traj-steps/s", "ms": ms64, "timed_runs": 1,
+                   "unit": "traj-steps/s", "ms": ms64, "timed_runs": 1, "trajectories": int(len(cidx)),
                    "max_abs_dP_vs_fp64": float(dp.max()), "max_abs_dP_same_steps": float(dp[same].max()),
                    "trajectories_same_steps": int(same.sum()),
                    "speedup": value / (float(d64["steps"].sum()) * ws / (ms64 * 1e-3))}
@@ -345,10 +372,14 @@ def gpu_arm(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         sub = oracle_sample(p, ts, 16)
+        what = f"{sub.n} trajectories of the workload (stratified over the collision energies, seeded)"
+        if args.workload == "asym1580":
+            sub.max_steps = 400  # the oracle takes ~10 ms per step at N = 1580: the first 400 steps of each
+            what += ", first 400 RK4 steps of each"
         cores = cpu_cores()
         s, t = run_oracle(p, sub, cores)
         cpu = {"value": s / t, "unit": "traj-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{sub.n} trajectories of the workload (4 per collision energy, seeded), {int(s)} traj-steps"}
+               "sample": f"{what}, {int(s)} traj-steps"}
     if dist:
         dist.destroy_process_group()
     if rank != 0:

@@ -142,6 +142,9 @@ typedef struct {
     int64_t table_bytes;      /* PLAIN: device bytes of the spline table                 */
     int64_t glambda_nnz;      /* FACTORISED: sum over lambda of non-zero G^lambda entries */
     int64_t device_bytes;     /* all device memory the system owns                        */
+    int32_t n_coupling_terms; /* FACTORISED: terms stored as matrices (identity terms are not) */
+    int32_t n_row_tiles;      /* BF16X3: 128-row tiles of whole m-blocks                   */
+    int64_t tc_kchunks;       /* BF16X3: non-zero 16-column K chunks over terms and tiles  */
 } mqct_system_info_t;
 
 /* Parameters of the built-in atom + linear rotor system (helper for users and tests):

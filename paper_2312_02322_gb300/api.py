@@ -49,7 +49,8 @@ class Info(C.Structure):
     _fields_ = [("n_states", C.c_int32), ("n_levels", C.c_int32), ("n_terms", C.c_int32), ("n_grid", C.c_int32),
                 ("n_blocks", C.c_int32), ("max_block", C.c_int32), ("path", C.c_int32), ("precision", C.c_int32),
                 ("table_nnz", C.c_int64), ("table_bytes", C.c_int64), ("glambda_nnz", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("n_coupling_terms", C.c_int32), ("n_row_tiles", C.c_int32),
+                ("tc_kchunks", C.c_int64)]
 
 
 class DiatomParams(C.Structure):

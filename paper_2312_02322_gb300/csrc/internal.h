@@ -70,6 +70,7 @@ struct DevSys {
     int n_tiles;
     const int *tile_r0;        // [n_tiles + 1] first row of each tile
     const uint16_t *g_tiles;   // [n_f][n_tiles][2][128 * 128]
+    const uint8_t *g_kmask;    // [n_f][n_tiles] bit ks set: K columns 16 ks .. 16 ks + 15 hold a non-zero
 };
 
 struct System {

@@ -457,7 +457,8 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
             t0.push_back(t0.back() + rows);
             const int nt = (int)t0.size() - 1;
             // block-diagonal 128 x 128 tiles, BF16 hi/lo split, canonical K-major MMA layout:
-            // element (r, k) at byte (r/8)*2048 + (k/8)*128 + (r%8)*16 + (k%8)*2
+            // element (r, k) at byte (r/8)*2048 + (k/8)*128 + (r%8)*16 + (k%8)*2; per tile the
+            // mask of its 16-column K chunks that hold a non-zero (the others are skipped)
             auto bf16_bits = [](float x) -> uint16_t {
                 uint32_t u;
                 std::memcpy(&u, &x, 4);
@@ -471,26 +472,34 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
                 return x;
             };
             std::vector<uint16_t> tiles((size_t)fterm.size() * nt * 2 * 16384, 0);
+            std::vector<uint8_t> kmask((size_t)fterm.size() * nt, 0);
             for (size_t f = 0; f < fterm.size(); ++f) {
                 const int l = fterm[f];
                 for (int t = 0; t < nt; ++t) {
                     uint16_t *hi = tiles.data() + (((size_t)f * nt + t) * 2) * 16384, *lo = hi + 16384;
+                    uint8_t &km = kmask[(size_t)f * nt + t];
                     for (int r = t0[t]; r < t0[t + 1]; ++r)
                         for (auto &e : grows[l][r]) {
                             const int rr = r - t0[t], kk = e.c - t0[t];
+                            km |= (uint8_t)(1u << (kk >> 4));
                             const float v = (float)e.v;
                             const uint16_t h = bf16_bits(v);
                             const size_t off = ((size_t)(rr >> 3) * 2048 + (size_t)(kk >> 3) * 128 + (rr & 7) * 16 + (kk & 7) * 2) / 2;
                             hi[off] = h;
                             lo[off] = bf16_bits(v - bf16_val(h));
                         }
+                    if (!km) km = 1;  // an all-zero tile still writes its (zero) product
+                    S.info.tc_kchunks += __builtin_popcount(km);
                 }
             }
             D.n_tiles = nt;
             up_(t0, &D.tile_r0);
             up_(tiles, &D.g_tiles);
+            up_(kmask, &D.g_kmask);
         }
         S.info.glambda_nnz = gnnz;
+        S.info.n_coupling_terms = D.n_f;
+        S.info.n_row_tiles = D.n_tiles;
     }
     if (st == MQCT_OK) {
         cudaError_t e = cudaMalloc(&S.d, sizeof(DevSys));

@@ -2,18 +2,16 @@
 //
 // All trajectories in flight form one N x S block of amplitudes in global memory (S slots,
 // one column per trajectory; finished slots are refilled from the device work queue).  Every
-// RK4 stage runs three kernels:
-//   k_tc_contract  tcgen05 GEMMs: for every row tile (packed m-blocks, <= 128 rows) and tile of
-//                  64 slots (128 real columns = Re, Im), the two accumulators
-//                      w = sum_l G^l (v_l(R_b) c_b)    u = sum_l G^l (v_l'(R_b) c_b)
-//                  (Eq. 12 with the spline values folded into the B operand) are built in tensor
-//                  memory from BF16 hi/lo splits, three MMAs per K step (hi.hi + hi.lo + lo.hi),
-//                  FP32 accumulation; identity terms are added in the epilogue;
-//   k_tc_update    per element: Coriolis stencil, derivative da/dt = -i exp(iEt) w +
-//                  (dPhi/dt/2) exp(iEt) D c (Eq. 5), compensated RK4 accumulation, next stage
-//                  input; per-slot partial sums of force, torque and (stage 0) diagnostics;
-//   k_tc_slots     one thread per slot, FP64: classical stage update (Eqs. 7-10), bookkeeping,
-//                  stop rule, refill, the spline values and phase factors of the next stage.
+// RK4 stage runs two kernels:
+//   k_tc_stage  one CTA per row tile (packed m-blocks, <= 128 rows) and tile of 64 slots (128
+//               real columns = Re, Im): tcgen05 GEMMs Y_l = G^l C from BF16 hi/lo splits (three
+//               MMAs per K chunk: hi.hi + hi.lo + lo.hi, FP32 accumulation in tensor memory),
+//               folded per slot into w = sum_l v_l(R_b) Y_l and u = sum_l v_l'(R_b) Y_l (Eq. 12);
+//               then per element the Coriolis stencil, da/dt = -i exp(iEt) w + (dPhi/dt/2)
+//               exp(iEt) D c (Eq. 5), the compensated RK4 accumulation and the next stage input,
+//               with per-slot partial sums of force, torque and (stage 0) diagnostics;
+//   k_tc_slots  one warp per slot, FP64: classical stage update (Eqs. 7-10), bookkeeping, stop
+//               rule, refill, the spline values and phase factors of the next stage.
 // The host runs chunks of steps as one CUDA graph and checks the number of live slots between
 // chunks.
 #include <cuda_bf16.h>
@@ -21,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -32,7 +31,6 @@ namespace mqct {
 namespace {
 
 constexpr int kTcSlotsPerTile = 64;  // 128 real columns
-constexpr int kTcRows = 8;           // rows per k_tc_update block (x 32 slots)
 constexpr long long kTcWait = 1ll << 24;
 
 enum { TS_IDLE = 0, TS_ACTIVE = 1, TS_FINAL = 2, TS_WAIT = 3 };
@@ -55,13 +53,12 @@ struct TcState {
     int nmax;
     float2 *C[2];             // [n][S] stage amplitudes (phase rotated), double buffered
     float2 *A, *ACC;          // [n][S]
-    float2 *W, *U;            // [n][S] contraction results
     float *coef;              // [2][L][S] v_l and v_l' at each slot's stage R
     float *vid;               // [2][S] identity-term sums of v and v'
     float *hp, *dtf;          // [S] dPhi/dt / 2 and dt (FP32 views)
     int *state;               // [S]
     float2 *PHa, *PHb;        // [n_levels][S]
-    double *part;             // [n_rowblocks][S][6]
+    double *part;             // [n_tiles][S][6] per-row-tile partial sums
     TSlot *slot;              // [S]
 };
 
@@ -81,139 +78,10 @@ __device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_usho
 __device__ __forceinline__ float bf16_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
 // ---------------------------------------------------------------------------------------------
-// contraction: one CTA per (row tile, slot tile), 4 warps; one thread issues the MMAs
-__global__ void __launch_bounds__(128) k_tc_contract(TcState T, int cur)
-{
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tmem_base;
-    __shared__ int any_live;
-    const DevSys &S = *T.sys;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = S.n_tiles;
-    const int rt = blockIdx.x % nt, ct = blockIdx.x / nt;
-    const int r0 = S.tile_r0[rt], R = S.tile_r0[rt + 1] - r0;
-    const int s0 = ct * kTcSlotsPerTile;
-    if (tid == 0) any_live = 0;
-    __syncthreads();
-    if (tid < kTcSlotsPerTile && s0 + tid < T.S) {
-        const int st = T.state[s0 + tid];
-        if (st == TS_ACTIVE || st == TS_FINAL) any_live = 1;
-    }
-    __syncthreads();
-    if (!any_live) return;
-    // shared memory: C tile FP32 [128][64] complex (64 KB), B operand hi/lo (2 x 32 KB),
-    // A operand hi/lo (2 x 32 KB)
-    float2 *Ct = reinterpret_cast<float2 *>(sm);
-    unsigned char *Bhi = sm + 65536, *Blo = Bhi + 32768, *Ahi = Blo + 32768, *Alo = Ahi + 32768;
-    const float2 *Cg = T.C[cur];
-    for (int i = tid; i < 128 * kTcSlotsPerTile; i += blockDim.x) {
-        const int k = i / kTcSlotsPerTile, j = i % kTcSlotsPerTile;
-        float2 v = make_float2(0.f, 0.f);
-        if (k < R && s0 + j < T.S) v = Cg[(size_t)(r0 + k) * T.S + s0 + j];
-        Ct[i] = v;
-    }
-    if (warp == 0) {
-        tc_tmem_alloc(&tmem_base, 256);
-        tc_tmem_relinquish();
-    }
-    if (tid == 0) tc_mbar_init(&mbar, 1);
-    __syncthreads();
-    tc_fence_after_sync();
-    const uint32_t tw = tmem_base, tu = tmem_base + 128;
-    const uint32_t idesc = tc_idesc_bf16_f32(128, 128);
-    uint32_t phase = 0;
-    bool ok = true, first_w = true, first_u = true;
-    for (int f = 0; f < S.n_f && ok; ++f) {
-        const int l = S.f_term[f];
-        // A operand: the G^l tile (hi, lo), 16-byte copies
-        const uint4 *src = reinterpret_cast<const uint4 *>(S.g_tiles + ((size_t)f * nt + rt) * 2 * 16384);
-        uint4 *dst = reinterpret_cast<uint4 *>(Ahi);
-        for (int i = tid; i < 2 * 32768 / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-        for (int which = 0; which < 2 && ok; ++which) {
-            const float *cf = T.coef + ((size_t)which * S.L + l) * T.S + s0;
-            // B operand: real column n = 2j + (Re, Im) of slot j, K = row k; coef_l(slot) * c
-            for (int i = tid; i < 128 * 128; i += blockDim.x) {
-                const int k = i / 128, nn = i % 128, j = nn >> 1;
-                const float2 c = Ct[k * kTcSlotsPerTile + j];
-                const float cv = (s0 + j < T.S) ? cf[j] : 0.f;
-                const float x = cv * ((nn & 1) ? c.y : c.x);
-                const uint16_t h = bf16_rn(x);
-                const uint16_t lo = bf16_rn(x - bf16_f(h));
-                const uint32_t off = tc_kmajor_offset(nn, k, 16);
-                *reinterpret_cast<uint16_t *>(Bhi + off) = h;
-                *reinterpret_cast<uint16_t *>(Blo + off) = lo;
-            }
-            tc_fence_proxy_async();
-            __syncthreads();
-            tc_fence_after_sync();
-            if (tid == 0) {
-                const uint32_t acc = which ? tu : tw;
-                bool fst = which ? first_u : first_w;
-                const uint32_t a_hi = tc_smem_addr(Ahi), a_lo = tc_smem_addr(Alo);
-                const uint32_t b_hi = tc_smem_addr(Bhi), b_lo = tc_smem_addr(Blo);
-                for (int ks = 0; ks < 8; ++ks) {
-                    const uint32_t o = ks * 256;
-                    tc_mma_bf16(acc, tc_sdesc(a_hi + o, 128, 2048), tc_sdesc(b_hi + o, 128, 2048), idesc, !fst);
-                    tc_mma_bf16(acc, tc_sdesc(a_hi + o, 128, 2048), tc_sdesc(b_lo + o, 128, 2048), idesc, true);
-                    tc_mma_bf16(acc, tc_sdesc(a_lo + o, 128, 2048), tc_sdesc(b_hi + o, 128, 2048), idesc, true);
-                    fst = false;
-                }
-                tc_commit(&mbar);
-            }
-            if (which) first_u = false; else first_w = false;
-            // the B buffers are rewritten next: wait for these MMAs
-            ok = tc_mbar_wait(&mbar, phase, kTcWait);
-            phase ^= 1u;
-            tc_fence_after_sync();
-            __syncthreads();
-        }
-    }
-    // epilogue: lane = row of the tile; identity terms added from the FP32 tile
-    if (ok && !first_w) {
-        const int row = warp * 32 + lane;
-        const float *vi = T.vid + s0, *dvi = T.vid + T.S + s0;
-        for (int c = 0; c < 128; c += 8) {
-            float vw[8], vu[8];
-            tc_ld_32x32b_x8(tw + ((uint32_t)(warp * 32) << 16) + c, vw);
-            tc_ld_32x32b_x8(tu + ((uint32_t)(warp * 32) << 16) + c, vu);
-            tc_wait_ld();
-            if (row < R)
-                for (int q = 0; q < 4; ++q) {
-                    const int j = c / 2 + q;
-                    if (s0 + j >= T.S) continue;
-                    const float2 cc = Ct[row * kTcSlotsPerTile + j];
-                    const size_t o = (size_t)(r0 + row) * T.S + s0 + j;
-                    T.W[o] = make_float2(vw[2 * q] + vi[j] * cc.x, vw[2 * q + 1] + vi[j] * cc.y);
-                    T.U[o] = make_float2(vu[2 * q] + dvi[j] * cc.x, vu[2 * q + 1] + dvi[j] * cc.y);
-                }
-        }
-    } else if (!ok && tid == 0) {
-        atomicOr(T.live + 1, 1);  // error flag: a bounded wait ran out
-    }
-    tc_fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc_tmem_dealloc(tmem_base, 256);
-}
-
-// contraction for systems whose terms are all identities (no stored G): w = v_id c, u = v'_id c
-__global__ void k_tc_identity(TcState T, int cur)
-{
-    const DevSys &S = *T.sys;
-    const size_t tot = (size_t)S.n * T.S;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-        const int s = (int)(i % T.S);
-        const float2 c = T.C[cur][i];
-        T.W[i] = make_float2(T.vid[s] * c.x, T.vid[s] * c.y);
-        T.U[i] = make_float2(T.vid[T.S + s] * c.x, T.vid[T.S + s] * c.y);
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
 // the update of one element (row r, slot sl) from w = M c and u = M' c (Eq. 5, RK4); adds its
 // force, torque and (stage 0) diagnostic contributions to part[6]
 __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s, int cur, int r, int sl, int st,
-                                        float2 w, float2 u, double *part)
+                                        float2 c, float2 w, float2 u, double *part)
 {
     const int nxt = cur ^ 1;
     const size_t e = (size_t)r * T.S + sl;
@@ -228,7 +96,6 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
     }
     if (st != TS_ACTIVE && st != TS_FINAL) return;
     const float2 *Cc = T.C[cur];
-    const float2 c = Cc[e];
     const float au = S.aupf[r], ad = S.adnf[r];
     const float2 cu = Cc[(size_t)S.up[r] * T.S + sl], cd = Cc[(size_t)S.dn[r] * T.S + sl];
     const float2 dc = make_float2(ad * cd.x - au * cu.x, ad * cd.y - au * cu.y);
@@ -287,27 +154,223 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
     }
 }
 
-// element update after k_tc_contract: block = kTcRows rows x 32 slots
-__global__ void __launch_bounds__(256) k_tc_update(TcState T, int s, int cur)
+// ---------------------------------------------------------------------------------------------
+// one RK4 stage of every element: one CTA per (row tile, 64-slot tile).
+//  - B operand: the tile's phase-rotated amplitudes as BF16 hi/lo, built once;
+//  - the G^l tiles (BF16 hi/lo) stream through a two-deep shared-memory ring by bulk TMA copies
+//    (warp 17); warp 16 issues, per term, the MMAs of the non-zero K chunks (three per chunk:
+//    hi.hi + hi.lo + lo.hi) into one of two TMEM accumulators, Y_l = G^l C;
+//  - sixteen epilogue warps (four per TMEM lane quadrant, 32 columns each) fold each term into
+//    w += v_l Y_l and u += v_l' Y_l with the per-slot spline weights (Eq. 12), in registers;
+//  - the element update of Eq. 5 and RK4 (tc_elem) runs on the staged w, u with the identity
+//    terms added, and the per-slot partial sums of force, torque and diagnostics over the
+//    tile's rows go to part[row tile][slot].
+constexpr int kTcEpiWarps = 16;
+constexpr int kTcMmaWarp = kTcEpiWarps, kTcLoadWarp = kTcEpiWarps + 1;
+constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);
+constexpr uint32_t kTcTileBytes = 2u * 128u * 128u * 2u;  // a G tile or the B operand, hi + lo
+constexpr size_t kTcSmemFixed = 3 * (size_t)kTcTileBytes;  // A ring (2) + B operand
+constexpr int kTcWs = kTcSlotsPerTile + 1;                  // padded row of the staged w, u
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, int cur)
 {
-    __shared__ double red[kTcRows][32][6];
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t bar_full[2], bar_mma[2], bar_epi[2], bar_drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int any_live, err;
     const DevSys &S = *T.sys;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int sl = blockIdx.x * 32 + tx, r = blockIdx.y * kTcRows + ty;
-    double part[6] = {0, 0, 0, 0, 0, 0};
-    if (sl < T.S && r < S.n) {
-        const size_t e = (size_t)r * T.S + sl;
-        tc_elem(T, S, s, cur, r, sl, T.state[sl], T.W[e], T.U[e], part);
-    }
-    for (int q = 0; q < 6; ++q) red[ty][tx][q] = part[q];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nt = S.n_tiles, nf = S.n_f;
+    const int rt = blockIdx.x % nt, ct = blockIdx.x / nt;
+    const int r0 = S.tile_r0[rt], R = S.tile_r0[rt + 1] - r0;
+    const int s0 = ct * kTcSlotsPerTile;
+    if (tid == 0) { any_live = 0; err = 0; }
     __syncthreads();
-    if (ty == 0 && sl < T.S) {
-        double acc6[6] = {0, 0, 0, 0, 0, 0};
-        for (int y = 0; y < kTcRows; ++y)
-            for (int q = 0; q < 6; ++q) acc6[q] += red[y][tx][q];
-        double *o = T.part + ((size_t)blockIdx.y * T.S + sl) * 6;
-        for (int q = 0; q < 6; ++q) o[q] = acc6[q];
+    if (tid < kTcSlotsPerTile) {
+        const int st = T.state[s0 + tid];
+        if (st != TS_IDLE) any_live = 1;
     }
+    __syncthreads();
+    if (!any_live) return;
+    unsigned char *Aring = sm, *Bop = sm + 2 * kTcTileBytes;
+    float *s_v = reinterpret_cast<float *>(sm + kTcSmemFixed), *s_dv = s_v + nf * kTcSlotsPerTile;
+    const float2 *Cg = T.C[cur];
+    // per-term spline weights of the tile's slots
+    for (int i = tid; i < nf * kTcSlotsPerTile; i += kTcThreads) {
+        const int f = i / kTcSlotsPerTile, j = i % kTcSlotsPerTile, l = S.f_term[f];
+        s_v[i] = T.coef[(size_t)l * T.S + s0 + j];
+        s_dv[i] = T.coef[((size_t)S.L + l) * T.S + s0 + j];
+    }
+    // B operand: real column n = 2j + (Re, Im) of slot j, K = row k of the tile; 8 rows of one
+    // slot per task, written as 16-byte core-matrix rows
+    for (int task = tid; task < kTcSlotsPerTile * 16; task += kTcThreads) {
+        const int j = task % kTcSlotsPerTile, o = task / kTcSlotsPerTile;
+        uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+            const int k = 8 * o + i;
+            if (k < R) c0 = Cg[(size_t)(r0 + k) * T.S + s0 + j];
+            if (k + 1 < R) c1 = Cg[(size_t)(r0 + k + 1) * T.S + s0 + j];
+            const uint16_t h0 = bf16_rn(c0.x), h1 = bf16_rn(c1.x), g0 = bf16_rn(c0.y), g1 = bf16_rn(c1.y);
+            rh[i / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            ih[i / 2] = (uint32_t)g0 | ((uint32_t)g1 << 16);
+            rl[i / 2] = (uint32_t)bf16_rn(c0.x - bf16_f(h0)) | ((uint32_t)bf16_rn(c1.x - bf16_f(h1)) << 16);
+            il[i / 2] = (uint32_t)bf16_rn(c0.y - bf16_f(g0)) | ((uint32_t)bf16_rn(c1.y - bf16_f(g1)) << 16);
+        }
+        const uint32_t ore = tc_kmajor_offset(2 * j, 8 * o, 16), oim = tc_kmajor_offset(2 * j + 1, 8 * o, 16);
+        *reinterpret_cast<uint4 *>(Bop + ore) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<uint4 *>(Bop + kTcTileBytes / 2 + ore) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+        *reinterpret_cast<uint4 *>(Bop + oim) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+        *reinterpret_cast<uint4 *>(Bop + kTcTileBytes / 2 + oim) = make_uint4(il[0], il[1], il[2], il[3]);
+    }
+    if (warp == kTcMmaWarp) {
+        tc_tmem_alloc(&tmem_base, 256);
+        tc_tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            tc_mbar_init(&bar_full[b], 1);
+            tc_mbar_init(&bar_mma[b], 1);
+            tc_mbar_init(&bar_epi[b], kTcEpiWarps);
+        }
+        tc_mbar_init(&bar_drain, 1);
+    }
+    tc_fence_proxy_async();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    float w[32], u[32];
+    if (warp == kTcLoadWarp) {
+        // ---- bulk copies of the G tiles into the ring (lane 0); slot f & 1 is free once the
+        // MMAs of term f - 2 completed
+        if (lane == 0) {
+            const unsigned char *gt = reinterpret_cast<const unsigned char *>(S.g_tiles);
+            int f = 0;
+            for (; f < nf; ++f) {
+                const int b = f & 1;
+                if (f >= 2 && !tc_mbar_wait(&bar_mma[b], ((f - 2) >> 1) & 1, kTcWait)) {
+                    err = 1;
+                    break;
+                }
+                tc_mbar_expect_tx(&bar_full[b], kTcTileBytes);
+                tc_bulk_g2s(Aring + b * kTcTileBytes, gt + ((size_t)f * nt + rt) * kTcTileBytes, kTcTileBytes,
+                            &bar_full[b]);
+            }
+            // before the buffers are released: the last copies issued have landed
+            for (int k = f - 1; k >= 0 && k >= f - 2; --k) tc_mbar_wait(&bar_full[k & 1], (k >> 1) & 1, kTcWait);
+        }
+    } else if (warp == kTcMmaWarp) {
+        // ---- MMA issue (lane 0)
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc_bf16_f32(128, 128);
+            const uint32_t b_hi = tc_smem_addr(Bop), b_lo = b_hi + kTcTileBytes / 2;
+            for (int f = 0; f < nf; ++f) {
+                const int b = f & 1;
+                bool ok = tc_mbar_wait(&bar_full[b], (f >> 1) & 1, kTcWait);
+                if (ok && f >= 2) ok = tc_mbar_wait(&bar_epi[b], ((f - 2) >> 1) & 1, kTcWait);
+                if (!ok) {
+                    // the MMAs already issued complete before the accumulators are released
+                    err = 1;
+                    tc_commit(&bar_drain);
+                    tc_mbar_wait(&bar_drain, 0, kTcWait);
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint32_t a_hi = tc_smem_addr(Aring + b * kTcTileBytes), a_lo = a_hi + kTcTileBytes / 2;
+                const uint32_t d = tbase + 128u * b;
+                const uint32_t km = S.g_kmask[(size_t)f * nt + rt];
+                bool acc = false;
+                for (int ks = 0; ks < 8; ++ks) {
+                    if (!((km >> ks) & 1u)) continue;
+                    const uint32_t o = ks * 256;
+                    tc_mma_bf16(d, tc_sdesc(a_hi + o, 128, 2048), tc_sdesc(b_hi + o, 128, 2048), idesc, acc);
+                    tc_mma_bf16(d, tc_sdesc(a_hi + o, 128, 2048), tc_sdesc(b_lo + o, 128, 2048), idesc, true);
+                    tc_mma_bf16(d, tc_sdesc(a_lo + o, 128, 2048), tc_sdesc(b_hi + o, 128, 2048), idesc, true);
+                    acc = true;
+                }
+                tc_commit(&bar_mma[b]);
+            }
+        }
+    } else {
+        // ---- epilogue warps: lanes of quadrant warp % 4, columns 32 * (warp / 4) .. + 31
+        const int q = warp & 3, hcol = 32 * (warp >> 2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) { w[i] = 0.f; u[i] = 0.f; }
+        for (int f = 0; f < nf; ++f) {
+            const int b = f & 1;
+            if (!tc_mbar_wait(&bar_mma[b], (f >> 1) & 1, kTcWait)) { err = 1; break; }
+            tc_fence_after_sync();
+            const float *vf = s_v + f * kTcSlotsPerTile + hcol / 2, *dvf = s_dv + f * kTcSlotsPerTile + hcol / 2;
+            const uint32_t ta = tbase + 128u * b + ((uint32_t)(32 * q) << 16) + hcol;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t d[16];
+                tc_ld16_raw(ta + 16 * hh, d);
+                tc_wait_ld_16(d);
+#pragma unroll
+                for (int c = 0; c < 16; c += 4) {
+                    const float2 v2 = *reinterpret_cast<const float2 *>(vf + 8 * hh + (c >> 1));
+                    const float2 dv2 = *reinterpret_cast<const float2 *>(dvf + 8 * hh + (c >> 1));
+                    const int o = 16 * hh + c;
+                    w[o] = fmaf(v2.x, __uint_as_float(d[c]), w[o]);
+                    w[o + 1] = fmaf(v2.x, __uint_as_float(d[c + 1]), w[o + 1]);
+                    w[o + 2] = fmaf(v2.y, __uint_as_float(d[c + 2]), w[o + 2]);
+                    w[o + 3] = fmaf(v2.y, __uint_as_float(d[c + 3]), w[o + 3]);
+                    u[o] = fmaf(dv2.x, __uint_as_float(d[c]), u[o]);
+                    u[o + 1] = fmaf(dv2.x, __uint_as_float(d[c + 1]), u[o + 1]);
+                    u[o + 2] = fmaf(dv2.y, __uint_as_float(d[c + 2]), u[o + 2]);
+                    u[o + 3] = fmaf(dv2.y, __uint_as_float(d[c + 3]), u[o + 3]);
+                }
+            }
+            tc_fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc_mbar_arrive(&bar_epi[b]);
+        }
+    }
+    __syncthreads();
+    // stage w and u through shared memory (the ring and B buffers are free now)
+    float2 *Wst = reinterpret_cast<float2 *>(sm), *Ust = Wst + 128 * kTcWs;
+    double *red = reinterpret_cast<double *>(Ust + 128 * kTcWs);  // [8][64][6]
+    if (!err && warp < kTcEpiWarps) {
+        const int row = 32 * (warp & 3) + lane, j0 = 16 * (warp >> 2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            Wst[row * kTcWs + j0 + i] = make_float2(w[2 * i], w[2 * i + 1]);
+            Ust[row * kTcWs + j0 + i] = make_float2(u[2 * i], u[2 * i + 1]);
+        }
+    }
+    __syncthreads();
+    if (!err) {
+        // element update: thread (row group g, slot j) takes rows g, g + 8, ... of slot j
+        if (tid < 8 * kTcSlotsPerTile) {
+            const int j = tid % kTcSlotsPerTile, g = tid / kTcSlotsPerTile, sl = s0 + j;
+            const int st = T.state[sl];
+            const float vi = T.vid[sl], dvi = T.vid[T.S + sl];
+            double part[6] = {0, 0, 0, 0, 0, 0};
+            for (int row = g; row < R; row += 8) {
+                const size_t o = (size_t)(r0 + row) * T.S + sl;
+                const float2 c = Cg[o], ws = Wst[row * kTcWs + j], us = Ust[row * kTcWs + j];
+                const float2 wt = make_float2(fmaf(vi, c.x, ws.x), fmaf(vi, c.y, ws.y));
+                const float2 ut = make_float2(fmaf(dvi, c.x, us.x), fmaf(dvi, c.y, us.y));
+                tc_elem(T, S, s, cur, r0 + row, sl, st, c, wt, ut, part);
+            }
+            for (int k = 0; k < 6; ++k) red[(g * kTcSlotsPerTile + j) * 6 + k] = part[k];
+        }
+        __syncthreads();
+        if (tid < kTcSlotsPerTile) {
+            double acc6[6] = {0, 0, 0, 0, 0, 0};
+            for (int g = 0; g < 8; ++g)
+                for (int k = 0; k < 6; ++k) acc6[k] += red[(g * kTcSlotsPerTile + tid) * 6 + k];
+            double *o = T.part + ((size_t)rt * T.S + s0 + tid) * 6;
+            for (int k = 0; k < 6; ++k) o[k] = acc6[k];
+        }
+    } else if (tid == 0) {
+        atomicOr(T.live + 1, 1);  // error flag: a bounded wait ran out
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == kTcMmaWarp) tc_tmem_dealloc(tbase, 256);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -324,32 +387,57 @@ __device__ void tc_locate(const DevSys &S, TSlot &m)
     if (R < S.r_min) m.status |= MQCT_TRAJ_TABLE_RANGE;
 }
 
-// spline values of the next stage, FP32 views, identity-term sums
-__device__ void tc_publish(const TcState &T, const DevSys &S, int sl)
+// spline values of the next stage, FP32 views, identity-term sums (one warp per slot; the
+// slot record is final when the warp calls this)
+__device__ void tc_publish(const TcState &T, const DevSys &S, int sl, int lane)
 {
     const TSlot &m = T.slot[sl];
-    T.state[sl] = m.state;
-    if (m.state == TS_IDLE) {
-        for (int l = 0; l < S.L; ++l) T.coef[(size_t)l * T.S + sl] = T.coef[((size_t)S.L + l) * T.S + sl] = 0.f;
-        T.vid[sl] = T.vid[T.S + sl] = 0.f;
-        T.hp[sl] = 0.f;
-        T.dtf[sl] = 1.f;
+    const int state = m.state;
+    if (lane == 0) T.state[sl] = state;
+    if (state == TS_IDLE) {
+        for (int l = lane; l < S.L; l += 32) T.coef[(size_t)l * T.S + sl] = T.coef[((size_t)S.L + l) * T.S + sl] = 0.f;
+        if (lane == 0) {
+            T.vid[sl] = T.vid[T.S + sl] = 0.f;
+            T.hp[sl] = 0.f;
+            T.dtf[sl] = 1.f;
+        }
         return;
     }
     float v0 = 0.f, d0 = 0.f;
     const float x = (float)m.x;
-    for (int l = 0; l < S.L; ++l) {
-        const float4 c = S.vcoef_f[(size_t)l * S.n_int + m.kint];
+    const int kint = m.kint;
+    for (int l = lane; l < S.L; l += 32) {
+        const float4 c = S.vcoef_f[(size_t)l * S.n_int + kint];
         const float v = fmaf(x, fmaf(x, fmaf(x, c.w, c.z), c.y), c.x);
         const float dv = fmaf(x, fmaf(3.0f * x, c.w, 2.0f * c.z), c.y);
         T.coef[(size_t)l * T.S + sl] = v;
         T.coef[((size_t)S.L + l) * T.S + sl] = dv;
         if ((S.id_mask >> l) & 1ull) { v0 += v; d0 += dv; }
     }
-    T.vid[sl] = v0;
-    T.vid[T.S + sl] = d0;
-    T.hp[sl] = (float)(0.5 * m.phidot);
-    T.dtf[sl] = (float)m.dt;
+    for (int o = 16; o; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+    }
+    if (lane == 0) {
+        T.vid[sl] = v0;
+        T.vid[T.S + sl] = d0;
+        T.hp[sl] = (float)(0.5 * m.phidot);
+        T.dtf[sl] = (float)m.dt;
+    }
+}
+
+// phase factors exp(-i E_l t) of every level for one slot (one warp): kind 1 -> PHa at t,
+// kind 2 -> PHb at t, kind 3 -> start of a trajectory: PHa = 1, PHb at t = dt/2
+__device__ void tc_phases(const TcState &T, const DevSys &S, int sl, int lane, int kind, double t)
+{
+    for (int l = lane; l < S.n_levels; l += 32) {
+        const float2 ph = tc_phase(S.lev_energy[l], t);
+        if (kind == 1) T.PHa[(size_t)l * T.S + sl] = ph;
+        else {
+            T.PHb[(size_t)l * T.S + sl] = ph;
+            if (kind == 3) T.PHa[(size_t)l * T.S + sl] = make_float2(1.f, 0.f);
+        }
+    }
 }
 
 __device__ void tc_claim(const TcState &T, const DevSys &S, int sl)
@@ -396,104 +484,112 @@ __device__ void tc_claim(const TcState &T, const DevSys &S, int sl)
     }
 }
 
-// a slot that starts a trajectory: phases of t = 0 and t = dt/2
-__device__ void tc_start_phases(const TcState &T, const DevSys &S, int sl)
-{
-    const TSlot &m = T.slot[sl];
-    for (int l = 0; l < S.n_levels; ++l) {
-        T.PHa[(size_t)l * T.S + sl] = make_float2(1.f, 0.f);
-        T.PHb[(size_t)l * T.S + sl] = tc_phase(S.lev_energy[l], 0.5 * m.dt);
-    }
-}
-
-__global__ void k_tc_init(TcState T)
+// one warp per slot: claim the first trajectory and initialise its column
+__global__ void __launch_bounds__(128) k_tc_init(TcState T)
 {
     const DevSys &S = *T.sys;
-    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, sl = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (sl >= T.S) return;
-    tc_claim(T, S, sl);
     TSlot &m = T.slot[sl];
+    if (lane == 0) tc_claim(T, S, sl);
+    __syncwarp();
     if (m.state == TS_WAIT) {
-        for (int r = 0; r < S.n; ++r) {
+        for (int r = lane; r < S.n; r += 32) {
             const float2 v = make_float2(r == m.s0 ? 1.0f : 0.0f, 0.0f);
             const size_t e = (size_t)r * T.S + sl;
             T.A[e] = v; T.ACC[e] = make_float2(0.f, 0.f); T.C[0][e] = v;
         }
-        m.state = m.max_steps > 0 ? TS_ACTIVE : TS_FINAL;
-        if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
-        tc_locate(S, m);
-        tc_start_phases(T, S, sl);
+        __syncwarp();
+        if (lane == 0) {
+            m.state = m.max_steps > 0 ? TS_ACTIVE : TS_FINAL;
+            if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
+            tc_locate(S, m);
+        }
+        __syncwarp();
+        tc_phases(T, S, sl, lane, 3, 0.5 * m.dt);
     }
-    tc_publish(T, S, sl);
+    __syncwarp();
+    tc_publish(T, S, sl, lane);
 }
 
-__global__ void k_tc_slots(TcState T, int s, int n_rowblocks)
+// one warp per slot: sum the row-block partials of force, torque and diagnostics, then (lane 0,
+// FP64) the classical stage update (Eqs. 7-10), bookkeeping, stop rule and refill; the lanes
+// share the phase factors and spline values of the next stage
+__global__ void __launch_bounds__(128) k_tc_slots(TcState T, int s, int n_rowblocks)
 {
     const DevSys &S = *T.sys;
-    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, sl = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (sl >= T.S) return;
     TSlot &m = T.slot[sl];
-    double F = 0, Tq = 0, V = 0, NR = 0, ER = 0, JY = 0;
-    for (int b = 0; b < n_rowblocks; ++b) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = lane; b < n_rowblocks; b += 32) {
         const double *p = T.part + ((size_t)b * T.S + sl) * 6;
-        F += p[0]; Tq += p[1];
-        if (s == 0) { V += p[2]; NR += p[3]; ER += p[4]; JY += p[5]; }
+        for (int q = 0; q < 6; ++q) acc[q] += p[q];
     }
-    if (m.state == TS_ACTIVE || m.state == TS_FINAL) {
-        const double R = m.qs[0], PR = m.qs[1], PP = m.qs[3], imu = m.inv_mu;
-        const double ir = 1.0 / R, ir2 = ir * ir;
-        if (s == 0) {
-            const double et = 0.5 * imu * (PR * PR + PP * PP * ir2) + ER + V;
-            const double jt = PP + 0.5 * JY;
-            if (m.steps == 0) { m.e0 = et; m.j0 = jt; }
-            m.ndev = fmax(m.ndev, fabs(NR - 1.0));
-            m.edev = fmax(m.edev, fabs(et - m.e0));
-            m.jdev = fmax(m.jdev, fabs(jt - m.j0));
-        }
-        if (m.state == TS_FINAL) {
+    for (int o = 16; o; o >>= 1)
+        for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    int kind = 0;
+    double tph = 0.0;
+    if (lane == 0) {
+        const double F = acc[0], Tq = acc[1], V = acc[2], NR = acc[3], ER = acc[4], JY = acc[5];
+        if (m.state == TS_ACTIVE || m.state == TS_FINAL) {
+            const double R = m.qs[0], PR = m.qs[1], PP = m.qs[3], imu = m.inv_mu;
+            const double ir = 1.0 / R, ir2 = ir * ir;
             if (s == 0) {
-                if (T.diag) {
-                    mqct_diag d;
-                    d.steps = m.steps; d.status = m.status;
-                    d.norm_dev = m.ndev; d.energy_dev = m.edev; d.angmom_dev = m.jdev;
-                    d.t_final = m.steps * m.dt;
-                    T.diag[m.traj] = d;
+                const double et = 0.5 * imu * (PR * PR + PP * PP * ir2) + ER + V;
+                const double jt = PP + 0.5 * JY;
+                if (m.steps == 0) { m.e0 = et; m.j0 = jt; }
+                m.ndev = fmax(m.ndev, fabs(NR - 1.0));
+                m.edev = fmax(m.edev, fabs(et - m.e0));
+                m.jdev = fmax(m.jdev, fabs(jt - m.j0));
+            }
+            if (m.state == TS_FINAL) {
+                if (s == 0) {
+                    if (T.diag) {
+                        mqct_diag d;
+                        d.steps = m.steps; d.status = m.status;
+                        d.norm_dev = m.ndev; d.energy_dev = m.edev; d.angmom_dev = m.jdev;
+                        d.t_final = m.steps * m.dt;
+                        T.diag[m.traj] = d;
+                    }
+                    tc_claim(T, S, sl);  // WAIT (column initialised at stage 3) or IDLE
                 }
-                tc_claim(T, S, sl);  // WAIT (column initialised at stage 3) or IDLE
-            }
-        } else {
-            const double l4[4] = {PR * imu, F + PP * PP * imu * ir2 * ir, m.phidot, Tq};
-            const double wg = (s == 1 || s == 2) ? 2.0 : 1.0;
-            for (int i = 0; i < 4; ++i) m.lacc[i] = s == 0 ? l4[i] : fma(wg, l4[i], m.lacc[i]);
-            if (s < 3) {
-                const double bnd = s == 2 ? m.dt : 0.5 * m.dt;
-                for (int i = 0; i < 4; ++i) m.qs[i] = fma(bnd, l4[i], m.q[i]);
             } else {
-                for (int i = 0; i < 4; ++i) { m.q[i] = fma(m.dt / 6.0, m.lacc[i], m.q[i]); m.qs[i] = m.q[i]; }
-                m.steps += 1;
-                const bool fin = isfinite(m.q[0]) && isfinite(m.q[1]) && isfinite(m.q[2]) && isfinite(m.q[3]);
-                if (!fin) m.status |= MQCT_TRAJ_NONFINITE;
-                if (!fin || (m.q[0] >= m.r_end && m.q[1] > 0.0)) m.state = TS_FINAL;
-                else if (m.steps >= m.max_steps) { m.status |= MQCT_TRAJ_MAX_STEPS; m.state = TS_FINAL; }
+                const double l4[4] = {PR * imu, F + PP * PP * imu * ir2 * ir, m.phidot, Tq};
+                const double wg = (s == 1 || s == 2) ? 2.0 : 1.0;
+                for (int i = 0; i < 4; ++i) m.lacc[i] = s == 0 ? l4[i] : fma(wg, l4[i], m.lacc[i]);
+                if (s < 3) {
+                    const double bnd = s == 2 ? m.dt : 0.5 * m.dt;
+                    for (int i = 0; i < 4; ++i) m.qs[i] = fma(bnd, l4[i], m.q[i]);
+                } else {
+                    for (int i = 0; i < 4; ++i) { m.q[i] = fma(m.dt / 6.0, m.lacc[i], m.q[i]); m.qs[i] = m.q[i]; }
+                    m.steps += 1;
+                    const bool fin = isfinite(m.q[0]) && isfinite(m.q[1]) && isfinite(m.q[2]) && isfinite(m.q[3]);
+                    if (!fin) m.status |= MQCT_TRAJ_NONFINITE;
+                    if (!fin || (m.q[0] >= m.r_end && m.q[1] > 0.0)) m.state = TS_FINAL;
+                    else if (m.steps >= m.max_steps) { m.status |= MQCT_TRAJ_MAX_STEPS; m.state = TS_FINAL; }
+                }
+                if (!(m.status & MQCT_TRAJ_NONFINITE)) tc_locate(S, m);
+                // phase factors needed ahead: after stage 1 the integer time t + dt, after stage 3
+                // the half time of the next step
+                if (s == 1) { kind = 1; tph = m.steps * m.dt + m.dt; }
+                if (s == 3 && m.state == TS_ACTIVE) { kind = 2; tph = m.steps * m.dt + 0.5 * m.dt; }
             }
-            if (!(m.status & MQCT_TRAJ_NONFINITE)) tc_locate(S, m);
-            // phase factors needed ahead: after stage 1 the integer time t + dt, after stage 3
-            // the half time of the next step
-            if (s == 1)
-                for (int l = 0; l < S.n_levels; ++l)
-                    T.PHa[(size_t)l * T.S + sl] = tc_phase(S.lev_energy[l], m.steps * m.dt + m.dt);
-            if (s == 3 && m.state == TS_ACTIVE)
-                for (int l = 0; l < S.n_levels; ++l)
-                    T.PHb[(size_t)l * T.S + sl] = tc_phase(S.lev_energy[l], m.steps * m.dt + 0.5 * m.dt);
+        } else if (m.state == TS_WAIT && s == 3) {
+            m.state = m.max_steps > 0 ? TS_ACTIVE : TS_FINAL;
+            if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
+            tc_locate(S, m);
+            kind = 3;
+            tph = 0.5 * m.dt;
         }
-    } else if (m.state == TS_WAIT && s == 3) {
-        m.state = m.max_steps > 0 ? TS_ACTIVE : TS_FINAL;
-        if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
-        tc_locate(S, m);
-        tc_start_phases(T, S, sl);
     }
-    tc_publish(T, S, sl);
-    if (s == 3 && m.state != TS_IDLE) atomicAdd(T.live, 1);
+    __syncwarp();
+    kind = __shfl_sync(0xffffffffu, kind, 0);
+    tph = __shfl_sync(0xffffffffu, tph, 0);
+    if (kind) tc_phases(T, S, sl, lane, kind, tph);
+    __syncwarp();
+    tc_publish(T, S, sl, lane);
+    if (lane == 0 && s == 3 && m.state != TS_IDLE) atomicAdd(T.live, 1);
 }
 
 }  // namespace
@@ -501,9 +597,22 @@ __global__ void k_tc_slots(TcState T, int s, int n_rowblocks)
 mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
 {
     const int n = h.n;
-    int S = std::min(a.n, 8192);
-    S = (S + kTcSlotsPerTile - 1) / kTcSlotsPerTile * kTcSlotsPerTile;
-    const int n_rowblocks = (n + kTcRows - 1) / kTcRows;
+    // slot count: the contraction runs one CTA per SM per (row tile, 64-slot tile), so the slots
+    // fill whole waves -- one wave when the trajectories fit in it, else two (more slots only
+    // lengthen the tail of uneven trajectories); MQCT_TC_SLOTS overrides (multiple of 64)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_wave = std::max(1, sms / std::max(1, h.n_tiles));
+    const int want = (a.n + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
+    int n_slot_tiles = want <= per_wave ? want : std::min(want, 2 * per_wave);
+    if (const char *ev = std::getenv("MQCT_TC_SLOTS")) {
+        const int v = std::atoi(ev) / kTcSlotsPerTile;
+        if (v >= 1) n_slot_tiles = v;
+    }
+    n_slot_tiles = std::max(1, std::min(n_slot_tiles, 8192 / kTcSlotsPerTile));
+    const int S = n_slot_tiles * kTcSlotsPerTile;
+    const int n_rowblocks = std::max(1, h.n_tiles);
     std::vector<void *> tmp;
     cudaError_t e = cudaSuccess;
     auto get = [&](void **p, size_t b) {
@@ -522,8 +631,6 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     get((void **)&T.C[1], sizeof(float2) * ns);
     get((void **)&T.A, sizeof(float2) * ns);
     get((void **)&T.ACC, sizeof(float2) * ns);
-    get((void **)&T.W, sizeof(float2) * ns);
-    get((void **)&T.U, sizeof(float2) * ns);
     get((void **)&T.coef, sizeof(float) * 2 * (size_t)h.L * S);
     get((void **)&T.vid, sizeof(float) * 2 * (size_t)S);
     get((void **)&T.hp, sizeof(float) * S);
@@ -537,15 +644,14 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         cleanup();
         return cuda_fail(e, "cudaMallocAsync (tensor-core path scratch)");
     }
-    const size_t smem = 65536 + 4 * 32768;
-    if ((e = cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+    const size_t smem = kTcSmemFixed + sizeof(float) * 2 * kTcSlotsPerTile * (size_t)h.n_f;
+    if ((e = cudaFuncSetAttribute(k_tc_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "cudaFuncSetAttribute");
     }
     cudaMemsetAsync(T.live, 0, 2 * sizeof(int), st);
-    k_tc_init<<<(S + 127) / 128, 128, 0, st>>>(T);
+    k_tc_init<<<(S + 3) / 4, 128, 0, st>>>(T);
     const int n_ct = S / kTcSlotsPerTile;
-    const dim3 ugrid((S + 31) / 32, n_rowblocks);
     // one chunk of steps, captured once as a graph
     const int chunk = 16;
     cudaGraph_t graph = nullptr;
@@ -561,10 +667,8 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         for (int k = 0; k < chunk; ++k)
             for (int s = 0; s < 4; ++s) {
                 const int cur = s & 1;
-                if (h.n_f > 0) k_tc_contract<<<h.n_tiles * n_ct, 128, smem, cap>>>(T, cur);
-                else k_tc_identity<<<4 * 152, 256, 0, cap>>>(T, cur);
-                k_tc_update<<<ugrid, 256, 0, cap>>>(T, s, cur);
-                k_tc_slots<<<(S + 127) / 128, 128, 0, cap>>>(T, s, n_rowblocks);
+                k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, cap>>>(T, s, cur);
+                k_tc_slots<<<(S + 3) / 4, 128, 0, cap>>>(T, s, n_rowblocks);
             }
         e = cudaStreamEndCapture(cap, &graph);
     }

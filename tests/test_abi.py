@@ -204,7 +204,8 @@ def test_struct_layouts_match_header(L, tmp_path):
     checks = {
         "mqct_system_desc": (api.Desc, ["n_states", "energy", "mu", "n_terms", "G", "g_nnz", "g_val", "n_grid",
                                         "r_min", "v", "n_params", "ddv_ends", "path", "flags"]),
-        "mqct_system_info_t": (api.Info, ["n_states", "table_nnz", "device_bytes"]),
+        "mqct_system_info_t": (api.Info, ["n_states", "table_nnz", "device_bytes", "n_coupling_terms",
+                                          "n_row_tiles", "tc_kchunks"]),
         "mqct_diatom_params": (api.DiatomParams, ["jmax", "bconst", "mu", "n_terms", "A", "beta", "c6", "rd",
                                                   "n_grid", "r_min", "with_params", "path", "precision"]),
         "mqct_asym_params": (api.AsymParams, ["jmax", "A", "B", "C", "max_states", "mu", "n_terms", "lam", "mproj",
