@@ -78,15 +78,42 @@ __device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_usho
 __device__ __forceinline__ float bf16_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
 // ---------------------------------------------------------------------------------------------
-// the update of one element (row r, slot sl) from w = M c and u = M' c (Eq. 5, RK4); adds its
-// force, torque and (stage 0) diagnostic contributions to part[6]
-__device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s, int cur, int r, int sl, int st,
-                                        float2 c, float2 w, float2 u, double *part)
+// the inputs of one element update (row r, slot sl) gathered from global memory
+struct ElemIn {
+    float2 c, cu, cd, p, q, a0, acc;
+    float au, ad;
+    int lev;
+};
+
+// gather: only loads, so that several elements' loads are in flight before any store
+__device__ __forceinline__ void tc_elem_gather(const TcState &T, const DevSys &S, int s, int cur, int r, int sl,
+                                               ElemIn &in)
+{
+    const size_t e = (size_t)r * T.S + sl;
+    const float2 *Cc = T.C[cur];
+    const float2 *PHc = (s == 0 || s == 3) ? T.PHa : T.PHb;
+    const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
+    in.c = __ldg(Cc + e);
+    in.au = __ldg(S.aupf + r);
+    in.ad = __ldg(S.adnf + r);
+    in.cu = __ldg(Cc + (size_t)__ldg(S.up + r) * T.S + sl);
+    in.cd = __ldg(Cc + (size_t)__ldg(S.dn + r) * T.S + sl);
+    in.lev = __ldg(S.lev + r);
+    in.p = __ldg(PHc + (size_t)in.lev * T.S + sl);
+    in.q = __ldg(PHn + (size_t)in.lev * T.S + sl);
+    in.a0 = T.A[e];
+    in.acc = T.ACC[e];
+}
+
+// the update of one element from w = M c and u = M' c (Eq. 5, RK4) and its gathered inputs;
+// adds its force, torque and (stage 0) diagnostic contributions to part[6] (FP32: a thread sums
+// a few rows; the sums across threads, row tiles and the classical update are FP64 -- the FP64
+// pipe of this GPU is far too narrow for per-element FP64 arithmetic)
+__device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S, int s, int cur, int r, int sl,
+                                              int st, const ElemIn &in, float2 w, float2 u, float *part)
 {
     const int nxt = cur ^ 1;
     const size_t e = (size_t)r * T.S + sl;
-    const float2 *PHc = (s == 0 || s == 3) ? T.PHa : T.PHb;
-    const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
     if (st == TS_WAIT && s == 3) {
         const float2 v = make_float2(r == T.slot[sl].s0 ? 1.0f : 0.0f, 0.0f);
         T.A[e] = v;
@@ -95,26 +122,21 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
         return;
     }
     if (st != TS_ACTIVE && st != TS_FINAL) return;
-    const float2 *Cc = T.C[cur];
-    const float au = S.aupf[r], ad = S.adnf[r];
-    const float2 cu = Cc[(size_t)S.up[r] * T.S + sl], cd = Cc[(size_t)S.dn[r] * T.S + sl];
-    const float2 dc = make_float2(ad * cd.x - au * cu.x, ad * cd.y - au * cu.y);
-    const int lev = S.lev[r];
-    const float2 p = PHc[(size_t)lev * T.S + sl];
+    const float2 c = in.c, p = in.p, a0 = in.a0;
+    const float2 dc = make_float2(in.ad * in.cd.x - in.au * in.cu.x, in.ad * in.cd.y - in.au * in.cu.y);
     const float2 da = make_float2(p.x * dc.x + p.y * dc.y, p.x * dc.y - p.y * dc.x);
     const float hp = T.hp[sl];
     float2 kk;
     kk.x = fmaf(hp, da.x, p.x * w.y - p.y * w.x);
     kk.y = fmaf(hp, da.y, -(p.x * w.x + p.y * w.y));
-    part[0] -= (double)(c.x * u.x + c.y * u.y);
-    part[1] -= (double)(dc.x * w.x + dc.y * w.y);
-    const float2 a0 = T.A[e];
+    part[0] -= c.x * u.x + c.y * u.y;
+    part[1] -= dc.x * w.x + dc.y * w.y;
     if (s == 0) {
         const float pp = a0.x * a0.x + a0.y * a0.y;
-        part[2] += (double)(c.x * w.x + c.y * w.y);
-        part[3] += (double)pp;
-        part[4] += S.lev_energy[lev] * (double)pp;
-        part[5] += (double)(a0.x * da.y - a0.y * da.x);
+        part[2] += c.x * w.x + c.y * w.y;
+        part[3] += pp;
+        part[4] += (float)S.lev_energy[in.lev] * pp;
+        part[5] += a0.x * da.y - a0.y * da.x;
     }
     if (st == TS_FINAL) {
         if (s == 0) {
@@ -125,7 +147,7 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
         return;
     }
     const float dtj = T.dtf[sl];
-    float2 acc = T.ACC[e];
+    float2 acc = in.acc;
     if (s == 0) {
         acc = make_float2(kk.x + acc.x, kk.y + acc.y);  // acc holds the last rounding error
     } else {
@@ -133,6 +155,7 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
         acc.x = fmaf(wg, kk.x, acc.x);
         acc.y = fmaf(wg, kk.y, acc.y);
     }
+    const float2 q = in.q;
     if (s == 3) {
         // compensated a + (dt/6) acc (two-sum); the rounding error goes to the accumulator
         const float h6 = dtj * (1.0f / 6.0f), ih6 = 6.0f / dtj;
@@ -143,13 +166,11 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
         const float ey = __fadd_rn(__fsub_rn(a0.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
         T.A[e] = make_float2(sx, sy);
         T.ACC[e] = make_float2(ex * ih6, ey * ih6);
-        const float2 q = PHn[(size_t)lev * T.S + sl];
         T.C[nxt][e] = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
     } else {
         T.ACC[e] = acc;
         const float bn = s == 2 ? dtj : 0.5f * dtj;
         const float2 yn = make_float2(fmaf(bn, kk.x, a0.x), fmaf(bn, kk.y, a0.y));
-        const float2 q = PHn[(size_t)lev * T.S + sl];
         T.C[nxt][e] = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
     }
 }
@@ -162,7 +183,8 @@ __device__ __forceinline__ void tc_elem(const TcState &T, const DevSys &S, int s
 //    hi.hi + hi.lo + lo.hi) into one of two TMEM accumulators, Y_l = G^l C;
 //  - sixteen epilogue warps (four per TMEM lane quadrant, 32 columns each) fold each term into
 //    w += v_l Y_l and u += v_l' Y_l with the per-slot spline weights (Eq. 12), in registers;
-//  - the element update of Eq. 5 and RK4 (tc_elem) runs on the staged w, u with the identity
+//  - the element update of Eq. 5 and RK4 (tc_elem_gather / tc_elem_apply, four rows' loads in
+//    flight per thread) runs on the staged w, u with the identity
 //    terms added, and the per-slot partial sums of force, torque and diagnostics over the
 //    tile's rows go to part[row tile][slot].
 constexpr int kTcEpiWarps = 16;
@@ -347,15 +369,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
             const int j = tid % kTcSlotsPerTile, g = tid / kTcSlotsPerTile, sl = s0 + j;
             const int st = T.state[sl];
             const float vi = T.vid[sl], dvi = T.vid[T.S + sl];
-            double part[6] = {0, 0, 0, 0, 0, 0};
-            for (int row = g; row < R; row += 8) {
-                const size_t o = (size_t)(r0 + row) * T.S + sl;
-                const float2 c = Cg[o], ws = Wst[row * kTcWs + j], us = Ust[row * kTcWs + j];
-                const float2 wt = make_float2(fmaf(vi, c.x, ws.x), fmaf(vi, c.y, ws.y));
-                const float2 ut = make_float2(fmaf(dvi, c.x, us.x), fmaf(dvi, c.y, us.y));
-                tc_elem(T, S, s, cur, r0 + row, sl, st, c, wt, ut, part);
+            float part[6] = {0, 0, 0, 0, 0, 0};
+            const bool work = st == TS_ACTIVE || st == TS_FINAL;
+            constexpr int kB = 4;  // rows gathered before any is updated
+            for (int rb = g; rb < R; rb += 8 * kB) {
+                ElemIn in[kB];
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const int row = rb + 8 * k;
+                    if (work && row < R) tc_elem_gather(T, S, s, cur, r0 + row, sl, in[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const int row = rb + 8 * k;
+                    if (row >= R) continue;
+                    float2 wt = make_float2(0.f, 0.f), ut = wt;
+                    if (work) {
+                        const float2 c = in[k].c, ws = Wst[row * kTcWs + j], us = Ust[row * kTcWs + j];
+                        wt = make_float2(fmaf(vi, c.x, ws.x), fmaf(vi, c.y, ws.y));
+                        ut = make_float2(fmaf(dvi, c.x, us.x), fmaf(dvi, c.y, us.y));
+                    }
+                    tc_elem_apply(T, S, s, cur, r0 + row, sl, st, in[k], wt, ut, part);
+                }
             }
-            for (int k = 0; k < 6; ++k) red[(g * kTcSlotsPerTile + j) * 6 + k] = part[k];
+            for (int k = 0; k < 6; ++k) red[(g * kTcSlotsPerTile + j) * 6 + k] = (double)part[k];
         }
         __syncthreads();
         if (tid < kTcSlotsPerTile) {
@@ -521,6 +558,7 @@ __global__ void __launch_bounds__(128) k_tc_slots(TcState T, int s, int n_rowblo
     const int lane = threadIdx.x & 31, sl = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (sl >= T.S) return;
     TSlot &m = T.slot[sl];
+    if (m.state == TS_IDLE) return;  // published as idle when it became idle
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int b = lane; b < n_rowblocks; b += 32) {
         const double *p = T.part + ((size_t)b * T.S + sl) * 6;

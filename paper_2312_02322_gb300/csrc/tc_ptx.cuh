@@ -67,19 +67,13 @@ __device__ __forceinline__ void tc_mbar_init(uint64_t *bar, uint32_t count)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ uint64_t tc_globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // wait for the mbarrier phase `parity`: at most `limit` polls (each suspends the thread for at
-// most ~1 us) and at most ~2 s of wall time; true once the phase completed
+// most ~1 us) and at most ~4e9 SM clock cycles (about 2 s); true once the phase completed.
+// The fast path (phase already complete) reads no clock.
 __device__ __forceinline__ bool tc_mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
 {
     const uint32_t a = tc_smem_addr(bar);
-    uint64_t t0 = 0;
+    long long t0 = 0;
     for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
@@ -90,11 +84,8 @@ __device__ __forceinline__ bool tc_mbar_wait(uint64_t *bar, uint32_t parity, lon
             : "r"(a), "r"(parity), "r"(1000u)
             : "memory");
         if (done) return true;
-        if ((i & 1023) == 0) {
-            const uint64_t t = tc_globaltimer();
-            if (i == 0) t0 = t;
-            else if (t - t0 > 2000000000ull) return false;
-        }
+        if (i == 0) t0 = clock64();
+        else if ((i & 63) == 0 && clock64() - t0 > 4000000000ll) return false;
     }
     return false;
 }
