@@ -31,6 +31,8 @@ from paper_2312_02322_gb300 import inputs as W  # noqa: E402
 METRIC = "MQCT trajectory-steps/s at N=441/1600, batched mixed vs plain FP64, same error"
 WORKLOAD = "diatom j<=20 (N=441), 3072 trajectories: E in {100,300,1000,3000} cm^-1 x j' in {0,1,2} x 256 b on 0-15 bohr"
 WORKLOAD_1600 = "diatom j<=39 (N=1600), 768 trajectories: E in {1000,3000} cm^-1 x j' in {0,1,2} x 128 b on 0-15 bohr"
+WORKLOAD_MIX = ("uneven batch: diatom bases N = 49, 121, 441, 1600 (j <= 6, 10, 20, 39) in a seeded 1:2:4:1 mix, "
+                "b ~ U(0,20), E log-uniform 10-5000 cm^-1, one propagation call")
 WORKLOAD_ASYM = ("asymmetric top A,B,C = 27.88,14.51,9.28 cm^-1, J<=12 truncated to N=1580 (110 levels), 28 terms "
                  "lam<=6, 8 E log-spaced 10-2000 cm^-1, b ~ U(0,15), initial level J=0")
 
@@ -51,9 +53,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-traj", type=int, default=0,
                     help="run a seeded subset of this many trajectories (profiling of a small case)")
-    ap.add_argument("--workload", default="n441", choices=["n441", "n1600", "asym1580"],
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the launch-shape candidates on a probe sample first and use the fastest")
+    ap.add_argument("--workload", default="n441", choices=["n441", "n1600", "asym1580", "mix"],
                     help="n441: the 3072-trajectory N = 441 workload; n1600: 768 trajectories with N = 1600; "
-                         "asym1580: the N = 1580 asymmetric-top workload (a seeded subset, --max-traj, default 1024)")
+                         "asym1580: the N = 1580 asymmetric-top workload (a seeded subset, --max-traj, default 1024); "
+                         "mix: the uneven four-basis batch (first --max-traj of its 50000 trajectories, default 4096)")
     ap.add_argument("--energy", type=float, default=0.0,
                     help="keep only the trajectories at this collision energy (cm^-1)")
     return ap.parse_args()
@@ -208,52 +213,102 @@ def gpu_arm(args):
     build.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    if args.workload == "asym1580":
+    # ---- workload: one system, or the uneven mix of four bases in one call
+    if args.workload == "mix":
+        ps, ts = W.workload4()
+        workload = WORKLOAD_MIX
+        if not args.max_traj:
+            args.max_traj = 4096
+    elif args.workload == "asym1580":
         p, ts = W.workload3()
+        ps = [p]
         workload = WORKLOAD_ASYM
         if not args.max_traj:
             args.max_traj = 1024
     else:
         p, ts = W.workload2() if args.workload == "n441" else W.workload2_n1600()
+        ps = [p]
         workload = WORKLOAD if args.workload == "n441" else WORKLOAD_1600
     if args.energy:
         ts = ts.subset(np.flatnonzero(np.isclose(ts.e_coll, float(W.cm(args.energy)))))
         workload = f"E = {args.energy} cm^-1 part of: {workload}"
-    if args.max_traj:
-        ts = oracle_sample(p, ts, args.max_traj, seed=5)
+    if args.max_traj and args.max_traj < ts.n:
+        if args.workload == "mix":
+            ts = ts.subset(np.arange(args.max_traj))  # the mix is already a seeded random draw
+        else:
+            ts = oracle_sample(ps[0], ts, args.max_traj, seed=5)
         workload = f"seeded subset of {ts.n} trajectories of: {workload}"
-    sys_ = make_system(api, p, args.path, args.precision)
-    info = sys_.info
-    tr = api.make_trajs(ts, sys_)
+    systems = [make_system(api, q, args.path, args.precision) for q in ps]
+    infos = [s_.info for s_ in systems]
+    tr = api.make_trajs(ts, systems)
+    sidx = tr["system_idx"].astype(int)
     trd = torch.from_numpy(tr.view(np.uint8).copy()).to(dev)
-    group_d = torch.from_numpy(ts.group.astype(np.int32)).to(dev)
+    tune = {}
+    if args.autotune and args.precision != "fp64":
+        from paper_2312_02322_gb300 import autotune
+
+        t_ = autotune.tune_batch(systems, tr)
+        tune = {"batch_shape": t_["batch_shape"], "tc_slots": t_["tc_slots"]}
+        tune_report = [None if r is None else {"option": r["option"], "rate": r["rate"],
+                                               "table": [(x["option"], round(x["rate"])) for x in r["table"]]}
+                       for r in t_["reports"]]
+    # per-system cross-section groups (rows of one system, its own basis width)
+    groups = []
+    for i, s_ in enumerate(systems):
+        rows = np.flatnonzero(sidx == i)
+        if len(rows) == 0:
+            continue
+        sub = ts.subset(rows)
+        if args.workload == "mix":
+            sub.group = np.zeros(len(rows), np.int32)
+            sub.n_groups = 1
+        groups.append((i, rows, sub))
 
     # the first warm-up pass also returns the step counts and statuses (every pass does the
-    # same deterministic work), which fix the cross-section weights
-    pop, _, diag = api.propagate(sys_, trd, device=True, stream=stream)
+    # same deterministic work), which fix the cross-section weights; and the completion times
+    t_start = torch.zeros(ts.n, dtype=torch.int64, device=dev)
+    t_done = torch.zeros(ts.n, dtype=torch.int64, device=dev)
+    pop, _, diag = api.propagate(systems, trd, device=True, stream=stream, timing=(t_start, t_done), **tune)
     torch.cuda.synchronize()
     dg = api.diag_to_numpy(diag)
-    w = api.sigma_weights(ts, dg["status"])
-    w_d = torch.from_numpy(w).to(dev)
     traj_steps = float(dg["steps"].sum())
     n_bad = int(np.count_nonzero(dg["status"] & (api.TRAJ_MAX_STEPS | api.TRAJ_NONFINITE)))
+    ts_np, td_np = t_start.cpu().numpy(), t_done.cpu().numpy()
+    done_ms = (td_np - ts_np.min()) * 1e-6
+    run_ms = (td_np - ts_np) * 1e-6
+    latency = {"p50_ms": float(np.percentile(done_ms, 50)), "p99_ms": float(np.percentile(done_ms, 99)),
+               "max_ms": float(done_ms.max()), "run_p50_ms": float(np.percentile(run_ms, 50)),
+               "run_p99_ms": float(np.percentile(run_ms, 99)),
+               "note": "completion time of each trajectory since the first one started (one batch submitted "
+                       "at once), and each trajectory's own start-to-finish time; GPU global timer"}
+    sig_args = []
+    for i, rows, sub in groups:
+        w = api.sigma_weights(sub, dg["status"][rows])
+        sig_args.append((systems[i], torch.from_numpy(rows).to(dev), infos[i]["n_states"], torch.from_numpy(w).to(dev),
+                         torch.from_numpy(sub.group.astype(np.int32)).to(dev), sub.n_groups))
+    one_sys = len(systems) == 1 and len(groups) == 1 and len(groups[0][1]) == ts.n
+
+    def sigma(pop_):
+        for s_, rows_d, nn, w_d, g_d, ng in sig_args:
+            pp = pop_ if one_sys else pop_.index_select(0, rows_d)[:, :nn].contiguous()
+            api.cross_sections(s_, pp, w_d, g_d, ng, stream=stream)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     for _ in range(max(0, args.warmup - 1)):
-        pop, _, _ = api.propagate(sys_, trd, want_diag=False, device=True, stream=stream)
-        api.cross_sections(sys_, pop, w_d, group_d, ts.n_groups, stream=stream)
+        pop, _, _ = api.propagate(systems, trd, want_diag=False, device=True, stream=stream, **tune)
+        sigma(pop)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    # events: step start, after the persistent RK4 launch (dominant kernel), step end
+    # events: step start, after the propagation call (dominant kernel), step end
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     with Clocks(local) as clk:
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            pop, _, _ = api.propagate(sys_, trd, want_diag=False, device=True, stream=stream)
+            pop, _, _ = api.propagate(systems, trd, want_diag=False, device=True, stream=stream, **tune)
             ev[k][1].record(stream)
-            api.cross_sections(sys_, pop, w_d, group_d, ts.n_groups, stream=stream)
+            sigma(pop)
             ev[k][2].record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -266,20 +321,29 @@ def gpu_arm(args):
         ms = float(t.item())
     clocks = clk.summary()
     value = traj_steps * ws / (ms * 1e-3 / args.steps)
-    stages = 4.0 * traj_steps + ts.n  # four RK4 stages per step + one final diagnostic evaluation
-    n = info["n_states"]
-    if args.path == "plain":
-        flops_stage = 16.0 * info["table_nnz"] + 40.0 * n
-        bytes_stage = 32.0 * info["table_nnz"] * (1.0 if args.precision == "fp64" else 0.5)
-    else:
-        flops_stage = 4.0 * info["glambda_nnz"] + (8.0 * info["n_terms"] + 40.0) * n
-        bytes_stage = 0.0
-    fp64_peak = api.fma_rate("fp64") if args.precision == "fp64" else api.fma_rate("fp32")
-    achieved = flops_stage * stages / (k_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
-                "frac": achieved * 1e3 / fp64_peak, "traffic": None,
-                "kernel": "k_propagate_fp64" if args.precision == "fp64" else "k_batched_f32", "peak_source": f"measured {args.precision.upper()} FMA probe (mqct_probe_fma_rate)",
-                "algorithmic_flops_per_traj_stage": flops_stage, "traj_stages_per_launch": stages,
+    # ---- roofline of the dominant launch: algorithmic work summed over the systems
+    flops_tot = bytes_tot = exec_tot = 0.0
+    stages_tot = 0.0
+    for i, s_ in enumerate(systems):
+        inf = infos[i]
+        rows = sidx == i
+        stages = 4.0 * float(dg["steps"][rows].sum()) + float(rows.sum())  # + one final evaluation each
+        n = inf["n_states"]
+        if args.path == "plain":
+            fs = 16.0 * inf["table_nnz"] + 40.0 * n
+            bytes_tot += 32.0 * inf["table_nnz"] * (1.0 if args.precision == "fp64" else 0.5) * stages
+        else:
+            fs = 4.0 * inf["glambda_nnz"] + (8.0 * inf["n_terms"] + 40.0) * n
+        flops_tot += fs * stages
+        exec_tot += inf["tc_kchunks"] * 3 * (2.0 * 128 * 128 * 16) / 64.0 * stages
+        stages_tot += stages
+    fp_peak = api.fma_rate("fp64") if args.precision == "fp64" else api.fma_rate("fp32")
+    achieved = flops_tot / (k_ms * 1e-3) / 1e12
+    kernel = {"fp64": "k_propagate_fp64", "fp32": "k_batched_f32", "bf16x3": "k_tc_stage"}[args.precision]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp_peak / 1e3, "unit": "TFLOP/s",
+                "frac": achieved * 1e3 / fp_peak, "traffic": None, "kernel": kernel,
+                "peak_source": f"measured {args.precision.upper()} FMA probe (mqct_probe_fma_rate)",
+                "algorithmic_flops_per_traj_stage": flops_tot / stages_tot, "traj_stages_per_launch": stages_tot,
                 "kernel_ms": k_ms}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -289,18 +353,18 @@ def gpu_arm(args):
     if args.precision == "bf16x3":
         # executed tensor work: per stage, per 64-slot tile, for every stored term and row tile its
         # non-zero 16-column K chunks x 3 split products of a 128 x 128 x 16 MMA; time = the whole
-        # propagate call (contraction, element update and slot kernels): a lower bound
-        exec_stage = info["tc_kchunks"] * 3 * (2.0 * 128 * 128 * 16) / 64.0
+        # propagate call (stage and slot kernels): a lower bound
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        ach = exec_stage * stages / (k_ms * 1e-3) / 1e12
+        ach = exec_tot / (k_ms * 1e-3) / 1e12
         roofline = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
                     "traffic": None, "kernel": "k_tc_stage (timed with the whole propagate call)",
                     "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
-                    "executed_flops_per_traj_stage": exec_stage, "useful_flops_per_traj_stage": flops_stage,
-                    "useful_over_executed": flops_stage / exec_stage, "traj_stages_per_launch": stages,
+                    "executed_flops_per_traj_stage": exec_tot / stages_tot,
+                    "useful_flops_per_traj_stage": flops_tot / stages_tot,
+                    "useful_over_executed": flops_tot / exec_tot, "traj_stages_per_launch": stages_tot,
                     "kernel_ms": k_ms}
-    if bytes_stage and hbm:
-        gbs = bytes_stage * stages / (k_ms * 1e-3) / 1e9
+    if bytes_tot and hbm:
+        gbs = bytes_tot / (k_ms * 1e-3) / 1e9
         roofline["hbm_view"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
                                 "note": "algorithmic table bytes; the table is L2-resident, so DRAM traffic is lower"}
 
@@ -309,29 +373,35 @@ def gpu_arm(args):
     if not args.no_e2e:
         tr_pin = torch.from_numpy(tr.view(np.uint8).copy()).pin_memory()
         tr_host = tr_pin.numpy().view(api.TRAJ_DTYPE)
-        pop_h = np.zeros((ts.n, n))
-        e_ms = []
-        for k in range(1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pop_h, _, diag_h = api.propagate(sys_, tr_host, device=False, stream=stream)
-            sig = api.cross_sections(sys_, pop_h, w, ts.group, ts.n_groups, stream=stream)
-            e_ms.append(1e3 * (time.perf_counter() - t0))
-        e_ms_step = float(np.mean(e_ms))
-        h2d = tr.nbytes + pop_h.nbytes + w.nbytes + ts.group.astype(np.int32).nbytes
-        d2h = pop_h.nbytes + ts.n * api.DIAG_DTYPE.itemsize + sig.nbytes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pop_h, _, diag_h = api.propagate(systems, tr_host, device=False, stream=stream, **tune)
+        sig_bytes = 0
+        for i, rows, sub in groups:
+            w = api.sigma_weights(sub, diag_h["status"][rows])
+            sg = api.cross_sections(systems[i], np.ascontiguousarray(pop_h[rows, :infos[i]["n_states"]]), w, sub.group,
+                                    sub.n_groups, stream=stream)
+            sig_bytes += sg.nbytes + w.nbytes + sub.group.astype(np.int32).nbytes
+        e_ms_step = 1e3 * (time.perf_counter() - t0)
+        h2d = tr.nbytes + pop_h.nbytes + sig_bytes
+        d2h = pop_h.nbytes + ts.n * api.DIAG_DTYPE.itemsize + sig_bytes
         e2e = {"value": traj_steps * ws / (e_ms_step * 1e-3), "unit": "traj-steps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms_step}
 
     # the same batch through the plain FP64 path: its throughput, and the largest population
-    # difference of the measured path against it over every trajectory ("same error")
+    # difference of the measured path against it over every trajectory compared ("same error")
     compare = None
     if not args.no_compare and not (args.path == "plain" and args.precision == "fp64"):
-        # the asymmetric-top plain FP64 run is long (one CTA per trajectory at N = 1580): it is
-        # timed on a stratified 128-trajectory part of the batch
-        cidx = strat_idx(ts, 128, seed=9) if args.workload == "asym1580" else np.arange(ts.n)
+        # one CTA per trajectory: at N = 1580 or 1600 the plain FP64 run is long, so those
+        # workloads compare on a stratified 128-trajectory part of the batch
+        if args.workload in ("asym1580", "mix"):
+            cidx = np.sort(np.random.default_rng(9).choice(ts.n, min(128, ts.n), replace=False))
+            if args.workload == "asym1580":
+                cidx = strat_idx(ts, 128, seed=9)
+        else:
+            cidx = np.arange(ts.n)
         pop_m = pop.cpu().numpy()[cidx]
-        s64 = make_system(api, p, "plain", "fp64")
+        s64 = [make_system(api, q, "plain", "fp64") for q in ps]
         trc = torch.from_numpy(tr[cidx].view(np.uint8).copy()).to(dev)
         flush.zero_()
         a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -371,30 +441,39 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sub = oracle_sample(p, ts, 16)
+        p0 = ps[0] if args.workload != "mix" else ps[2]
+        ts0 = ts if args.workload != "mix" else ts.subset(np.flatnonzero(sidx == 2))
+        sub = oracle_sample(p0, ts0, 16) if args.workload != "mix" else ts0.subset(np.arange(min(16, ts0.n)))
         what = f"{sub.n} trajectories of the workload (stratified over the collision energies, seeded)"
         if args.workload == "asym1580":
             sub.max_steps = 400  # the oracle takes ~10 ms per step at N = 1580: the first 400 steps of each
             what += ", first 400 RK4 steps of each"
+        if args.workload == "mix":
+            sub.max_steps = 2000
+            what = f"{sub.n} trajectories of the N = 441 part of the mix, first 2000 RK4 steps of each"
         cores = cpu_cores()
-        s, t = run_oracle(p, sub, cores)
-        cpu = {"value": s / t, "unit": "traj-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{what}, {int(s)} traj-steps"}
+        s_, t_ = run_oracle(p0, sub, cores)
+        cpu = {"value": s_ / t_, "unit": "traj-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{what}, {int(s_)} traj-steps"}
     if dist:
         dist.destroy_process_group()
     if rank != 0:
         return
-    launches_per_step = 4  # order keys, persistent RK4, level sums, group sums (plus CUB's radix-sort passes)
+    # order keys, CUB radix sort passes, the propagation launch(es), level and group sums per system
+    launches_per_step = 3 + len(systems) + 2 * len(groups)
+    cfg = {"workload": workload, "path": args.path, "precision": args.precision,
+           "n_states": [inf["n_states"] for inf in infos] if len(infos) > 1 else infos[0]["n_states"],
+           "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,
+           "l2": "flushed (256 MB write) before every timed step", "seed": W.DEFAULT_SEED}
+    if tune:
+        cfg["autotuned"] = {"option": tune, "reports": tune_report}
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[args.precision],
-        "data": "synthetic",
-        "config": {"workload": workload, "path": args.path, "precision": args.precision, "n_states": n,
-                   "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,
-                   "l2": "flushed (256 MB write) before every timed step", "seed": W.DEFAULT_SEED},
+        "data": "synthetic", "config": cfg,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps, "comparison": compare, "adjoint": adj,
+        "gpu_launches": launches_per_step * args.steps, "latency": latency, "comparison": compare, "adjoint": adj,
     }))
 
 

@@ -224,11 +224,13 @@ mqct_status mqct_create_system(const mqct_system_desc *desc, mqct_system *out);
 mqct_status mqct_destroy_system(mqct_system sys);
 mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out);
 
-/* Propagate n trajectories (Eqs. 4-10, RK4) in one persistent launch; trajectories may
- * refer to different systems (uneven basis sizes), which must share path and precision.
+/* Propagate n trajectories (Eqs. 4-10, RK4); trajectories may refer to different systems
+ * (uneven basis sizes), which must share path and precision (see mqct_propagate_ex for how
+ * each precision schedules them).
  *   trajs      [n] mqct_traj (host or device)
  *   final_pop  [n][N_t] |a_s|^2 in the caller's state order of the trajectory's system,
- *              rows packed with stride N_max = max over the systems used; or NULL
+ *              rows packed with stride N_max = max over the systems used (the entries past
+ *              N_t of a row are not written); or NULL
  *   final_amp  [n][N_max][2] final interaction-picture amplitudes (re, im); or NULL
  *   diag       [n] mqct_diag; or NULL
  * Work order: trajectories are claimed from a device work queue, longest estimated
@@ -239,6 +241,30 @@ mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out);
  * MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
 mqct_status mqct_propagate(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
                            double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream);
+
+/* Options of mqct_propagate_ex; zero-initialise and set what is needed.  None of them changes
+ * the arithmetic of a trajectory: they select launch shapes and report timing. */
+typedef struct {
+    int64_t *t_start_ns;  /* [n] GPU global-timer value (ns) when each trajectory was started, or NULL;
+                             host or device pointer                                               */
+    int64_t *t_done_ns;   /* [n] GPU global-timer value (ns) when its results were written, or NULL */
+    const int32_t *batch_shape; /* [n_systems] HOST array or NULL: FP32 batched kernel shape of each
+                             system, 0 = automatic (widest that fits), 1..6 = (slots per CTA,
+                             threads) of (32,256) (16,256) (8,256) (16,512) (8,512) (4,512); a shape
+                             that does not fit the system's basis -> MQCT_ERR_UNSUPPORTED          */
+    const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: BF16X3 trajectories in flight per
+                             system (rounded up to a multiple of 64, at most 8192), 0 = automatic
+                             (one or two waves of the GPU)                                       */
+} mqct_propagate_opts;
+
+/* mqct_propagate with options (opts may be NULL).  Uneven batches: the trajectories of several
+ * systems of one call run together -- FP64: in one persistent launch; FP32: one persistent
+ * batched launch per system, all concurrent, each on a share of the SMs proportional to its
+ * estimated work; BF16X3: one system after the other.  Errors as for mqct_propagate, plus
+ * MQCT_ERR_INVALID_ARG for out-of-range options. */
+mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
+                              double *final_pop, double *final_amp, mqct_diag *diag, const mqct_propagate_opts *opts,
+                              void *cuda_stream);
 
 /* mqct_propagate without any memory allocation.  The paper has no counterpart: this call
  * exists for callers that may not allocate GPU memory while they run it -- frameworks that

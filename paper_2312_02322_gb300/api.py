@@ -69,6 +69,14 @@ class AsymParams(C.Structure):
                 ("tau_out", C.c_void_p)]
 
 
+class PropagateOpts(C.Structure):
+    _fields_ = [("t_start_ns", C.c_void_p), ("t_done_ns", C.c_void_p), ("batch_shape", C.c_void_p),
+                ("tc_slots", C.c_void_p)]
+
+
+# (slots per CTA, threads) of the FP32 batched kernel for batch_shape = index + 1
+BATCH_SHAPES = [(32, 256), (16, 256), (8, 256), (16, 512), (8, 512), (4, 512)]
+
 TRAJ_DTYPE = np.dtype([("e_coll", "<f8"), ("b", "<f8"), ("r0", "<f8"), ("r_end", "<f8"), ("dt", "<f8"),
                        ("init_state", "<i4"), ("max_steps", "<i4"), ("system_idx", "<i4"), ("_pad", "<i4")])
 DIAG_DTYPE = np.dtype([("steps", "<i4"), ("status", "<i4"), ("norm_dev", "<f8"), ("energy_dev", "<f8"),
@@ -96,6 +104,7 @@ def lib():
             L.mqct_destroy_system.argtypes = [vp]
             L.mqct_system_info.argtypes = [vp, C.POINTER(Info)]
             L.mqct_propagate.argtypes = [C.POINTER(vp), i32, vp, i32, vp, vp, vp, vp]
+            L.mqct_propagate_ex.argtypes = [C.POINTER(vp), i32, vp, i32, vp, vp, vp, C.POINTER(PropagateOpts), vp]
             L.mqct_cross_sections.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp]
             L.mqct_adjoint.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, vp]
             L.mqct_probe_fma_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
@@ -103,7 +112,7 @@ def lib():
             L.mqct_last_error.restype = C.c_char_p
             L.mqct_version.restype = C.c_char_p
             for f in ("mqct_build_diatom", "mqct_build_asym_top", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
-                      "mqct_propagate", "mqct_cross_sections", "mqct_adjoint"):
+                      "mqct_propagate", "mqct_propagate_ex", "mqct_cross_sections", "mqct_adjoint"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -251,11 +260,15 @@ def make_trajs(ts: "_inputs.TrajSet", systems) -> np.ndarray:
 
 
 def propagate(systems, trajs, want_pop=True, want_amp=False, want_diag=True, device=None, stream=None,
-              allow_traj_status=True):
-    """Run mqct_propagate.
+              allow_traj_status=True, batch_shape=0, tc_slots=0, timing=None):
+    """Run mqct_propagate_ex.
 
     trajs: numpy TRAJ_DTYPE array (host) or a torch uint8 CUDA tensor holding the same bytes.
     device=True returns torch CUDA tensors (asynchronous); device=False returns numpy arrays.
+    batch_shape / tc_slots: launch-shape options, one value or one per system (0 = automatic,
+    see mqct_propagate_opts).
+    timing: optional pair (t_start, t_done) of int64 arrays (numpy or CUDA tensors) of length n
+    that receive each trajectory's start and finish time on the GPU clock (ns).
     Returns (pop [n][N_max], amp [n][N_max] complex, diag) with None for outputs not requested."""
     systems = systems if isinstance(systems, (list, tuple)) else [systems]
     hs = (C.c_void_p * len(systems))(*[s.handle.value for s in systems])
@@ -284,7 +297,15 @@ def propagate(systems, trajs, want_pop=True, want_amp=False, want_diag=True, dev
             amp = np.zeros((n, nmax, 2))
         if want_diag:
             diag = np.zeros(n, DIAG_DTYPE)
-    st = lib().mqct_propagate(hs, len(systems), _ptr(trajs), n, _ptr(pop), _ptr(amp), _ptr(diag), _stream(stream))
+    op = PropagateOpts()
+    ns = len(systems)
+    shapes = np.ascontiguousarray(np.broadcast_to(np.asarray(batch_shape, np.int32), (ns,)))
+    slots = np.ascontiguousarray(np.broadcast_to(np.asarray(tc_slots, np.int32), (ns,)))
+    op.batch_shape, op.tc_slots = shapes.ctypes.data, slots.ctypes.data
+    if timing is not None:
+        op.t_start_ns, op.t_done_ns = _ptr(timing[0]), _ptr(timing[1])
+    st = lib().mqct_propagate_ex(hs, len(systems), _ptr(trajs), n, _ptr(pop), _ptr(amp), _ptr(diag), C.byref(op),
+                                 _stream(stream))
     _check(st, allow=(ERR_TRAJ,) if allow_traj_status else ())
     if amp is not None and not device:
         amp = amp[..., 0] + 1j * amp[..., 1]

@@ -1,0 +1,98 @@
+"""Launch-shape autotuner for the mixed-precision trajectory paths.
+
+The FP32 batched kernel exists in six (slots per CTA, threads) instances and the BF16X3 path
+runs a chosen number of trajectories in flight; which is fastest depends on the basis size, the
+density of the coupling terms and the GPU.  ``tune`` times short probe runs of every candidate
+on a sample of the caller's trajectories, each capped at ``probe_steps`` RK4 steps so that a
+probe costs milliseconds, and returns the fastest option together with the measured table.
+The options change launch shapes only, never the arithmetic of a trajectory beyond the order
+of its FP32 partial sums.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import api
+
+
+def _sample(trajs: np.ndarray, n: int) -> np.ndarray:
+    if len(trajs) <= n:
+        return trajs.copy()
+    return trajs[np.linspace(0, len(trajs) - 1, n).astype(int)].copy()
+
+
+def _time(system, tr_dev, opts, repeats, stream):
+    import torch
+
+    api.propagate(system, tr_dev, want_pop=False, want_diag=False, device=True, stream=stream, **opts)  # warm-up
+    best = None
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        api.propagate(system, tr_dev, want_pop=False, want_diag=False, device=True, stream=stream, **opts)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def candidates(system, n_traj: int) -> list[dict]:
+    """The launch options worth timing for this system and this many trajectories."""
+    info = system.info
+    if info["precision"] == api.FP32:
+        return [{"batch_shape": k} for k in range(1, len(api.BATCH_SHAPES) + 1)]
+    if info["precision"] == api.BF16X3:
+        import torch
+
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        per_wave = max(1, sms // max(1, info["n_row_tiles"]))
+        top = min(8192, 64 * ((n_traj + 63) // 64))
+        out = sorted({min(top, 64 * per_wave * k) for k in (1, 2, 3, 4)})
+        return [{"tc_slots": s} for s in out]
+    return [{}]
+
+
+def tune(system, trajs: np.ndarray, probe_steps: int = 300, max_sample: int = 8192, repeats: int = 2,
+         stream=None) -> dict:
+    """Time every candidate option on a sample of `trajs` (TRAJ_DTYPE, all naming this system as
+    system 0) with each trajectory capped at probe_steps steps.  Returns
+    {"option": best options (keywords of api.propagate), "rate": traj-steps/s, "table": [...]}."""
+    import torch
+
+    tr = _sample(trajs, max_sample)
+    tr["max_steps"] = np.minimum(tr["max_steps"], probe_steps)
+    tr["system_idx"] = 0
+    tr_dev = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+    _, _, dg = api.propagate(system, tr, want_pop=False, device=False)
+    steps = float(dg["steps"].sum())
+    table = []
+    for opt in candidates(system, len(tr)):
+        try:
+            ms = _time(system, tr_dev, opt, repeats, stream)
+        except api.MQCTError as err:
+            if err.status == api.ERR_UNSUPPORTED:
+                continue  # this shape does not fit the basis
+            raise
+        table.append({"option": opt, "ms": ms, "rate": steps / (ms * 1e-3)})
+    best = max(table, key=lambda r: r["rate"])
+    return {"option": best["option"], "rate": best["rate"], "table": table, "probe_steps": probe_steps,
+            "sample": int(len(tr))}
+
+
+def tune_batch(systems, trajs: np.ndarray, **kw) -> dict:
+    """Tune each system of an uneven batch on its own trajectories; returns the per-system
+    option lists {"batch_shape": [...], "tc_slots": [...]} for api.propagate and the reports."""
+    shapes, slots, reports = [], [], []
+    for i, s in enumerate(systems):
+        sub = trajs[trajs["system_idx"] == i]
+        if len(sub) == 0:
+            shapes.append(0)
+            slots.append(0)
+            reports.append(None)
+            continue
+        r = tune(s, sub, **kw)
+        shapes.append(int(r["option"].get("batch_shape", 0)))
+        slots.append(int(r["option"].get("tc_slots", 0)))
+        reports.append(r)
+    return {"batch_shape": shapes, "tc_slots": slots, "reports": reports}

@@ -81,6 +81,7 @@ __device__ void claim(const BatchArgs &a, const DevSys &S, Slot &sl)
             }
             continue;
         }
+        if (a.t_start) a.t_start[t] = mqct_clock_ns();
         const int s0 = S.inv[tr.init_state];
         int k = (int)floor((tr.r0 - S.r_min) * S.inv_h);
         k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(T, 512 / T) k_batched_f32(BatchArgs a)
                                 d.t_final = m.steps * m.dt;
                                 a.diag[m.traj] = d;
                             }
+                            if (a.t_done) a.t_done[m.traj] = mqct_clock_ns();
                             claim(a, S, m);
                         }
                     } else {
@@ -481,6 +483,7 @@ bool batched_fits(const DevSys &h, size_t cap)
 template <int B, int T>
 cudaError_t launch_batched(const BatchArgs &a, const DevSys &h, int sms, cudaStream_t st)
 {
+    if (a.sm_limit > 0) sms = std::min(sms, a.sm_limit);
     const size_t smem = batched_smem<B, T>(h);
     cudaError_t e = cudaFuncSetAttribute(k_batched_f32<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -496,32 +499,50 @@ cudaError_t launch_batched(const BatchArgs &a, const DevSys &h, int sms, cudaStr
 
 // Batch shape: 256-thread CTAs, two per SM, when a CTA's block fits in half the shared
 // memory; otherwise 512-thread CTAs, one per SM.  Widest batch first.
-int batched_width(const DevSys &h)
+bool batched_shape_fits(const DevSys &h, int i)
 {
     const size_t half = 110 * 1024, full = 220 * 1024;
-    if (batched_fits<32, 256>(h, half)) return 32 * 1000 + 256;
-    if (batched_fits<16, 256>(h, half)) return 16 * 1000 + 256;
-    if (batched_fits<8, 256>(h, half)) return 8 * 1000 + 256;
-    if (batched_fits<16, 512>(h, full)) return 16 * 1000 + 512;
-    if (batched_fits<8, 512>(h, full)) return 8 * 1000 + 512;
-    if (batched_fits<4, 512>(h, full)) return 4 * 1000 + 512;
+    switch (i) {
+        case 0: return batched_fits<32, 256>(h, half);
+        case 1: return batched_fits<16, 256>(h, half);
+        case 2: return batched_fits<8, 256>(h, half);
+        case 3: return batched_fits<16, 512>(h, full);
+        case 4: return batched_fits<8, 512>(h, full);
+        case 5: return batched_fits<4, 512>(h, full);
+        default: return false;
+    }
+}
+
+int batched_width(const DevSys &h)
+{
+    for (int i = 0; i < 6; ++i)
+        if (batched_shape_fits(h, i)) return kBatchShapes[i][0] * 1000 + kBatchShapes[i][1];
     return 0;
 }
 
+// launch with the requested shape (a.shape = index + 1) or the automatic one
 cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int shape = batched_width(h);
-    if (width) *width = shape / 1000;
-    switch (shape) {
-        case 32256: return launch_batched<32, 256>(a, h, sms, st);
-        case 16256: return launch_batched<16, 256>(a, h, sms, st);
-        case 8256: return launch_batched<8, 256>(a, h, sms, st);
-        case 16512: return launch_batched<16, 512>(a, h, sms, st);
-        case 8512: return launch_batched<8, 512>(a, h, sms, st);
-        case 4512: return launch_batched<4, 512>(a, h, sms, st);
+    int idx = -1;
+    if (a.shape > 0) {
+        if (a.shape > 6 || !batched_shape_fits(h, a.shape - 1)) return cudaErrorInvalidConfiguration;
+        idx = a.shape - 1;
+    } else {
+        for (int i = 0; i < 6 && idx < 0; ++i)
+            if (batched_shape_fits(h, i)) idx = i;
+    }
+    if (idx < 0) return cudaErrorInvalidConfiguration;
+    if (width) *width = kBatchShapes[idx][0];
+    switch (idx) {
+        case 0: return launch_batched<32, 256>(a, h, sms, st);
+        case 1: return launch_batched<16, 256>(a, h, sms, st);
+        case 2: return launch_batched<8, 256>(a, h, sms, st);
+        case 3: return launch_batched<16, 512>(a, h, sms, st);
+        case 4: return launch_batched<8, 512>(a, h, sms, st);
+        case 5: return launch_batched<4, 512>(a, h, sms, st);
         default: return cudaErrorInvalidConfiguration;
     }
 }

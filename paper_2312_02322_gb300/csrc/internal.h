@@ -97,12 +97,20 @@ struct PropArgs {
     double *pop;
     double *amp;
     mqct_diag *diag;
+    long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
     int nmax;      // row stride of pop / amp
     int smem_n;    // shared-memory vector length (max n over systems)
     int smem_lev;  // max n_levels over systems
 };
 #ifdef __CUDACC__
 __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a);
+// device clock in nanoseconds (the global timer every SM shares)
+__device__ __forceinline__ long long mqct_clock_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
 #endif
 
 // arguments of the batched mixed-precision launch (batched.cu)
@@ -115,9 +123,17 @@ struct BatchArgs {
     double *pop;
     double *amp;
     mqct_diag *diag;
+    long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
     int nmax;
-    int sys_idx;  // trajectories must name this system
+    int sys_idx;   // trajectories must name this system
+    int shape;     // FP32 batched kernel: 0 = automatic, else a kBatchShapes index + 1
+    int sm_limit;  // FP32 batched kernel: SMs its persistent grid may fill (0 = all)
+    int tc_slots;  // tensor-core path: trajectories in flight (0 = automatic)
 };
+// the (slots per CTA, threads) instances of the FP32 batched kernel, widest first
+constexpr int kBatchShapes[6][2] = {{32, 256}, {16, 256}, {8, 256}, {16, 512}, {8, 512}, {4, 512}};
+// true when shape index i (0-based) fits the system's basis
+bool batched_shape_fits(const DevSys &h, int i);
 cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width);
 // stage-synchronous tensor-core launch sequence (tc_batched.cu); allocates its scratch with
 // stream-ordered allocation and synchronises `st` between chunks of steps

@@ -115,7 +115,7 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate_fp64, threads, smem)) != cudaSuccess)
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate_noalloc: kernel does not fit on an SM");
-    PropArgs pa;
+    PropArgs pa{};
     pa.sys = dsys; pa.trajs = trajs; pa.order = nullptr; pa.n = n; pa.n_systems = n_systems; pa.queue = queue;
     pa.pop = final_pop; pa.amp = final_amp; pa.diag = diag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
     k_propagate_fp64<<<std::min(n, sms * per_sm), threads, smem, st>>>(pa);

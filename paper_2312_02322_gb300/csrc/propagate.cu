@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_select.cuh>
 #include <vector>
 
 #include "internal.h"
@@ -168,7 +169,10 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
             __syncthreads();
             continue;
         }
-        if (tid == 0) S = a.sys[tr.system_idx];
+        if (tid == 0) {
+            S = a.sys[tr.system_idx];
+            if (a.t_start) a.t_start[t] = mqct_clock_ns();
+        }
         __syncthreads();
         const int n = S.n;
         const int s0 = S.inv[tr.init_state];
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
             d.t_final = c.steps * dt;
             a.diag[t] = d;
         }
+        if (a.t_done && tid == 0) a.t_done[t] = mqct_clock_ns();
         __syncthreads();
     }
 }
@@ -419,9 +424,45 @@ struct StreamAllocs {
 
 }  // namespace
 
+namespace {
+
+// trajectory index i of the work order belongs to system s
+struct IsSystem {
+    const mqct_traj *tr;
+    int s;
+    __device__ bool operator()(const int &i) const { return tr[i].system_idx == s; }
+};
+
+// estimated work of each system: sum of its trajectories' (negated) order keys
+__global__ void k_system_work(const mqct_traj *trajs, const int *order, const float *keys, int n, int n_systems,
+                              double *work)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = trajs[order[i]].system_idx;
+    if (s >= 0 && s < n_systems) atomicAdd(work + s, -(double)keys[i]);
+}
+
+}  // namespace
+
 extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
                                       double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream)
 {
+    return mqct_propagate_ex(systems, n_systems, trajs, n, final_pop, final_amp, diag, nullptr, cuda_stream);
+}
+
+extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs,
+                                         int32_t n, double *final_pop, double *final_amp, mqct_diag *diag,
+                                         const mqct_propagate_opts *opts, void *cuda_stream)
+{
+    const mqct_propagate_opts no_opts{};
+    const mqct_propagate_opts &op = opts ? *opts : no_opts;
+    auto shape_of = [&](int i) { return op.batch_shape ? op.batch_shape[i] : 0; };
+    auto slots_of = [&](int i) { return op.tc_slots ? op.tc_slots[i] : 0; };
+    for (int i = 0; i < std::max(0, (int)n_systems); ++i) {
+        if (shape_of(i) < 0 || shape_of(i) > 6) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: batch_shape outside [0, 6]");
+        if (slots_of(i) < 0 || slots_of(i) > 8192) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: tc_slots outside [0, 8192]");
+    }
     if (!systems || n_systems < 1) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: no systems");
     if (n < 0) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: n < 0");
     if (n > 0 && !trajs) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: trajs is NULL");
@@ -438,11 +479,13 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
         if (h.path != path || h.precision != prec)
             return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: systems differ in path or precision");
     }
-    if (prec != MQCT_FP64) {
-        if (n_systems != 1) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: mixed precision takes one system per call");
-        if (prec == MQCT_FP32 && batched_width(systems[0]->s.h) == 0)
-            return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: basis too large for the batched kernel");
-    }
+    if (prec == MQCT_FP32)
+        for (int i = 0; i < n_systems; ++i) {
+            const DevSys &h = systems[i]->s.h;
+            if (batched_width(h) == 0) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: basis too large for the batched kernel");
+            if (shape_of(i) > 0 && !batched_shape_fits(h, shape_of(i) - 1))
+                return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: batch_shape does not fit a system's basis");
+        }
     if (n == 0) return MQCT_OK;
 
     const bool trajs_dev = is_device_ptr(trajs);
@@ -491,6 +534,10 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
     if (diag && diag_dev) ddiag = diag;
     else if ((diag || any_host) && (e = sa.get((void **)&ddiag, sizeof(mqct_diag) * (size_t)n)) != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync");
+    long long *dts = reinterpret_cast<long long *>(op.t_start_ns), *dtd = reinterpret_cast<long long *>(op.t_done_ns);
+    const bool ts_host = op.t_start_ns && !is_device_ptr(op.t_start_ns), td_host = op.t_done_ns && !is_device_ptr(op.t_done_ns);
+    if (ts_host && (e = sa.get((void **)&dts, sizeof(long long) * (size_t)n)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    if (td_host && (e = sa.get((void **)&dtd, sizeof(long long) * (size_t)n)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     // work order: longest estimated trajectory first
     float *keys = nullptr, *keys2 = nullptr;
     int *idx = nullptr, *order = nullptr, *queue = nullptr;
@@ -508,14 +555,86 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
     if ((e = cudaMemsetAsync(queue, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     if (prec != MQCT_FP64) {
-        BatchArgs ba;
-        ba.sys = systems[0]->s.d; ba.trajs = dtr; ba.order = order; ba.n = n; ba.queue = queue;
-        ba.pop = dpop; ba.amp = damp; ba.diag = ddiag; ba.nmax = nmax; ba.sys_idx = 0;
-        if (prec == MQCT_BF16X3) {
-            const mqct_status ts = run_tc_batched(ba, systems[0]->s.h, st);
-            if (ts != MQCT_OK) return ts;
-        } else if ((e = run_batched(ba, systems[0]->s.h, st, nullptr)) != cudaSuccess) {
-            return cuda_fail(e, "batched launch");
+        BatchArgs ba{};
+        ba.trajs = dtr; ba.pop = dpop; ba.amp = damp; ba.diag = ddiag; ba.nmax = nmax;
+        ba.t_start = dts; ba.t_done = dtd;
+        if (n_systems == 1) {
+            ba.sys = systems[0]->s.d; ba.order = order; ba.n = n; ba.queue = queue; ba.sys_idx = 0;
+            ba.shape = shape_of(0); ba.tc_slots = slots_of(0);
+            if (prec == MQCT_BF16X3) {
+                const mqct_status ts = run_tc_batched(ba, systems[0]->s.h, st);
+                if (ts != MQCT_OK) return ts;
+            } else if ((e = run_batched(ba, systems[0]->s.h, st, nullptr)) != cudaSuccess) {
+                return cuda_fail(e, "batched launch");
+            }
+        } else {
+            // uneven batch of several systems: the work order split per system (stable, so each
+            // list stays longest first) and the estimated work of each system
+            int *lists = nullptr, *counts = nullptr, *queues = nullptr;
+            double *work = nullptr;
+            if ((e = sa.get((void **)&lists, sizeof(int) * (size_t)n * n_systems)) != cudaSuccess ||
+                (e = sa.get((void **)&counts, sizeof(int) * n_systems)) != cudaSuccess ||
+                (e = sa.get((void **)&queues, sizeof(int) * n_systems)) != cudaSuccess ||
+                (e = sa.get((void **)&work, sizeof(double) * n_systems)) != cudaSuccess)
+                return cuda_fail(e, "cudaMallocAsync");
+            cudaMemsetAsync(queues, 0, sizeof(int) * n_systems, st);
+            cudaMemsetAsync(work, 0, sizeof(double) * n_systems, st);
+            k_system_work<<<(n + 255) / 256, 256, 0, st>>>(dtr, order, keys2, n, n_systems, work);
+            size_t sel_bytes = 0;
+            cub::DeviceSelect::If(nullptr, sel_bytes, order, lists, counts, n, IsSystem{dtr, 0}, st);
+            void *sel_tmp = nullptr;
+            if ((e = sa.get(&sel_tmp, sel_bytes)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+            for (int i = 0; i < n_systems; ++i)
+                if ((e = cub::DeviceSelect::If(sel_tmp, sel_bytes, order, lists + (size_t)i * n, counts + i, n,
+                                               IsSystem{dtr, i}, st)) != cudaSuccess)
+                    return cuda_fail(e, "cub::DeviceSelect");
+            std::vector<int> hc(n_systems);
+            std::vector<double> hw(n_systems);
+            if ((e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * n_systems, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(hw.data(), work, sizeof(double) * n_systems, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cuda_fail(e, "work partition");
+            if (prec == MQCT_BF16X3) {
+                // the stage-synchronous path fills the GPU with one system at a time
+                for (int i = 0; i < n_systems; ++i) {
+                    if (hc[i] == 0) continue;
+                    BatchArgs bi = ba;
+                    bi.sys = systems[i]->s.d; bi.order = lists + (size_t)i * n; bi.n = hc[i]; bi.queue = queues + i;
+                    bi.sys_idx = i; bi.tc_slots = slots_of(i);
+                    const mqct_status ts = run_tc_batched(bi, systems[i]->s.h, st);
+                    if (ts != MQCT_OK) return ts;
+                }
+            } else {
+                // one persistent batched kernel per system, concurrently on forked streams, each
+                // on a share of the SMs proportional to its estimated work
+                int dev = 0, sms = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                double tot = 0.0;
+                for (int i = 0; i < n_systems; ++i) tot += hc[i] ? hw[i] : 0.0;
+                std::vector<cudaStream_t> ss(n_systems, nullptr);
+                std::vector<cudaEvent_t> ev(n_systems + 1, nullptr);
+                for (auto &x : ev)
+                    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[n_systems], st);
+                for (int i = 0; i < n_systems && e == cudaSuccess; ++i) {
+                    if (hc[i] == 0) continue;
+                    e = cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss[i], ev[n_systems], 0);
+                    BatchArgs bi = ba;
+                    bi.sys = systems[i]->s.d; bi.order = lists + (size_t)i * n; bi.n = hc[i]; bi.queue = queues + i;
+                    bi.sys_idx = i; bi.shape = shape_of(i);
+                    bi.sm_limit = std::max(1, (int)std::lround(sms * (tot > 0 ? hw[i] / tot : 1.0 / n_systems)));
+                    if (e == cudaSuccess) e = run_batched(bi, systems[i]->s.h, ss[i], nullptr);
+                    if (e == cudaSuccess) e = cudaEventRecord(ev[i], ss[i]);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[i], 0);
+                }
+                for (int i = 0; i < n_systems; ++i)
+                    if (ss[i]) cudaStreamDestroy(ss[i]);
+                for (auto &x : ev)
+                    if (x) cudaEventDestroy(x);
+                if (e != cudaSuccess) return cuda_fail(e, "batched launch (several systems)");
+            }
         }
     } else {
     // launch shape: one warp per 32-row slice (balanced), persistent grid
@@ -533,14 +652,22 @@ extern "C" mqct_status mqct_propagate(const mqct_system *systems, int32_t n_syst
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: kernel does not fit on an SM");
     int grid = std::min(n, sms * per_sm);
-    PropArgs pa;
+    PropArgs pa{};
     pa.sys = dsys; pa.trajs = dtr; pa.order = order; pa.n = n; pa.n_systems = n_systems; pa.queue = queue;
     pa.pop = dpop; pa.amp = damp; pa.diag = ddiag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
+    pa.t_start = dts; pa.t_done = dtd;
     k_propagate_fp64<<<grid, threads, smem, st>>>(pa);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");
     }
 
-    if (!any_host) return MQCT_OK;
+    if (ts_host && (e = cudaMemcpyAsync(op.t_start_ns, dts, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync");
+    if (td_host && (e = cudaMemcpyAsync(op.t_done_ns, dtd, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync");
+    if (!any_host) {
+        if ((ts_host || td_host) && (e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        return MQCT_OK;
+    }
     if (final_pop && !pop_dev &&
         (e = cudaMemcpyAsync(final_pop, dpop, sizeof(double) * (size_t)n * nmax, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync");

@@ -50,7 +50,8 @@ struct TcState {
     int *live;                // live slots after the last step
     double *pop, *amp;
     mqct_diag *diag;
-    int nmax;
+    long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
+    int nmax, sys_idx;
     float2 *C[2];             // [n][S] stage amplitudes (phase rotated), double buffered
     float2 *A, *ACC;          // [n][S]
     float *coef;              // [2][L][S] v_l and v_l' at each slot's stage R
@@ -488,7 +489,7 @@ __device__ void tc_claim(const TcState &T, const DevSys &S, int sl)
         }
         const int t = T.order ? T.order[item] : item;
         const mqct_traj tr = T.trajs[t];
-        const bool ok = tr.system_idx == 0 && tr.dt > 0.0 && tr.e_coll > 0.0 && tr.b >= 0.0 && tr.r0 > 0.0 &&
+        const bool ok = tr.system_idx == T.sys_idx && tr.dt > 0.0 && tr.e_coll > 0.0 && tr.b >= 0.0 && tr.r0 > 0.0 &&
                         tr.b < tr.r0 && isfinite(tr.r_end) && tr.max_steps >= 0 && tr.init_state >= 0 &&
                         tr.init_state < S.n;
         if (!ok) {
@@ -498,6 +499,7 @@ __device__ void tc_claim(const TcState &T, const DevSys &S, int sl)
             }
             continue;
         }
+        if (T.t_start) T.t_start[t] = mqct_clock_ns();
         const int s0 = S.inv[tr.init_state];
         int k = (int)floor((tr.r0 - S.r_min) * S.inv_h);
         k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
@@ -590,6 +592,7 @@ __global__ void __launch_bounds__(128) k_tc_slots(TcState T, int s, int n_rowblo
                         d.t_final = m.steps * m.dt;
                         T.diag[m.traj] = d;
                     }
+                    if (T.t_done) T.t_done[m.traj] = mqct_clock_ns();
                     tc_claim(T, S, sl);  // WAIT (column initialised at stage 3) or IDLE
                 }
             } else {
@@ -637,17 +640,14 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     const int n = h.n;
     // slot count: the contraction runs one CTA per SM per (row tile, 64-slot tile), so the slots
     // fill whole waves -- one wave when the trajectories fit in it, else two (more slots only
-    // lengthen the tail of uneven trajectories); MQCT_TC_SLOTS overrides (multiple of 64)
+    // lengthen the tail of uneven trajectories); a.tc_slots overrides (rounded up to 64)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_wave = std::max(1, sms / std::max(1, h.n_tiles));
     const int want = (a.n + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
     int n_slot_tiles = want <= per_wave ? want : std::min(want, 2 * per_wave);
-    if (const char *ev = std::getenv("MQCT_TC_SLOTS")) {
-        const int v = std::atoi(ev) / kTcSlotsPerTile;
-        if (v >= 1) n_slot_tiles = v;
-    }
+    if (a.tc_slots > 0) n_slot_tiles = (a.tc_slots + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
     n_slot_tiles = std::max(1, std::min(n_slot_tiles, 8192 / kTcSlotsPerTile));
     const int S = n_slot_tiles * kTcSlotsPerTile;
     const int n_rowblocks = std::max(1, h.n_tiles);
@@ -662,7 +662,8 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     TcState T;
     std::memset(&T, 0, sizeof(T));
     T.sys = a.sys; T.trajs = a.trajs; T.order = a.order; T.n = a.n; T.S = S; T.queue = a.queue;
-    T.pop = a.pop; T.amp = a.amp; T.diag = a.diag; T.nmax = a.nmax;
+    T.pop = a.pop; T.amp = a.amp; T.diag = a.diag; T.nmax = a.nmax; T.sys_idx = a.sys_idx;
+    T.t_start = a.t_start; T.t_done = a.t_done;
     const size_t ns = (size_t)n * S;
     get((void **)&T.live, 2 * sizeof(int));
     get((void **)&T.C[0], sizeof(float2) * ns);

@@ -208,6 +208,7 @@ def test_struct_layouts_match_header(L, tmp_path):
                                           "n_row_tiles", "tc_kchunks"]),
         "mqct_diatom_params": (api.DiatomParams, ["jmax", "bconst", "mu", "n_terms", "A", "beta", "c6", "rd",
                                                   "n_grid", "r_min", "with_params", "path", "precision"]),
+        "mqct_propagate_opts": (api.PropagateOpts, ["t_start_ns", "t_done_ns", "batch_shape", "tc_slots"]),
         "mqct_asym_params": (api.AsymParams, ["jmax", "A", "B", "C", "max_states", "mu", "n_terms", "lam", "mproj",
                                               "coef", "beta", "c6", "rd", "n_grid", "r_min", "r_max",
                                               "with_params", "path", "precision", "tau_out"]),
