@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-traj", type=int, default=0,
                     help="run a seeded subset of this many trajectories (profiling of a small case)")
+    ap.add_argument("--max-steps", type=int, default=0,
+                    help="cap every trajectory at this many RK4 steps (profiling a small case; not a bench line)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the launch-shape candidates on a probe sample first and use the fastest")
     ap.add_argument("--workload", default="n441", choices=["n441", "n1600", "asym1580", "mix"],
@@ -238,6 +240,9 @@ def gpu_arm(args):
         else:
             ts = oracle_sample(ps[0], ts, args.max_traj, seed=5)
         workload = f"seeded subset of {ts.n} trajectories of: {workload}"
+    if args.max_steps:
+        ts.max_steps = args.max_steps
+        workload = f"every trajectory capped at {args.max_steps} steps (profiling case) of: {workload}"
     systems = [make_system(api, q, args.path, args.precision) for q in ps]
     infos = [s_.info for s_ in systems]
     tr = api.make_trajs(ts, systems)
@@ -412,7 +417,10 @@ def gpu_arm(args):
         ms64 = a_.elapsed_time(b_)
         d64 = api.diag_to_numpy(d64)
         same = d64["steps"] == dg["steps"][cidx]
-        dp = np.abs(pop_m - pop64.cpu().numpy()[:, :pop_m.shape[1]])
+        # only the first N_t entries of a row belong to its system (the rest are not written)
+        width = np.array([infos[k]["n_states"] for k in sidx[cidx]])
+        valid = np.arange(pop_m.shape[1])[None, :] < width[:, None]
+        dp = np.where(valid, np.abs(pop_m - pop64.cpu().numpy()[:, :pop_m.shape[1]]), 0.0)
         compare = {"path": "plain", "precision": "fp64", "value": float(d64["steps"].sum()) * ws / (ms64 * 1e-3),
                    "unit": "traj-steps/s", "ms": ms64, "timed_runs": 1, "trajectories": int(len(cidx)),
                    "max_abs_dP_vs_fp64": float(dp.max()), "max_abs_dP_same_steps": float(dp[same].max()),
