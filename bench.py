@@ -55,8 +55,9 @@ def parse():
                     help="run a seeded subset of this many trajectories (profiling of a small case)")
     ap.add_argument("--max-steps", type=int, default=0,
                     help="cap every trajectory at this many RK4 steps (profiling a small case; not a bench line)")
-    ap.add_argument("--autotune", action="store_true",
-                    help="time the launch-shape candidates on a probe sample first and use the fastest")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the library's automatic launch shapes instead of timing the candidates on a "
+                         "probe sample first (outside the timed region) and using the fastest")
     ap.add_argument("--workload", default="n441", choices=["n441", "n1600", "asym1580", "mix"],
                     help="n441: the 3072-trajectory N = 441 workload; n1600: 768 trajectories with N = 1600; "
                          "asym1580: the N = 1580 asymmetric-top workload (a seeded subset, --max-traj, default 1024); "

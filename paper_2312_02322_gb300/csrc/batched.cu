@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(T, 512 / T) k_batched_f32(BatchArgs a)
                     const int *ptr = S.csr_ptr + (size_t)f * (n + 1);
                     const int q0 = __ldg(ptr + r), q1 = __ldg(ptr + r + 1);
                     float2 y[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+                    // two entries per iteration: their loads are in flight together (same sum order)
+#pragma unroll 2
                     for (int q = q0; q < q1; ++q) {
                         const int col = __ldg(S.csr_col + q);
                         const float gv = __ldg(S.csr_val + q);
