@@ -249,8 +249,9 @@ typedef struct {
                              host or device pointer                                               */
     int64_t *t_done_ns;   /* [n] GPU global-timer value (ns) when its results were written, or NULL */
     const int32_t *batch_shape; /* [n_systems] HOST array or NULL: FP32 batched kernel shape of each
-                             system, 0 = automatic (widest that fits), 1..6 = (slots per CTA,
-                             threads) of (32,256) (16,256) (8,256) (16,512) (8,512) (4,512); a shape
+                             system, 0 = automatic (widest of the first six that fits), 1..7 =
+                             (slots per CTA, threads) of (32,256) (16,256) (8,256) (16,512) (8,512)
+                             (4,512) (4,256); a shape
                              that does not fit the system's basis -> MQCT_ERR_UNSUPPORTED          */
     const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: BF16X3 trajectories in flight per
                              system (rounded up to a multiple of 64, at most 8192), 0 = automatic

@@ -75,7 +75,7 @@ class PropagateOpts(C.Structure):
 
 
 # (slots per CTA, threads) of the FP32 batched kernel for batch_shape = index + 1
-BATCH_SHAPES = [(32, 256), (16, 256), (8, 256), (16, 512), (8, 512), (4, 512)]
+BATCH_SHAPES = [(32, 256), (16, 256), (8, 256), (16, 512), (8, 512), (4, 512), (4, 256)]
 
 TRAJ_DTYPE = np.dtype([("e_coll", "<f8"), ("b", "<f8"), ("r0", "<f8"), ("r_end", "<f8"), ("dt", "<f8"),
                        ("init_state", "<i4"), ("max_steps", "<i4"), ("system_idx", "<i4"), ("_pad", "<i4")])

@@ -511,13 +511,14 @@ bool batched_shape_fits(const DevSys &h, int i)
         case 3: return batched_fits<16, 512>(h, full);
         case 4: return batched_fits<8, 512>(h, full);
         case 5: return batched_fits<4, 512>(h, full);
+        case 6: return batched_fits<4, 256>(h, half);
         default: return false;
     }
 }
 
 int batched_width(const DevSys &h)
 {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 6; ++i)  // automatic choice: the first six, widest first
         if (batched_shape_fits(h, i)) return kBatchShapes[i][0] * 1000 + kBatchShapes[i][1];
     return 0;
 }
@@ -530,7 +531,7 @@ cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int idx = -1;
     if (a.shape > 0) {
-        if (a.shape > 6 || !batched_shape_fits(h, a.shape - 1)) return cudaErrorInvalidConfiguration;
+        if (a.shape > 7 || !batched_shape_fits(h, a.shape - 1)) return cudaErrorInvalidConfiguration;
         idx = a.shape - 1;
     } else {
         for (int i = 0; i < 6 && idx < 0; ++i)
@@ -545,6 +546,7 @@ cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, in
         case 3: return launch_batched<16, 512>(a, h, sms, st);
         case 4: return launch_batched<8, 512>(a, h, sms, st);
         case 5: return launch_batched<4, 512>(a, h, sms, st);
+        case 6: return launch_batched<4, 256>(a, h, sms, st);
         default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -130,8 +130,9 @@ struct BatchArgs {
     int sm_limit;  // FP32 batched kernel: SMs its persistent grid may fill (0 = all)
     int tc_slots;  // tensor-core path: trajectories in flight (0 = automatic)
 };
-// the (slots per CTA, threads) instances of the FP32 batched kernel, widest first
-constexpr int kBatchShapes[6][2] = {{32, 256}, {16, 256}, {8, 256}, {16, 512}, {8, 512}, {4, 512}};
+// the (slots per CTA, threads) instances of the FP32 batched kernel; the automatic choice takes
+// the first that fits (the last one is only ever chosen on request, e.g. by the autotuner)
+constexpr int kBatchShapes[7][2] = {{32, 256}, {16, 256}, {8, 256}, {16, 512}, {8, 512}, {4, 512}, {4, 256}};
 // true when shape index i (0-based) fits the system's basis
 bool batched_shape_fits(const DevSys &h, int i);
 cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width);

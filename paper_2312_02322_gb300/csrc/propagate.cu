@@ -460,7 +460,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
     auto shape_of = [&](int i) { return op.batch_shape ? op.batch_shape[i] : 0; };
     auto slots_of = [&](int i) { return op.tc_slots ? op.tc_slots[i] : 0; };
     for (int i = 0; i < std::max(0, (int)n_systems); ++i) {
-        if (shape_of(i) < 0 || shape_of(i) > 6) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: batch_shape outside [0, 6]");
+        if (shape_of(i) < 0 || shape_of(i) > 7) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: batch_shape outside [0, 7]");
         if (slots_of(i) < 0 || slots_of(i) > 8192) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: tc_slots outside [0, 8192]");
     }
     if (!systems || n_systems < 1) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: no systems");

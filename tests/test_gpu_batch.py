@@ -89,7 +89,7 @@ def test_shape_options_validated(mq):
     s = mq.System.diatom(p, path="factorised", precision="fp32")
     tr = mq.make_trajs(ts, s)
     with pytest.raises(mq.MQCTError) as e:
-        mq.propagate(s, tr, device=False, batch_shape=7)
+        mq.propagate(s, tr, device=False, batch_shape=8)
     assert e.value.status == mq.ERR_INVALID_ARG
     big = mq.System.diatom(W.diatom_pes_params(jmax=39, n_grid=60), path="factorised", precision="fp32")
     trb = mq.make_trajs(ts, big)
