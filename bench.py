@@ -470,6 +470,14 @@ def gpu_arm(args):
         return
     # order keys, CUB radix sort passes, the propagation launch(es), level and group sums per system
     launches_per_step = 3 + len(systems) + 2 * len(groups)
+    if args.precision == "bf16x3":
+        # the stage-synchronous path: graphs of 16 steps x 4 stages x (stage + slot kernel) per
+        # system, run until the longest trajectory ends, plus the slot initialisation
+        launches_per_step = 3 + 2 * len(groups)
+        for i in range(len(systems)):
+            rows = sidx == i
+            if rows.any():
+                launches_per_step += 1 + 128 * int(np.ceil((int(dg["steps"][rows].max()) + 1) / 16.0))
     cfg = {"workload": workload, "path": args.path, "precision": args.precision,
            "n_states": [inf["n_states"] for inf in infos] if len(infos) > 1 else infos[0]["n_states"],
            "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,

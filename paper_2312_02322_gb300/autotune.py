@@ -46,9 +46,9 @@ def candidates(system, n_traj: int) -> list[dict]:
         import torch
 
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        per_wave = max(1, sms // max(1, info["n_row_tiles"]))
+        nt = max(1, info["n_row_tiles"])
         top = min(8192, 64 * ((n_traj + 63) // 64))
-        out = sorted({min(top, 64 * per_wave * k) for k in (1, 2, 3, 4)})
+        out = sorted({min(top, 64 * max(1, (k * sms) // nt)) for k in (1, 2, 3, 4)})
         return [{"tc_slots": s} for s in out]
     return [{}]
 

@@ -644,9 +644,10 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_wave = std::max(1, sms / std::max(1, h.n_tiles));
+    const int nt = std::max(1, h.n_tiles);
+    const int one_wave = std::max(1, sms / nt), two_waves = std::max(1, 2 * sms / nt);
     const int want = (a.n + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
-    int n_slot_tiles = want <= per_wave ? want : std::min(want, 2 * per_wave);
+    int n_slot_tiles = want <= one_wave ? want : std::min(want, two_waves);
     if (a.tc_slots > 0) n_slot_tiles = (a.tc_slots + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
     n_slot_tiles = std::max(1, std::min(n_slot_tiles, 8192 / kTcSlotsPerTile));
     const int S = n_slot_tiles * kTcSlotsPerTile;
