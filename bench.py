@@ -67,6 +67,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """The largest value of x over all ranks (the whole job's time is its slowest rank's);
+    x itself when there is one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -321,10 +333,7 @@ def gpu_arm(args):
         dist.barrier()
     ms = sum(e[0].elapsed_time(e[2]) for e in ev)
     k_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     clocks = clk.summary()
     value = traj_steps * ws / (ms * 1e-3 / args.steps)
     # ---- roofline of the dominant launch: algorithmic work summed over the systems
