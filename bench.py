@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """MQCT trajectory-steps/s on one GB300 (and N GPUs as independent replicas).
 
-Workload: the N = 441 atom + diatom system (j <= 20), E in {100, 300, 1000, 3000} cm^-1,
-j' in {0, 1, 2}, 256 midpoint impact parameters on 0-15 bohr per (E, j'): 3072
-trajectories, 400-point spline grid, RK4 dt = 5 a.u.  One step = propagate every
-trajectory to its end (Eqs. 4-10) plus the cross-section reduction (Sec. II), inputs
-resident in HBM.  Prints one JSON line (rank 0).
+Default workload: the N = 441 atom + diatom system (j <= 20), E in {100, 300, 1000, 3000}
+cm^-1, j' in {0, 1, 2}, 256 midpoint impact parameters on 0-15 bohr per (E, j'): 3072
+trajectories, 400-point spline grid, RK4 dt = 5 a.u.  One step = propagate every trajectory to
+its end (Eqs. 4-10) plus the cross-section reduction (Sec. II), inputs resident in HBM.
+Other workloads: --workload n1600 (N = 1600 diatom), asym1580 (N = 1580 asymmetric top),
+mix (uneven four-basis batch in one call).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--path plain|factorised] [--precision fp64|fp32]
+                  [--workload n441|n1600|asym1580|mix] [--path plain|factorised]
+                  [--precision fp64|fp32|bf16x3] [--no-autotune] [--max-traj M]
 """
 from __future__ import annotations
 
