@@ -235,9 +235,12 @@ mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out);
  *   diag       [n] mqct_diag; or NULL
  * Work order: trajectories are claimed from a device work queue, longest estimated
  * first.  Scratch memory is taken with stream-ordered allocation on `cuda_stream`.
- * With device output pointers the call only enqueues work and returns MQCT_OK; with
- * any host output it synchronises the stream and returns MQCT_ERR_TRAJ if a trajectory
- * status is non-zero.  Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_OOM,
+ * With device output pointers the FP64 and single-system FP32 calls only enqueue work and
+ * return MQCT_OK; the BF16X3 path synchronises the stream between chunks of 16 steps (it
+ * checks on the host whether trajectories are still running), and FP32 / BF16X3 calls with
+ * several systems synchronise it once to size the per-system launches.  With any host
+ * output the call synchronises the stream and returns MQCT_ERR_TRAJ if a trajectory status
+ * is non-zero.  Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_OOM,
  * MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
 mqct_status mqct_propagate(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
                            double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream);
@@ -251,8 +254,8 @@ typedef struct {
     const int32_t *batch_shape; /* [n_systems] HOST array or NULL: FP32 batched kernel shape of each
                              system, 0 = automatic (widest of the first six that fits), 1..7 =
                              (slots per CTA, threads) of (32,256) (16,256) (8,256) (16,512) (8,512)
-                             (4,512) (4,256); a shape
-                             that does not fit the system's basis -> MQCT_ERR_UNSUPPORTED          */
+                             (4,512) (4,256); a shape that does not fit the system's basis
+                             -> MQCT_ERR_UNSUPPORTED                                             */
     const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: BF16X3 trajectories in flight per
                              system (rounded up to a multiple of 64, at most 8192), 0 = automatic
                              (one or two waves of the GPU)                                       */
