@@ -64,6 +64,11 @@ def parse():
                     help="n441: the 3072-trajectory N = 441 workload; n1600: 768 trajectories with N = 1600; "
                          "asym1580: the N = 1580 asymmetric-top workload (a seeded subset, --max-traj, default 1024); "
                          "mix: the uneven four-basis batch (first --max-traj of its 50000 trajectories, default 4096)")
+    ap.add_argument("--batch-shape", type=int, default=0,
+                    help="FP32 batched kernel shape 1..7 for every system (see mqct_propagate_opts); implies "
+                         "--no-autotune")
+    ap.add_argument("--no-n1600", dest="n1600", action="store_false",
+                    help="skip the N = 1600 block (the metric's second basis size, timed after the headline)")
     ap.add_argument("--energy", type=float, default=0.0,
                     help="keep only the trajectories at this collision energy (cm^-1)")
     return ap.parse_args()
@@ -214,6 +219,165 @@ def reference_arm(args):
     }))
 
 
+# ---------------------------------------------------------------------------- roofline
+KERNEL_SRC = {"k_propagate_fp64": "propagate.cu", "k_batched_f32": "batched.cu", "k_tc_stage": "tc_batched.cu"}
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per trajectory-stage of `kernel` from its committed ncu summary
+    (profiles/<kernel>_*.md lines "dram_bytes_per_traj_stage:" and "source_sha256:"), or None
+    when there is none or the kernel's source has changed since the counters were taken."""
+    import glob
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2312_02322_gb300", "csrc", KERNEL_SRC[kernel])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+        kv = {}
+        for line in open(f):
+            if ":" in line and line.split(":", 1)[0].strip() in ("dram_bytes_per_traj_stage", "source_sha256"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha256") == sha and "dram_bytes_per_traj_stage" in kv:
+            return float(kv["dram_bytes_per_traj_stage"]), os.path.relpath(f, ROOT)
+    return None, None
+
+
+def roofline_of(api, path, precision, infos, steps, sidx, k_ms):
+    """Roofline object of the dominant kernel of one propagate call (its time k_ms).
+
+    Units: trajectory-stages (4 per RK4 step, plus the final evaluation of each trajectory).
+    Useful work per trajectory-stage: the coupling contraction, 4 flops per stored non-zero of
+    the coupling (factorised: sum over terms of nnz(G^l); plain: 4 spline coefficients x nnz(M));
+    the per-state work (phases, Coriolis stencil, RK4 update, reductions) is reported beside it,
+    not counted."""
+    useful = per_state = exec_tc = stages_tot = table_bytes = 0.0
+    for i, inf in enumerate(infos):
+        rows = sidx == i
+        stages = 4.0 * float(steps[rows].sum()) + float(rows.sum())
+        n = inf["n_states"]
+        if path == "plain":
+            useful += 16.0 * inf["table_nnz"] * stages
+            per_state += 40.0 * n * stages
+            table_bytes += 32.0 * inf["table_nnz"] * (1.0 if precision == "fp64" else 0.5) * stages
+        else:
+            useful += 4.0 * inf["glambda_nnz"] * stages
+            per_state += (8.0 * inf["n_terms"] + 40.0) * n * stages
+        exec_tc += inf["tc_kchunks"] * 3 * (2.0 * 128 * 128 * 16) / 64.0 * stages
+        stages_tot += stages
+    kernel = {"fp64": "k_propagate_fp64", "fp32": "k_batched_f32", "bf16x3": "k_tc_stage"}[precision]
+    per_stage_traffic, prof = profile_traffic(kernel)
+    traffic = None if per_stage_traffic is None else per_stage_traffic * stages_tot
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    if precision == "bf16x3":
+        # executed tensor work: per stage, per 64-slot tile, for every stored term and row tile its
+        # non-zero 16-column K chunks x 3 split products of a 128 x 128 x 16 MMA; time = the whole
+        # propagate call (stage and slot kernels): a lower bound
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        ach = exec_tc / (k_ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                "traffic": traffic, "kernel": "k_tc_stage (timed with the whole propagate call)",
+                "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json)",
+                "executed_flops_per_traj_stage": exec_tc / stages_tot,
+                "useful_flops_per_traj_stage": useful / stages_tot, "useful_over_executed": useful / exec_tc,
+                "traj_stages_per_launch": stages_tot, "kernel_ms": k_ms, "traffic_source": prof}
+    fp_peak = api.fma_rate("fp64") if precision == "fp64" else api.fma_rate("fp32")
+    achieved = useful / (k_ms * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": fp_peak / 1e3, "unit": "TFLOP/s",
+           "frac": achieved * 1e3 / fp_peak, "traffic": traffic, "kernel": kernel,
+           "peak_source": f"of measured {precision.upper()} FMA rate (library probe mqct_probe_fma_rate)",
+           "useful_flops_per_traj_stage": useful / stages_tot,
+           "per_state_flops_per_traj_stage": per_state / stages_tot,
+           "frac_with_per_state_work": (useful + per_state) / (k_ms * 1e-3) / fp_peak / 1e9,
+           "traj_stages_per_launch": stages_tot, "kernel_ms": k_ms, "traffic_source": prof}
+    hbm = peaks.get("hbm_gbs")
+    if table_bytes and hbm:
+        gbs = table_bytes / (k_ms * 1e-3) / 1e9
+        out["hbm_view"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                           "note": "algorithmic table bytes; the table is L2-resident, so DRAM traffic is lower"}
+    return out
+
+
+def compare_fp64(api, ps, tr, cidx, steps_m, pop_m, sidx, infos, dev, stream, flush, value, ws, runs=3):
+    """The trajectories cidx of a measured batch through the plain FP64 path: its throughput
+    (median of `runs` timed runs, L2 flushed before each) and the largest population difference of
+    the measured path against it ("same error")."""
+    import torch
+
+    s64 = [make_system(api, q, "plain", "fp64") for q in ps]
+    trc = torch.from_numpy(tr[cidx].view(np.uint8).copy()).to(dev)
+    pop64, _, d64 = api.propagate(s64, trc, device=True, stream=stream)  # also the warm-up
+    torch.cuda.synchronize()
+    d64 = api.diag_to_numpy(d64)
+    ms_runs = []
+    for _ in range(runs):
+        flush.zero_()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        api.propagate(s64, trc, want_pop=False, want_diag=False, device=True, stream=stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms_runs.append(a_.elapsed_time(b_))
+    ms64 = float(np.median(ms_runs))
+    same = d64["steps"] == steps_m[cidx]
+    # only the first N_t entries of a row belong to its system (the rest are not written)
+    width = np.array([infos[k]["n_states"] for k in sidx[cidx]])
+    valid = np.arange(pop_m.shape[1])[None, :] < width[:, None]
+    dp = np.where(valid, np.abs(pop_m - pop64.cpu().numpy()[:, :pop_m.shape[1]]), 0.0)
+    v64 = float(d64["steps"].sum()) * ws / (ms64 * 1e-3)
+    return {"path": "plain", "precision": "fp64", "value": v64, "unit": "traj-steps/s", "ms": ms64,
+            "ms_runs": ms_runs, "timed_runs": runs, "trajectories": int(len(cidx)),
+            "max_abs_dP_vs_fp64": float(dp.max()), "max_abs_dP_same_steps": float(dp[same].max()),
+            "trajectories_same_steps": int(same.sum()), "speedup": value / v64}
+
+
+def n1600_block(api, args, dev, stream, flush, ws, runs=3):
+    """The N = 1600 workload (768 trajectories) through the measured precision and, beside it,
+    the plain FP64 path: traj-steps/s of each (median of `runs` timed runs, L2 flushed before
+    each), max |dP| between them, sigma-sets/s."""
+    import torch
+
+    p, ts = W.workload2_n1600()
+    sys_ = make_system(api, p, args.path, args.precision)
+    info = sys_.info
+    tr = api.make_trajs(ts, sys_)
+    trd = torch.from_numpy(tr.view(np.uint8).copy()).to(dev)
+    tune = {}
+    if args.autotune and args.precision != "fp64":
+        from paper_2312_02322_gb300 import autotune
+
+        t_ = autotune.tune_batch([sys_], tr)
+        tune = {"batch_shape": t_["batch_shape"], "tc_slots": t_["tc_slots"]}
+    pop, _, diag = api.propagate(sys_, trd, device=True, stream=stream, **tune)
+    torch.cuda.synchronize()
+    dg = api.diag_to_numpy(diag)
+    w = torch.from_numpy(api.sigma_weights(ts, dg["status"])).to(dev)
+    g = torch.from_numpy(ts.group.astype(np.int32)).to(dev)
+    ms_runs = []
+    for _ in range(runs):
+        flush.zero_()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        pp, _, _ = api.propagate(sys_, trd, want_diag=False, device=True, stream=stream, **tune)
+        api.cross_sections(sys_, pp, w, g, ts.n_groups, stream=stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms_runs.append(a_.elapsed_time(b_))
+    ms = float(np.median(ms_runs))
+    steps = float(dg["steps"].sum())
+    value = steps * ws / (ms * 1e-3)
+    sidx = np.zeros(ts.n, int)
+    comp = compare_fp64(api, [p], tr, np.arange(ts.n), dg["steps"], pop.cpu().numpy(), sidx, [info], dev, stream,
+                        flush, value, ws, runs=runs)
+    return {"workload": WORKLOAD_1600, "path": args.path, "precision": args.precision, "value": value,
+            "unit": "traj-steps/s", "ms_per_step": ms, "ms_runs": ms_runs, "timed_runs": runs,
+            "traj_steps_per_step": steps, "sigma_sets_per_s": ts.n_groups * ws / (ms * 1e-3),
+            "launch_option": tune, "comparison": comp}
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def gpu_arm(args):
     import torch
@@ -264,7 +428,10 @@ def gpu_arm(args):
     sidx = tr["system_idx"].astype(int)
     trd = torch.from_numpy(tr.view(np.uint8).copy()).to(dev)
     tune = {}
-    if args.autotune and args.precision != "fp64":
+    if args.batch_shape:
+        tune = {"batch_shape": args.batch_shape}
+        tune_report = None
+    elif args.autotune and args.precision != "fp64":
         from paper_2312_02322_gb300 import autotune
 
         t_ = autotune.tune_batch(systems, tr)
@@ -339,51 +506,7 @@ def gpu_arm(args):
     clocks = clk.summary()
     value = traj_steps * ws / (ms * 1e-3 / args.steps)
     # ---- roofline of the dominant launch: algorithmic work summed over the systems
-    flops_tot = bytes_tot = exec_tot = 0.0
-    stages_tot = 0.0
-    for i, s_ in enumerate(systems):
-        inf = infos[i]
-        rows = sidx == i
-        stages = 4.0 * float(dg["steps"][rows].sum()) + float(rows.sum())  # + one final evaluation each
-        n = inf["n_states"]
-        if args.path == "plain":
-            fs = 16.0 * inf["table_nnz"] + 40.0 * n
-            bytes_tot += 32.0 * inf["table_nnz"] * (1.0 if args.precision == "fp64" else 0.5) * stages
-        else:
-            fs = 4.0 * inf["glambda_nnz"] + (8.0 * inf["n_terms"] + 40.0) * n
-        flops_tot += fs * stages
-        exec_tot += inf["tc_kchunks"] * 3 * (2.0 * 128 * 128 * 16) / 64.0 * stages
-        stages_tot += stages
-    fp_peak = api.fma_rate("fp64") if args.precision == "fp64" else api.fma_rate("fp32")
-    achieved = flops_tot / (k_ms * 1e-3) / 1e12
-    kernel = {"fp64": "k_propagate_fp64", "fp32": "k_batched_f32", "bf16x3": "k_tc_stage"}[args.precision]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp_peak / 1e3, "unit": "TFLOP/s",
-                "frac": achieved * 1e3 / fp_peak, "traffic": None, "kernel": kernel,
-                "peak_source": f"measured {args.precision.upper()} FMA probe (mqct_probe_fma_rate)",
-                "algorithmic_flops_per_traj_stage": flops_tot / stages_tot, "traj_stages_per_launch": stages_tot,
-                "kernel_ms": k_ms}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm = peaks.get("hbm_gbs")
-    except Exception:
-        peaks, hbm = {}, None
-    if args.precision == "bf16x3":
-        # executed tensor work: per stage, per 64-slot tile, for every stored term and row tile its
-        # non-zero 16-column K chunks x 3 split products of a 128 x 128 x 16 MMA; time = the whole
-        # propagate call (stage and slot kernels): a lower bound
-        bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        ach = exec_tot / (k_ms * 1e-3) / 1e12
-        roofline = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                    "traffic": None, "kernel": "k_tc_stage (timed with the whole propagate call)",
-                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
-                    "executed_flops_per_traj_stage": exec_tot / stages_tot,
-                    "useful_flops_per_traj_stage": flops_tot / stages_tot,
-                    "useful_over_executed": flops_tot / exec_tot, "traj_stages_per_launch": stages_tot,
-                    "kernel_ms": k_ms}
-    if bytes_tot and hbm:
-        gbs = bytes_tot / (k_ms * 1e-3) / 1e9
-        roofline["hbm_view"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
-                                "note": "algorithmic table bytes; the table is L2-resident, so DRAM traffic is lower"}
+    roofline = roofline_of(api, args.path, args.precision, infos, dg["steps"], sidx, k_ms)
 
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -417,28 +540,13 @@ def gpu_arm(args):
                 cidx = strat_idx(ts, 128, seed=9)
         else:
             cidx = np.arange(ts.n)
-        pop_m = pop.cpu().numpy()[cidx]
-        s64 = [make_system(api, q, "plain", "fp64") for q in ps]
-        trc = torch.from_numpy(tr[cidx].view(np.uint8).copy()).to(dev)
-        flush.zero_()
-        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        pop64, _, d64 = api.propagate(s64, trc, device=True, stream=stream)
-        b_.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a_.elapsed_time(b_)
-        d64 = api.diag_to_numpy(d64)
-        same = d64["steps"] == dg["steps"][cidx]
-        # only the first N_t entries of a row belong to its system (the rest are not written)
-        width = np.array([infos[k]["n_states"] for k in sidx[cidx]])
-        valid = np.arange(pop_m.shape[1])[None, :] < width[:, None]
-        dp = np.where(valid, np.abs(pop_m - pop64.cpu().numpy()[:, :pop_m.shape[1]]), 0.0)
-        compare = {"path": "plain", "precision": "fp64", "value": float(d64["steps"].sum()) * ws / (ms64 * 1e-3),
-                   "unit": "traj-steps/s", "ms": ms64, "timed_runs": 1, "trajectories": int(len(cidx)),
-                   "max_abs_dP_vs_fp64": float(dp.max()), "max_abs_dP_same_steps": float(dp[same].max()),
-                   "trajectories_same_steps": int(same.sum()),
-                   "speedup": value / (float(d64["steps"].sum()) * ws / (ms64 * 1e-3))}
-        del s64
+        compare = compare_fp64(api, ps, tr, cidx, dg["steps"], pop.cpu().numpy()[cidx], sidx, infos, dev, stream,
+                               flush, value, ws)
+
+    # the N = 1600 workload, the metric's second basis size: the same measurement in short form
+    n1600 = None
+    if args.n1600 and args.workload == "n441" and not args.max_traj and not args.max_steps and not args.energy:
+        n1600 = n1600_block(api, args, dev, stream, flush, ws)
 
     adj = None
     if args.adjoint:
@@ -489,6 +597,7 @@ def gpu_arm(args):
             rows = sidx == i
             if rows.any():
                 launches_per_step += 1 + 128 * int(np.ceil((int(dg["steps"][rows].max()) + 1) / 16.0))
+    sigma_sets = sum(sub.n_groups for _, _, sub in groups)
     cfg = {"workload": workload, "path": args.path, "precision": args.precision,
            "n_states": [inf["n_states"] for inf in infos] if len(infos) > 1 else infos[0]["n_states"],
            "trajectories": ts.n, "traj_steps_per_step": traj_steps, "excluded_trajectories": n_bad,
@@ -502,6 +611,9 @@ def gpu_arm(args):
         "data": "synthetic", "config": cfg,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps, "latency": latency, "comparison": compare, "adjoint": adj,
+        "sigma_sets_per_s": sigma_sets * ws / (ms * 1e-3 / args.steps),
+        "sigma_set": "all cross sections out of one (collision energy, initial level) group",
+        "n1600": n1600,
     }))
 
 

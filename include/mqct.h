@@ -281,12 +281,15 @@ mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_systems, con
  *   - at most 16 systems per call (the size of that array); more -> MQCT_ERR_INVALID_ARG;
  *   - trajs, final_pop, final_amp and diag must be DEVICE pointers (outputs may be NULL);
  *     layouts as for mqct_propagate; trajectories are claimed in the caller's order;
- *   - the call only enqueues work on `cuda_stream` and returns MQCT_OK; per-trajectory
- *     status is in diag;
+ *   - the call only enqueues work on `cuda_stream` (two launches: one writes the system views,
+ *     which travel by value in its launch parameters, into the array and clears the counter;
+ *     the other propagates) and returns MQCT_OK; per-trajectory status is in diag;
  *   - all calls share the one scratch array: two calls whose work overlaps on the GPU (on
  *     different streams, or from different threads without ordering) race on it;
- *   - the first call on a device looks up the array's device address on that device (with
- *     it current); make that first call before any stream capture.
+ *   - the first call in a CUDA context (per device, with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.  The address is
+ *     cached per context: a context created later on the device (e.g. after cudaDeviceReset)
+ *     gets its own lookup on its first call.
  * Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_CUDA. */
 mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
                                    double *final_pop, double *final_amp, mqct_diag *diag, void *cuda_stream);

@@ -109,6 +109,8 @@ def lib():
             L.mqct_adjoint.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, vp]
             L.mqct_probe_fma_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
             L.mqct_probe_fma_rate.restype = C.c_int
+            L.mqct_probe_op_latency.argtypes = [i32, i32, C.POINTER(C.c_double), vp]
+            L.mqct_probe_op_latency.restype = C.c_int
             L.mqct_last_error.restype = C.c_char_p
             L.mqct_version.restype = C.c_char_p
             for f in ("mqct_build_diatom", "mqct_build_asym_top", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
@@ -410,6 +412,15 @@ def fma_rate(kind: str = "fp64", stream=None) -> float:
     """Measured FMA throughput of the current GPU in GFLOP/s ("fp64" or "fp32")."""
     out = C.c_double()
     _check(lib().mqct_probe_fma_rate({"fp64": 0, "fp32": 1}[kind], C.byref(out), _stream(stream)))
+    return out.value
+
+
+def op_latency(kind: str = "dfma", warps: int = 1, stream=None) -> float:
+    """SM clock cycles per operation of a dependent chain ("dfma", "ffma", "ddiv", "cvt"), with
+    `warps` warps of one CTA running chains at once (mqct_probe_op_latency)."""
+    out = C.c_double()
+    k = {"dfma": 0, "ffma": 1, "ddiv": 2, "cvt": 3}[kind]
+    _check(lib().mqct_probe_op_latency(k, int(warps), C.byref(out), _stream(stream)))
     return out.value
 
 

@@ -1,6 +1,6 @@
 """Launch-shape autotuner for the mixed-precision trajectory paths.
 
-The FP32 batched kernel exists in six (slots per CTA, threads) instances and the BF16X3 path
+The FP32 batched kernel exists in seven (slots per CTA, threads) instances and the BF16X3 path
 runs a chosen number of trajectories in flight; which is fastest depends on the basis size, the
 density of the coupling terms and the GPU.  ``tune`` times short probe runs of every candidate
 on a sample of the caller's trajectories, each capped at ``probe_steps`` RK4 steps so that a

@@ -8,11 +8,11 @@
 // takes with stream-ordered allocation.  This entry point takes that scratch from one
 // file-scope device array instead, so it allocates nothing.  The caller still passes its
 // own device buffers for every input and output.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <mutex>
-#include <vector>
 
 #include "internal.h"
 
@@ -26,25 +26,76 @@ constexpr size_t kNoallocQueueBytes = 256;
 constexpr size_t kNoallocBytes = kNoallocQueueBytes + sizeof(DevSys) * kNoallocMaxSystems;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
+// One launch writes the system views into the scratch array and clears the work counter: the
+// views travel by value in the launch's parameter block, so the call stages nothing in host
+// memory and needs no copy from a host buffer that might be gone before the copy runs.
+struct NoallocViews {
+    DevSys v[kNoallocMaxSystems];
+};
+static_assert(sizeof(NoallocViews) <= 30000, "system views exceed the kernel parameter space");
+
+__global__ void k_noalloc_setup(NoallocViews views, int n_systems, DevSys *dst, int *queue)
+{
+    const int i = threadIdx.x;
+    if (i < n_systems) dst[i] = views.v[i];
+    if (i == 0) *queue = 0;  // the counter keeps the previous call's value
+}
+
 namespace {
 
-// The symbol name is a host-side stand-in; the device address is looked up once per device,
-// with that device current.
+// The array's name is a host-side stand-in for it; its device address is looked up with the
+// device current, the first time a call runs in a CUDA context (the primary context of a device
+// unless the caller made another current).  The cache is keyed by the context's unique id, so a
+// context created after cudaDeviceReset (whose module load may place the array elsewhere) gets a
+// fresh lookup instead of the old address.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    void *addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+cudaError_t current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+        get_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    return cudaSuccess;
+}
 
 cudaError_t scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchAddr &c = g_scratch_addr[dev];
+    if (!c.addr || c.ctx_id != id) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        c.addr = p;
+        c.ctx_id = id;
     }
-    *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    *out = static_cast<unsigned char *>(c.addr);
     return cudaSuccess;
 }
 
@@ -95,13 +146,10 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
     if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static scratch)");
     int *queue = reinterpret_cast<int *>(scratch);
     DevSys *dsys = reinterpret_cast<DevSys *>(scratch + kNoallocQueueBytes);
-    // system views: the copy is staged from the host vector before cudaMemcpyAsync returns
-    std::vector<DevSys> hv(n_systems);
-    for (int i = 0; i < n_systems; ++i) hv[i] = systems[i]->s.h;
-    if ((e = cudaMemcpyAsync(dsys, hv.data(), sizeof(DevSys) * n_systems, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync (system views)");
-    // the counter keeps the previous call's value: clear it
-    if ((e = cudaMemsetAsync(queue, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    NoallocViews views;
+    for (int i = 0; i < n_systems; ++i) views.v[i] = systems[i]->s.h;
+    k_noalloc_setup<<<1, 32, 0, st>>>(views, n_systems, dsys, queue);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_noalloc_setup launch");
 
     const int maxw = kPropThreads / 32;
     const int per = (max_slices + maxw - 1) / maxw;

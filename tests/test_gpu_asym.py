@@ -65,15 +65,16 @@ def test_small_asym_every_path(mq, small, path, prec):
 @pytest.fixture(scope="module")
 def full(ora):
     """The N = 1580 workload (110 levels, 28 terms).  The GPU runs 48 of its trajectories (the
-    three highest energies) in one launch together with three short sampled ones that start at
-    R0 = 10 bohr; the oracle runs the sampled ones one by one."""
+    three highest energies) in one launch together with three sampled ones at the highest energy
+    (b = 0.5, 2.5, 5 bohr) that start, like every trajectory of the workload, at R0 = 30 bohr; the
+    oracle runs the sampled ones one by one."""
     p, ts = W.workload3(n_per_e=64)
     keep = np.flatnonzero(ts.e_coll >= ts.e_coll.max() * 0.2)
     rng = np.random.default_rng(3)
     bulk = ts.subset(np.sort(rng.choice(keep, 48, replace=False)))
     samp = ts.subset(np.flatnonzero(ts.e_coll == ts.e_coll.max())[:3])
     samp.b = np.array([0.5, 2.5, 5.0])
-    samp.r0 = samp.r_end = 10.0
+    assert samp.r0 == 30.0 and samp.r_end == 30.0
     osys = ora.asym_system(p)
     amp, res = ora.propagate(osys, samp.e_coll, samp.b, np.zeros(samp.n, int), r0=samp.r0, r_end=samp.r_end,
                              dt=samp.dt)

@@ -119,13 +119,33 @@ def test_mixed_small_and_workload1(mq, ora, prec):
         assert np.max(np.abs(sig_g - sig_o)) < TOL_MIXED * np.pi * ts.b_max ** 2
 
 
+def w2_picks(ts):
+    """One seeded trajectory per (collision energy, initial j') of the N = 441 workload: every
+    energy is covered, from the longest trajectories (E = 100 cm^-1, ~29k steps, the most FP32
+    accumulation in the mixed paths) to the shortest (E = 3000 cm^-1, ~5.6k steps)."""
+    rng = np.random.default_rng(7)
+    pick = [rng.choice(np.flatnonzero((ts.e_coll == e) & (ts.init_j == j)))
+            for e in np.unique(ts.e_coll) for j in (0, 1, 2)]
+    return np.array(sorted(pick))
+
+
+@pytest.fixture(scope="module")
+def w2(ora):
+    """The N = 441 workload and the oracle's populations of its stratified sample (w2_picks)."""
+    p, ts = W.workload2()
+    pick = w2_picks(ts)
+    pop_o, res_o = oracle_run(ora, oracle_system(ora, p), ts.subset(pick))
+    return p, ts, pick, pop_o, res_o
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_mixed_workload2_sampled_at_full_size(mq, ora, prec):
-    """N = 441 workload, all 3072 trajectories through a batched mixed launch; a seeded sample
-    is recomputed by the oracle; the whole batch agrees with the FP64 path to 1e-4."""
+def test_mixed_workload2_sampled_at_full_size(mq, w2, prec):
+    """N = 441 workload, all 3072 trajectories through a batched mixed launch (the bench's launch
+    configuration); one trajectory per (E, j') is compared with the oracle at 1e-4, and the whole
+    batch agrees with the FP64 path to 1e-4."""
     import torch
 
-    p, ts = W.workload2()
+    p, ts, pick, pop_o, res_o = w2
     sysm = mq.System.diatom(p, path="factorised", precision=prec)
     tr = mq.make_trajs(ts, sysm)
     trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
@@ -141,33 +161,35 @@ def test_mixed_workload2_sampled_at_full_size(mq, ora, prec):
     same = diag["steps"] == d64["steps"]
     assert np.mean(same) > 0.99
     assert np.max(np.abs(pop[same] - pop64.cpu().numpy()[same])) < TOL_MIXED
-    rng = np.random.default_rng(8)
-    cand = np.flatnonzero(ts.e_coll == ts.e_coll.max())
-    pick = np.concatenate([rng.choice(cand[ts.init_j[cand] == j], 1) for j in (0, 1, 2)])
-    pop_o, res_o = oracle_run(ora, oracle_system(ora, p), ts.subset(pick))
     sub = {k: diag[k][pick] for k in diag.dtype.names}
     compare(pop[pick], sub, pop_o, res_o, tol=TOL_MIXED)
 
 
-def test_n1600_sampled(mq, ora):
-    """N = 1600 (j <= 39): 24 trajectories of the N = 1600 workload through the plain FP64 and
-    the batched mixed paths; two of them recomputed by the oracle."""
-    import torch
-
+@pytest.fixture(scope="module")
+def n1600(ora):
+    """24 trajectories of the N = 1600 workload (12 at E = 1000 and 12 at E = 3000 cm^-1, all
+    three initial j') and the oracle's populations of one per (E, j')."""
     p, ts = W.workload2_n1600()
     rng = np.random.default_rng(9)
-    cand = np.flatnonzero(ts.e_coll == ts.e_coll.max())
-    sub = ts.subset(np.sort(rng.choice(cand, 24, replace=False)))
-    s64 = mq.System.diatom(p, path="plain")
-    s32 = mq.System.diatom(p, path="factorised", precision="fp32")
-    p64, d64 = gpu_run(mq, s64, sub, device=True)
-    p32, d32 = gpu_run(mq, s32, sub, device=True)
-    assert np.all(d64["status"] == 0) and np.all(d32["status"] == 0)
-    assert np.max(np.abs(p32 - p64)) < TOL_MIXED
-    pick = [0, 13]
+    idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(ts.e_coll == e), 12, replace=False)
+                                  for e in np.unique(ts.e_coll)]))
+    sub = ts.subset(idx)
+    pick = np.array([np.flatnonzero((sub.e_coll == e) & (sub.init_j == j))[0]
+                     for e in np.unique(sub.e_coll) for j in (0, 1, 2)])
     pop_o, res_o = oracle_run(ora, oracle_system(ora, p), sub.subset(pick))
-    compare(p64[pick], {k: d64[k][pick] for k in d64.dtype.names}, pop_o, res_o)
-    compare(p32[pick], {k: d32[k][pick] for k in d32.dtype.names}, pop_o, res_o, tol=TOL_MIXED)
+    return p, sub, pick, pop_o, res_o
+
+
+@pytest.mark.parametrize("path,prec", [("plain", "fp64"), ("factorised", "fp32"), ("factorised", "bf16x3")])
+def test_n1600_sampled(mq, n1600, path, prec):
+    """N = 1600 (j <= 39): 24 trajectories through the plain FP64 path and the two batched mixed
+    paths; one per (E, j') recomputed by the oracle (1e-8 / 1e-4)."""
+    p, sub, pick, pop_o, res_o = n1600
+    sys_ = mq.System.diatom(p, path=path, precision=prec)
+    pg, dg = gpu_run(mq, sys_, sub, device=True)
+    assert np.all(dg["status"] == 0)
+    compare(pg[pick], {k: dg[k][pick] for k in dg.dtype.names}, pop_o, res_o,
+            tol=TOL_FP64 if prec == "fp64" else TOL_MIXED)
 
 
 def test_paths_agree(mq):
@@ -190,12 +212,13 @@ def test_host_and_device_pointers_agree(mq):
     assert np.array_equal(dh["steps"], dd["steps"])
 
 
-def test_workload2_sampled_at_full_size(mq, ora):
-    """N = 441 workload: the full 3072-trajectory batch in the bench launch configuration;
-    a seeded sample of its trajectories is recomputed one by one by the oracle."""
+def test_workload2_sampled_at_full_size(mq, ora, w2):
+    """N = 441 workload: the full 3072-trajectory batch in the bench launch configuration; one
+    trajectory per (E, j') and the trajectory with the largest norm drift are recomputed one by
+    one by the oracle (1e-8, identical step counts)."""
     import torch
 
-    p, ts = W.workload2()
+    p, ts, pick, pop_o, res_o = w2
     sys = mq.System.diatom(p, path="plain")
     tr = mq.make_trajs(ts, sys)
     trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
@@ -209,16 +232,12 @@ def test_workload2_sampled_at_full_size(mq, ora):
     # same drift on the sampled trajectories below
     assert np.max(diag["norm_dev"]) < 1e-6
     assert np.max(np.abs(pop.sum(axis=1) - 1.0)) <= np.max(diag["norm_dev"]) * 1.0001
-    rng = np.random.default_rng(7)
-    # short trajectories (E = 3000 cm^-1) keep the oracle within seconds; one per initial level,
-    # plus the trajectory with the largest norm drift
-    cand = np.flatnonzero(ts.e_coll == ts.e_coll.max())
-    pick = np.concatenate([rng.choice(cand[ts.init_j[cand] == j], 1) for j in (0, 1, 2)])
-    pick = np.unique(np.append(pick, np.argmax(diag["norm_dev"])))
-    pop_o, res_o = oracle_run(ora, oracle_system(ora, p), ts.subset(pick))
     sub = {k: diag[k][pick] for k in diag.dtype.names}
     compare(pop[pick], sub, pop_o, res_o)
     assert np.allclose(sub["norm_dev"], res_o["norm_dev"], rtol=1e-3, atol=1e-12)
+    worst = int(np.argmax(diag["norm_dev"]))
+    pw, rw = oracle_run(ora, oracle_system(ora, p), ts.subset([worst]))
+    compare(pop[[worst]], {k: diag[k][[worst]] for k in diag.dtype.names}, pw, rw)
 
 
 def test_edge_cases(mq, ora):
