@@ -80,6 +80,17 @@ typedef enum { MQCT_FP64 = 0, MQCT_FP32 = 1, MQCT_BF16X3 = 2 } mqct_precision;
 #define MQCT_TRAJ_INVALID 16    /* device-resident trajectory failed validation; not run    */
 #define MQCT_TRAJ_CKPT 32       /* adjoint: the forward pass outran its checkpoint storage  */
 
+/* mqct_system_desc.flags */
+#define MQCT_PRESCRIBED_TRAJ 1  /* prescribed classical trajectory (FP64 systems only): instead of
+   the Ehrenfest motion of Eqs. 7-10, each trajectory follows the straight line
+   R(t) = sqrt(b^2 + v^2 (t - t_0)^2), dPhi/dt = b v / R^2, with v = sqrt(2 e_coll / mu) and
+   t_0 = max_steps dt / 2 (time-symmetric about the middle of the run), for exactly max_steps RK4
+   steps (r0 and r_end are not used; the mean field does not act back on the motion).  The
+   quantum equation (Eqs. 4-6) is integrated along it.  This is the setting in which microscopic
+   reversibility (Eq. 19) holds exactly for the discrete propagator, and the classical-trajectory-
+   first decoupling the paper's production runs use (Sec. III).  P_R = P_Phi = 0 in the
+   diagnostics' energy. */
+
 /* Description of one atom + rotor system.  All pointers are HOST pointers, read and
  * copied during mqct_create_system only. */
 typedef struct {
@@ -106,7 +117,7 @@ typedef struct {
     const double *ddv_ends;  /* [P][L][2] their R-derivatives at both ends                   */
     int32_t path;            /* mqct_path                                                    */
     int32_t precision;       /* mqct_precision                                               */
-    int32_t flags;           /* reserved, must be 0                                          */
+    int32_t flags;           /* 0 or MQCT_PRESCRIBED_TRAJ                                     */
 } mqct_system_desc;
 
 /* One trajectory (Sec. III: collision energy, impact parameter, initial state). */
@@ -218,7 +229,8 @@ void mqct_free_desc(mqct_system_desc *desc);
  * device memory and return an immutable system (safe to use from several streams).
  * Validation: N >= 1; finite energies, equal within a level; levels in [0, N); G real
  * symmetric within 1e-12 max|G| and zero between different m (Eq. 6); n_grid >= 4;
- * r_max > r_min; mu > 0; path and precision known; flags == 0.
+ * r_max > r_min; mu > 0; path and precision known; flags 0 or MQCT_PRESCRIBED_TRAJ (the latter
+ * with precision MQCT_FP64 only, else MQCT_ERR_UNSUPPORTED).
  * Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_OOM, MQCT_ERR_CUDA. */
 mqct_status mqct_create_system(const mqct_system_desc *desc, mqct_system *out);
 mqct_status mqct_destroy_system(mqct_system sys);
@@ -253,8 +265,8 @@ typedef struct {
     int64_t *t_done_ns;   /* [n] GPU global-timer value (ns) when its results were written, or NULL */
     const int32_t *batch_shape; /* [n_systems] HOST array or NULL: FP32 batched kernel shape of each
                              system, 0 = automatic (widest of the first six that fits), 1..7 =
-                             (slots per CTA, threads) of (32,256) (16,256) (8,256) (16,512) (8,512)
-                             (4,512) (4,256); a shape that does not fit the system's basis
+                             (slots per CTA, threads) of (32,512) (16,512) (8,256) (8,512) (4,512)
+                             (16,256) (4,256); a shape that does not fit the system's basis
                              -> MQCT_ERR_UNSUPPORTED                                             */
     const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: BF16X3 trajectories in flight per
                              system (rounded up to a multiple of 64, at most 8192), 0 = automatic

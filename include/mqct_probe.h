@@ -23,7 +23,7 @@ mqct_status mqct_probe_fma_rate(int32_t kind, double *gflops, void *cuda_stream)
 /* Latency of one operation in a dependent chain, in SM clock cycles per operation, with `warps`
  * warps (1..32) of one CTA each running its own chain (the slowest warp is reported):
  *   kind 0: FP64 FMA   kind 1: FP32 FMA   kind 2: FP64 division (plus one FP64 add)
- *   kind 3: FP64 -> FP32 -> FP64 conversion pair.
+ *   kind 3: FP64 -> FP32 conversion, FP32 multiply, FP32 -> FP64 conversion.
  * It shows how the FP64 work of a kernel serialises on this GPU (one FP64 warp instruction holds
  * its sub-partition's FP64 pipe for tens of cycles whatever the number of active lanes).
  * Synchronises `cuda_stream`; *cycles is a host pointer.

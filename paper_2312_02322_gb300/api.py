@@ -22,6 +22,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_TRAJ =
 PATH_PLAIN, PATH_FACTORISED = 0, 1
 FP64, FP32, BF16X3 = 0, 1, 2
 TRAJ_MAX_STEPS, TRAJ_TABLE_RANGE, TRAJ_NONFINITE, TRAJ_TIMEOUT, TRAJ_INVALID = 1, 2, 4, 8, 16
+PRESCRIBED_TRAJ = 1  # mqct_system_desc.flags
 
 _PATHS = {"plain": PATH_PLAIN, "factorised": PATH_FACTORISED}
 _PRECS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
@@ -75,7 +76,7 @@ class PropagateOpts(C.Structure):
 
 
 # (slots per CTA, threads) of the FP32 batched kernel for batch_shape = index + 1
-BATCH_SHAPES = [(32, 256), (16, 256), (8, 256), (16, 512), (8, 512), (4, 512), (4, 256)]
+BATCH_SHAPES = [(32, 512), (16, 512), (8, 256), (8, 512), (4, 512), (16, 256), (4, 256)]
 
 TRAJ_DTYPE = np.dtype([("e_coll", "<f8"), ("b", "<f8"), ("r0", "<f8"), ("r_end", "<f8"), ("dt", "<f8"),
                        ("init_state", "<i4"), ("max_steps", "<i4"), ("system_idx", "<i4"), ("_pad", "<i4")])
@@ -173,7 +174,10 @@ class System:
         self.tau = None  # per-level tau label (asymmetric top only)
 
     @classmethod
-    def diatom(cls, p: "_inputs.DiatomParams", path="plain", precision="fp64", with_params=False) -> "System":
+    def diatom(cls, p: "_inputs.DiatomParams", path="plain", precision="fp64", with_params=False,
+               prescribed=False) -> "System":
+        """prescribed=True: MQCT_PRESCRIBED_TRAJ, each trajectory follows the time-symmetric straight
+        line of impact parameter b and speed sqrt(2 e_coll / mu) for exactly max_steps steps."""
         dp = DiatomParams()
         dp.jmax, dp.bconst, dp.mu, dp.n_terms = p.jmax, p.bconst, p.mu, p.n_terms
         for i in range(p.n_terms):
@@ -184,6 +188,7 @@ class System:
         dp.path, dp.precision = _PATHS[path], _PRECS[precision]
         d = Desc()
         _check(lib().mqct_build_diatom(C.byref(dp), C.byref(d)))
+        d.flags = PRESCRIBED_TRAJ if prescribed else 0
         try:
             return cls(d)
         finally:

@@ -1,524 +1,747 @@
 // Batched mixed-precision trajectory kernel (factorised path, FP32 amplitudes).
 //
-// One CTA integrates B trajectories at once: their phase-rotated stage amplitudes form the
-// N x B block C (one column per trajectory, FP32 complex, shared memory, row-major so that a
-// row of four columns is 32 contiguous bytes).  A thread owns units (row r, 4 columns); the
-// sparse G entries of a row are loaded once and applied to the four columns.  Per RK4 stage:
-//   P3  contraction: for every stored term lambda, Y_lambda = G^lambda C, combined per column
-//       with the FP32 spline values v_lambda(R_b), v_lambda'(R_b):  w = M(R_b) c_b and
-//       u = M'(R_b) c_b   (Eq. 12); Coriolis stencil Dc_b = (J+ - J-) c_b; partial sums of
-//       the force -Re(c^dag u), the torque Re(c^dag D w) = -Re((Dc)^dag w) and (stage 0)
-//       Re(c^dag w);
-//   P4  derivative assembly da/dt = -i exp(iEt) w + (dPhi/dt/2) exp(iEt) Dc   (Eq. 5, using
-//       that Coriolis partners share the level energy), RK4 accumulation and next stage input;
-//       the step update a + (dt/6) acc is compensated (two-sum), its rounding error carried
-//       into the next step's accumulator;
-//   C   one lane per trajectory: FP64 classical stage update (Eqs. 7-10), FP64 bookkeeping of
-//       norm, total energy and P_Phi + <J_y>, termination, and refill of the slot from the
-//       device work queue (trajectories of uneven length share a CTA).
-// Phase factors exp(-i E_l t) per level and slot: argument E_l t and its reduction modulo
-// 2 pi in FP64, sine and cosine of the reduced angle in FP32.
+// One CTA integrates B trajectories ("slots") at once; finished slots are refilled from the
+// device work queue, so trajectories of uneven length share a CTA.  Their phase-rotated stage
+// amplitudes form the N x B block C (one column per trajectory, FP32 complex, shared memory,
+// row-major: a row of four columns is 32 contiguous bytes).  The warps have two roles:
+//
+//   element warps  own units (row r, 4 columns); per RK4 stage
+//     P3  contraction (Eq. 12): for every stored term l, Y_l = G^l C over the coalesced
+//         32-row sliced-ELL copy of G^l, combined per column with the FP32 spline values:
+//         w = M(R_b) c_b and u = M'(R_b) c_b; Coriolis stencil Dc = (J+ - J-) c; the stage
+//         derivative da/dt = -i exp(iEt) w + (dPhi/dt / 2) exp(iEt) Dc (Eq. 5) and the partial
+//         sums of the force -Re(c^dag u) (Eq. 9), the torque Re(c^dag D w) = -Re((Dc)^dag w)
+//         (Eq. 10) and, at stage 0, Re(c^dag w), |a|^2, E|a|^2, <J_y>;
+//     P4  RK4 accumulation and the next stage's input c (phase-rotated); the step update
+//         a + (dt/6) acc is compensated (two-sum), its rounding error carried into the next
+//         step's accumulator;
+//   slot warps     hold the FP64 classical state of the slots in registers, one lane per
+//     (component, slot): lane 8 c + j carries component c of (R, P_R, Phi, P_Phi) of slot j, so
+//     one FP64 instruction advances all four components of eight trajectories.  While the
+//     element warps contract stage s they look ahead: R of stage s+1 depends only on P_R of
+//     stage s, so its spline interval, 1/R and the spline values v_l, v_l' of stage s+1 are
+//     ready before stage s's force is known.  After the force and torque reductions only the
+//     RK4 update of (R, P_R, Phi, P_Phi) and dPhi/dt of the next stage remain (a handful of
+//     FP64 instructions); the bookkeeping of norm, total energy and P_Phi + <J_y>, the stop
+//     rule's outputs and the refill of a finished slot run during the next contraction.
+//
+// On this GPU an FP64 instruction holds its sub-partition's FP64 pipe for tens of cycles
+// whatever the number of active lanes, so the kernel keeps FP64 off the per-element work:
+// the phase arguments are 64-bit fixed-point turn counts (traj_common.cuh), the partial sums
+// are FP32 within a warp and compensated FP32 (two-sum) across warps, converted to FP64 once per
+// trajectory and stage.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
+#include "traj_common.cuh"
 
 namespace mqct {
 
-constexpr int kUpt = 4;  // (row, 4-column) units per thread
 
 enum { SLOT_IDLE = 0, SLOT_ACTIVE = 1, SLOT_FINAL = 2, SLOT_WAIT = 3 };
 
-struct Slot {
-    double q[4], qs[4], lacc[4];
-    double dt, r_end, e0, j0, ndev, edev, jdev, x, phidot, inv_mu;
-    int kint, status, steps, max_steps, traj, state, s0;
-};
-
-__device__ __forceinline__ float2 phase_of(double e, double t)
-{
-    const double two_pi_hi = 6.283185307179586232, two_pi_lo = 2.4492935982947064e-16;
-    double th = e * t;
-    double k = rint(th * 0.15915494309189535);
-    double r = fma(-k, two_pi_hi, th);
-    r = fma(-k, two_pi_lo, r);
-    float s, c;
-    sincosf((float)r, &s, &c);
-    return make_float2(c, -s);
-}
-
-__device__ __forceinline__ void locate_slot(const DevSys &S, Slot &sl)
-{
-    const double R = sl.qs[0];
-    int k = (int)floor((R - S.r_min) * S.inv_h);
-    k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
-    sl.kint = k;
-    sl.x = R - (S.r_min + k * S.h);
-    const double ir = 1.0 / R;
-    sl.phidot = sl.qs[3] * sl.inv_mu * ir * ir;
-    if (R < S.r_min) sl.status |= MQCT_TRAJ_TABLE_RANGE;
-}
-
-// slot lane: claim the next valid trajectory (FP64 initial conditions)
-__device__ void claim(const BatchArgs &a, const DevSys &S, Slot &sl)
-{
-    for (;;) {
-        const int item = atomicAdd(a.queue, 1);
-        if (item >= a.n) {
-            sl.state = SLOT_IDLE;
-            return;
-        }
-        const int t = a.order ? a.order[item] : item;
-        const mqct_traj tr = a.trajs[t];
-        const bool ok = tr.system_idx == a.sys_idx && tr.dt > 0.0 && tr.e_coll > 0.0 && tr.b >= 0.0 && tr.r0 > 0.0 &&
-                        tr.b < tr.r0 && isfinite(tr.r_end) && tr.max_steps >= 0 && tr.init_state >= 0 &&
-                        tr.init_state < S.n;
-        if (!ok) {
-            if (a.diag) {
-                mqct_diag d = {0, MQCT_TRAJ_INVALID, 0.0, 0.0, 0.0, 0.0};
-                a.diag[t] = d;
-            }
-            continue;
-        }
-        if (a.t_start) a.t_start[t] = mqct_clock_ns();
-        const int s0 = S.inv[tr.init_state];
-        int k = (int)floor((tr.r0 - S.r_min) * S.inv_h);
-        k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
-        const double x = tr.r0 - (S.r_min + k * S.h);
-        double m00 = 0.0;
-        for (int l = 0; l < S.L; ++l) {
-            const dbl4 c = S.vcoef[(size_t)l * S.n_int + k];
-            m00 += (c.x + x * (c.y + x * (c.z + x * c.w))) * S.diag_g[(size_t)l * S.n + s0];
-        }
-        const double lz = tr.b * sqrt(2.0 * S.mu * tr.e_coll);
-        sl.q[0] = tr.r0; sl.q[2] = 0.0; sl.q[3] = lz;
-        sl.q[1] = -sqrt(2.0 * S.mu * (tr.e_coll - m00) - lz * lz / (tr.r0 * tr.r0));
-        for (int i = 0; i < 4; ++i) sl.qs[i] = sl.q[i];
-        sl.dt = tr.dt; sl.r_end = tr.r_end; sl.max_steps = tr.max_steps;
-        sl.ndev = sl.edev = sl.jdev = 0.0;
-        sl.inv_mu = 1.0 / S.mu;
-        sl.status = 0; sl.steps = 0; sl.traj = t; sl.s0 = s0;
-        sl.state = SLOT_WAIT;
-        sl.kint = k; sl.x = x; sl.phidot = 0.0;
-        return;
-    }
-}
+// slot warps for B slots (eight slots per warp, four component lanes per slot)
+__host__ __device__ constexpr int batch_slot_warps(int B) { return B > 8 ? B / 8 : 1; }
 
 struct F4x2 {  // four complex FP32 values (one unit row of four columns)
     float2 v[4];
 };
 
-__device__ __forceinline__ F4x2 ld4(const float2 *p)
+// Shared-memory layout of the [rows][B] float2 arrays (C, A, ACC, PHa, PHb): element e = row B + col
+// is stored at swz(e), which swaps the two 16-byte halves of a four-column unit when bit 3 of its
+// 16-byte chunk index is set.  Warps access units of consecutive rows (their own rows, and the
+// gathered neighbours of a banded coupling), whose 16-byte chunks would otherwise fall on only
+// half of the eight bank groups of a 128-byte line.
+__device__ __forceinline__ int swz(int e) { return e ^ (((e >> 4) & 1) << 1); }
+
+// the four columns e0 .. e0 + 3 (e0 a multiple of 4)
+__device__ __forceinline__ F4x2 ld4(const float2 *p, int e0)
 {
-    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    const float4 a = *reinterpret_cast<const float4 *>(p + swz(e0));
+    const float4 b = *reinterpret_cast<const float4 *>(p + swz(e0 + 2));
     F4x2 r;
     r.v[0] = make_float2(a.x, a.y); r.v[1] = make_float2(a.z, a.w);
     r.v[2] = make_float2(b.x, b.y); r.v[3] = make_float2(b.z, b.w);
     return r;
 }
 
-__device__ __forceinline__ void st4(float2 *p, const F4x2 &r)
+__device__ __forceinline__ void st4(float2 *p, int e0, const F4x2 &r)
 {
-    reinterpret_cast<float4 *>(p)[0] = make_float4(r.v[0].x, r.v[0].y, r.v[1].x, r.v[1].y);
-    reinterpret_cast<float4 *>(p)[1] = make_float4(r.v[2].x, r.v[2].y, r.v[3].x, r.v[3].y);
+    *reinterpret_cast<float4 *>(p + swz(e0)) = make_float4(r.v[0].x, r.v[0].y, r.v[1].x, r.v[1].y);
+    *reinterpret_cast<float4 *>(p + swz(e0 + 2)) = make_float4(r.v[2].x, r.v[2].y, r.v[3].x, r.v[3].y);
 }
 
-template <int B, int T>
-__global__ void __launch_bounds__(T, 512 / T) k_batched_f32(BatchArgs a)
+// error-free sum of two FP32 numbers: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    static_assert(B % 4 == 0 && B <= 32, "batch width");
-    constexpr int G4 = B / 4;  // four-column groups per row
-    constexpr int NW = T / 32;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ DevSys S;
-    __shared__ Slot sl[B];
-    __shared__ __align__(16) float vid[B];
-    __shared__ __align__(16) float dvid[B];
-    __shared__ __align__(16) float s_hp[B];
-    __shared__ __align__(16) float s_dt[B];
-    __shared__ int s_state[B], s_traj[B], s_s0[B];
-    __shared__ double red2[B][6];
-    __shared__ int s_live;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = tid % G4;
-    if (tid == 0) S = *a.sys;
-    __syncthreads();
-    const int n = S.n, NL = S.n_levels, L = S.L;
-    float2 *C = reinterpret_cast<float2 *>(smraw);
-    float2 *A = C + (size_t)n * B, *ACC = A + (size_t)n * B;
-    float2 *PHa = ACC + (size_t)n * B, *PHb = PHa + (size_t)NL * B;
-    float *vv = reinterpret_cast<float *>(PHb + (size_t)NL * B), *dvv = vv + (size_t)L * B;
-    double *red = reinterpret_cast<double *>(dvv + (size_t)L * B);  // [NW][B][6]
-    const int upt = (n * G4 + T - 1) / T;
-
-    // per-column views written by the slot lanes after every update
-    auto publish = [&](int b) {
-        const Slot &m = sl[b];
-        s_hp[b] = (float)(0.5 * m.phidot);
-        s_dt[b] = (float)m.dt;
-        s_state[b] = m.state;
-        s_traj[b] = m.traj;
-        s_s0[b] = m.s0;
-    };
-    // v_lambda, v_lambda' at every running slot's stage R (FP32 spline, FP64-located interval)
-    auto terms = [&]() {
-        for (int i = tid; i < L * B; i += T) {
-            const int l = i / B, bb = i % B;
-            const Slot &s = sl[bb];
-            if (s.state == SLOT_IDLE || s.state == SLOT_WAIT) { vv[i] = 0.f; dvv[i] = 0.f; continue; }
-            const float4 c = S.vcoef_f[(size_t)l * S.n_int + s.kint];
-            const float x = (float)s.x;
-            vv[i] = fmaf(x, fmaf(x, fmaf(x, c.w, c.z), c.y), c.x);
-            dvv[i] = fmaf(x, fmaf(3.0f * x, c.w, 2.0f * c.z), c.y);
-        }
-        __syncthreads();
-        if (tid < B) {
-            float v0 = 0.f, d0 = 0.f;
-            for (int l = 0; l < L; ++l)
-                if ((S.id_mask >> l) & 1ull) { v0 += vv[l * B + tid]; d0 += dvv[l * B + tid]; }
-            vid[tid] = v0;
-            dvid[tid] = d0;
-        }
-    };
-
-    // ---- start: every slot claims a trajectory; columns e_s0, accumulators 0, phases 1
-    if (tid < B) {
-        claim(a, S, sl[tid]);
-        publish(tid);
-    }
-    __syncthreads();
-    for (int i = tid; i < n * B; i += T) {
-        const int r = i / B, bb = i % B;
-        if (s_state[bb] != SLOT_WAIT) continue;
-        const float2 v = make_float2(r == s_s0[bb] ? 1.0f : 0.0f, 0.0f);
-        A[i] = v; ACC[i] = make_float2(0.f, 0.f); C[i] = v;
-    }
-    for (int i = tid; i < NL * B; i += T) PHa[i] = make_float2(1.f, 0.f);
-    __syncthreads();
-    if (tid < B) {
-        Slot &m = sl[tid];
-        if (m.state == SLOT_WAIT) {
-            m.state = m.max_steps > 0 ? SLOT_ACTIVE : SLOT_FINAL;
-            if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
-            locate_slot(S, m);
-        }
-        publish(tid);
-    }
-    if (tid == 0) s_live = 1;
-    __syncthreads();
-    terms();
-    __syncthreads();
-
-    while (s_live) {
-        for (int s = 0; s < 4; ++s) {
-            const float2 *PHc = (s == 0 || s == 3) ? PHa : PHb;
-            const float2 *PHn = (s == 0 || s == 1) ? PHb : PHa;
-            if (s == 0 || s == 2) {
-                float2 *dst = s == 0 ? PHb : PHa;
-                for (int i = tid; i < NL * B; i += T) {
-                    const Slot &q = sl[i % B];
-                    if (q.state != SLOT_ACTIVE) continue;
-                    const double t = q.steps * q.dt + (s == 0 ? 0.5 * q.dt : q.dt);
-                    dst[i] = phase_of(S.lev_energy[i / B], t);
-                }
-            }
-            // column states of my group
-            int cst[4];
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                cst[j] = s_state[4 * g + j];
-                any |= cst[j] == SLOT_ACTIVE || cst[j] == SLOT_FINAL;
-            }
-            // ---- P3
-            F4x2 kq[kUpt];  // derivative da/dt of the unit's four columns (Eq. 5)
-            float fp[4] = {0, 0, 0, 0}, tp[4] = {0, 0, 0, 0}, vp[4] = {0, 0, 0, 0};
-            float np_[4] = {0, 0, 0, 0}, ep[4] = {0, 0, 0, 0}, jp[4] = {0, 0, 0, 0};
-            const float4 hp4 = reinterpret_cast<const float4 *>(s_hp)[g];
-            const float hp[4] = {hp4.x, hp4.y, hp4.z, hp4.w};
-#pragma unroll
-            for (int k = 0; k < kUpt; ++k) {
-                const int r = (tid + k * T) / G4;
-                if (k >= upt || r >= n || !any) continue;
-                const F4x2 c = ld4(C + (size_t)r * B + 4 * g);
-                const float4 vi = reinterpret_cast<const float4 *>(vid)[g], dvi = reinterpret_cast<const float4 *>(dvid)[g];
-                const float vi_[4] = {vi.x, vi.y, vi.z, vi.w}, dvi_[4] = {dvi.x, dvi.y, dvi.z, dvi.w};
-                F4x2 w, u;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    w.v[j] = make_float2(vi_[j] * c.v[j].x, vi_[j] * c.v[j].y);
-                    u.v[j] = make_float2(dvi_[j] * c.v[j].x, dvi_[j] * c.v[j].y);
-                }
-                for (int f = 0; f < S.n_f; ++f) {
-                    const int *ptr = S.csr_ptr + (size_t)f * (n + 1);
-                    const int q0 = __ldg(ptr + r), q1 = __ldg(ptr + r + 1);
-                    float2 y[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-                    // two entries per iteration: their loads are in flight together (same sum order)
-#pragma unroll 2
-                    for (int q = q0; q < q1; ++q) {
-                        const int col = __ldg(S.csr_col + q);
-                        const float gv = __ldg(S.csr_val + q);
-                        const F4x2 z = ld4(C + (size_t)col * B + 4 * g);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            y[j].x = fmaf(gv, z.v[j].x, y[j].x);
-                            y[j].y = fmaf(gv, z.v[j].y, y[j].y);
-                        }
-                    }
-                    const int l = S.f_term[f];
-                    const float4 v4 = reinterpret_cast<const float4 *>(vv + l * B)[g];
-                    const float4 d4 = reinterpret_cast<const float4 *>(dvv + l * B)[g];
-                    const float vl[4] = {v4.x, v4.y, v4.z, v4.w}, dl[4] = {d4.x, d4.y, d4.z, d4.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        w.v[j].x = fmaf(vl[j], y[j].x, w.v[j].x); w.v[j].y = fmaf(vl[j], y[j].y, w.v[j].y);
-                        u.v[j].x = fmaf(dl[j], y[j].x, u.v[j].x); u.v[j].y = fmaf(dl[j], y[j].y, u.v[j].y);
-                    }
-                }
-                const float au = __ldg(S.aupf + r), ad = __ldg(S.adnf + r);
-                const F4x2 cu = ld4(C + (size_t)__ldg(S.up + r) * B + 4 * g);
-                const F4x2 cd = ld4(C + (size_t)__ldg(S.dn + r) * B + 4 * g);
-                const int lev = S.lev[r];
-                const F4x2 p = ld4(PHc + (size_t)lev * B + 4 * g);
-                F4x2 a0;
-                if (s == 0) a0 = ld4(A + (size_t)r * B + 4 * g);
-                const float elev = (float)S.lev_energy[lev];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 dc = make_float2(ad * cd.v[j].x - au * cu.v[j].x, ad * cd.v[j].y - au * cu.v[j].y);
-                    const float2 wj = w.v[j], pj = p.v[j];
-                    fp[j] -= c.v[j].x * u.v[j].x + c.v[j].y * u.v[j].y;
-                    tp[j] -= dc.x * wj.x + dc.y * wj.y;
-                    vp[j] += c.v[j].x * wj.x + c.v[j].y * wj.y;
-                    // conj(p) Dc = (J+ - J-) a at this stage (partners share the level energy)
-                    const float2 da = make_float2(pj.x * dc.x + pj.y * dc.y, pj.x * dc.y - pj.y * dc.x);
-                    kq[k].v[j].x = fmaf(hp[j], da.x, pj.x * wj.y - pj.y * wj.x);
-                    kq[k].v[j].y = fmaf(hp[j], da.y, -(pj.x * wj.x + pj.y * wj.y));
-                    if (s == 0) {
-                        const float2 aj = a0.v[j];
-                        const float pp = aj.x * aj.x + aj.y * aj.y;
-                        np_[j] += pp;
-                        ep[j] += elev * pp;
-                        jp[j] += aj.x * da.y - aj.y * da.x;
-                    }
-                }
-            }
-            __syncthreads();
-            // ---- P4 (own units only)
-            const float4 dt4 = reinterpret_cast<const float4 *>(s_dt)[g];
-            const float dtj[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
-            const float wgt = (s == 1 || s == 2) ? 2.0f : 1.0f;
-#pragma unroll
-            for (int k = 0; k < kUpt; ++k) {
-                const int r = (tid + k * T) / G4;
-                if (k >= upt || r >= n) continue;
-                const size_t o = (size_t)r * B + 4 * g;
-                const int lev = S.lev[r];
-                F4x2 a0 = ld4(A + o), acc = ld4(ACC + o), cn = ld4(C + o);
-                const F4x2 pn = ld4(PHn + (size_t)lev * B + 4 * g);
-                bool wr_a = false;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int stj = cst[j];
-                    if (stj == SLOT_WAIT) {
-                        if (s == 3) {
-                            const float2 v = make_float2(r == s_s0[4 * g + j] ? 1.0f : 0.0f, 0.0f);
-                            a0.v[j] = v; acc.v[j] = make_float2(0.f, 0.f); cn.v[j] = v;
-                            wr_a = true;
-                        }
-                        continue;
-                    }
-                    if (stj != SLOT_ACTIVE && stj != SLOT_FINAL) continue;
-                    const float2 kk = kq[k].v[j];
-                    const float2 aj = a0.v[j];
-                    if (s == 0) {
-                        if (stj == SLOT_FINAL) {
-                            const float pp = aj.x * aj.x + aj.y * aj.y;
-                            const size_t oo = (size_t)s_traj[4 * g + j] * a.nmax + S.perm[r];
-                            if (a.pop) a.pop[oo] = (double)pp;
-                            if (a.amp) { a.amp[2 * oo] = aj.x; a.amp[2 * oo + 1] = aj.y; }
-                            continue;
-                        }
-                        // the accumulator enters the step holding the rounding error of the last update
-                        acc.v[j] = make_float2(kk.x + acc.v[j].x, kk.y + acc.v[j].y);
-                    } else {
-                        acc.v[j].x = fmaf(wgt, kk.x, acc.v[j].x);
-                        acc.v[j].y = fmaf(wgt, kk.y, acc.v[j].y);
-                        if (s == 3) {
-                            // compensated a + (dt/6) acc (two-sum): far from the collision the
-                            // interaction-picture amplitudes change by increments a plain FP32 add
-                            // would round away; the error is carried to the next accumulator
-                            const float h6 = dtj[j] * (1.0f / 6.0f), ih6 = 6.0f / dtj[j];
-                            const float ix = h6 * acc.v[j].x, iy = h6 * acc.v[j].y;
-                            const float sx = __fadd_rn(aj.x, ix), sy = __fadd_rn(aj.y, iy);
-                            const float bx = __fsub_rn(sx, aj.x), by = __fsub_rn(sy, aj.y);
-                            const float ex = __fadd_rn(__fsub_rn(aj.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
-                            const float ey = __fadd_rn(__fsub_rn(aj.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
-                            a0.v[j] = make_float2(sx, sy);
-                            acc.v[j] = make_float2(ex * ih6, ey * ih6);
-                            const float2 q = pn.v[j];
-                            cn.v[j] = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
-                            wr_a = true;
-                            continue;
-                        }
-                    }
-                    const float bn = s == 2 ? dtj[j] : 0.5f * dtj[j];
-                    const float2 yn = make_float2(fmaf(bn, kk.x, aj.x), fmaf(bn, kk.y, aj.y));
-                    const float2 q = pn.v[j];
-                    cn.v[j] = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
-                }
-                if (wr_a) st4(A + o, a0);
-                st4(ACC + o, acc);
-                st4(C + o, cn);
-            }
-            // ---- per-column reduction: lanes of one group inside the warp, then warps in FP64
-            const int nq = s == 0 ? 6 : 2;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float part[6] = {fp[j], tp[j], vp[j], np_[j], ep[j], jp[j]};
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    if (q >= nq) break;
-                    float v = part[q];
-#pragma unroll
-                    for (int off = G4; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                    part[q] = v;
-                }
-                if (lane < G4)
-                    for (int q = 0; q < nq; ++q) red[((size_t)warp * B + 4 * lane + j) * 6 + q] = (double)part[q];
-            }
-            __syncthreads();
-            if (tid < B * 6) {
-                const int bb = tid / 6, q = tid % 6;
-                double sum = 0.0;
-                if (q < nq)
-                    for (int w2 = 0; w2 < NW; ++w2) sum += red[((size_t)w2 * B + bb) * 6 + q];
-                red2[bb][q] = sum;
-            }
-            __syncthreads();
-            // ---- C: one lane per slot, FP64
-            if (tid < B) {
-                Slot &m = sl[tid];
-                const double F = red2[tid][0], Tq = red2[tid][1];
-                if (m.state == SLOT_ACTIVE || m.state == SLOT_FINAL) {
-                    const double R = m.qs[0], PR = m.qs[1], PP = m.qs[3], imu = m.inv_mu;
-                    const double ir = 1.0 / R, ir2 = ir * ir;
-                    if (s == 0) {
-                        const double V = red2[tid][2], NR = red2[tid][3], ER = red2[tid][4], JY = red2[tid][5];
-                        const double et = 0.5 * imu * (PR * PR + PP * PP * ir2) + ER + V;
-                        const double jt = PP + 0.5 * JY;
-                        if (m.steps == 0) { m.e0 = et; m.j0 = jt; }
-                        m.ndev = fmax(m.ndev, fabs(NR - 1.0));
-                        m.edev = fmax(m.edev, fabs(et - m.e0));
-                        m.jdev = fmax(m.jdev, fabs(jt - m.j0));
-                    }
-                    if (m.state == SLOT_FINAL) {
-                        if (s == 0) {
-                            if (a.diag) {
-                                mqct_diag d;
-                                d.steps = m.steps; d.status = m.status;
-                                d.norm_dev = m.ndev; d.energy_dev = m.edev; d.angmom_dev = m.jdev;
-                                d.t_final = m.steps * m.dt;
-                                a.diag[m.traj] = d;
-                            }
-                            if (a.t_done) a.t_done[m.traj] = mqct_clock_ns();
-                            claim(a, S, m);
-                        }
-                    } else {
-                        const double l4[4] = {PR * imu, F + PP * PP * imu * ir2 * ir, m.phidot, Tq};
-                        const double wg = (s == 1 || s == 2) ? 2.0 : 1.0;
-                        for (int i = 0; i < 4; ++i) m.lacc[i] = s == 0 ? l4[i] : fma(wg, l4[i], m.lacc[i]);
-                        if (s < 3) {
-                            const double bnd = s == 2 ? m.dt : 0.5 * m.dt;
-                            for (int i = 0; i < 4; ++i) m.qs[i] = fma(bnd, l4[i], m.q[i]);
-                        } else {
-                            for (int i = 0; i < 4; ++i) { m.q[i] = fma(m.dt / 6.0, m.lacc[i], m.q[i]); m.qs[i] = m.q[i]; }
-                            m.steps += 1;
-                            const bool fin = isfinite(m.q[0]) && isfinite(m.q[1]) && isfinite(m.q[2]) && isfinite(m.q[3]);
-                            if (!fin) m.status |= MQCT_TRAJ_NONFINITE;
-                            if (!fin || (m.q[0] >= m.r_end && m.q[1] > 0.0)) m.state = SLOT_FINAL;
-                            else if (m.steps >= m.max_steps) { m.status |= MQCT_TRAJ_MAX_STEPS; m.state = SLOT_FINAL; }
-                        }
-                        if (!(m.status & MQCT_TRAJ_NONFINITE)) locate_slot(S, m);
-                    }
-                } else if (m.state == SLOT_WAIT && s == 3) {
-                    m.state = m.max_steps > 0 ? SLOT_ACTIVE : SLOT_FINAL;
-                    if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
-                    locate_slot(S, m);
-                }
-                publish(tid);
-            }
-            __syncthreads();
-            if (s == 3) {
-                if (tid == 0) {
-                    int live_n = 0;
-                    for (int q = 0; q < B; ++q) live_n += sl[q].state != SLOT_IDLE;
-                    s_live = live_n;
-                }
-                // slots that start a trajectory at the next stage: phases of t = 0 (their columns
-                // were initialised in P4 of this stage)
-                for (int i = tid; i < NL * B; i += T) {
-                    const Slot &q = sl[i % B];
-                    if ((q.state == SLOT_ACTIVE || q.state == SLOT_FINAL) && q.steps == 0) PHa[i] = make_float2(1.f, 0.f);
-                }
-            }
-            terms();
-            __syncthreads();
-        }
-    }
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// double without the FP64 pipe: for positive finite x, x >= y (y > 0) compares the bit patterns
+__device__ __forceinline__ bool ge_pos(double x, double y)
+{
+    return __double_as_longlong(x) >= __double_as_longlong(y);
+}
+__device__ __forceinline__ bool finite64(double x)
+{
+    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+// the stage update of one classical component (lane layout of the slot warps): derivative
+// l = alpha X + beta, accumulator, next stage input (s < 3) or step update (s = 3).  The look-ahead
+// of R calls the same function, so both produce the same bits.
+__device__ __forceinline__ void stage_component(int s, double alpha, double X, double beta, double hdt, double dt,
+                                                double h6, double q, double &qs, double &lacc)
+{
+    const double l = fma(alpha, X, beta);
+    if (s == 0) lacc = l;
+    else lacc = fma((s == 1 || s == 2) ? 2.0 : 1.0, l, lacc);
+    if (s < 3) qs = fma(s == 2 ? dt : hdt, l, q);
+    else qs = fma(h6, lacc, q);
+}
+
+// per-slot values the element warps read during one stage, written by the slot warps during the
+// stage before (double-buffered by stage parity, so that writer and readers never overlap)
+template <int B>
+struct SlotView {
+    __align__(16) float hp[B];    // dPhi/dt / 2 (FP32 view)
+    __align__(16) float dtf[B];   // dt (FP32 view)
+    __align__(16) float vid[B];   // sum of the identity terms' v_l (FP32 spline)
+    __align__(16) float dvid[B];  // and of their v_l'
+    int state[B], traj[B], s0[B], steps[B];
+};
+
+// per-slot values of the slot warps that are not needed at every stage (shared memory keeps
+// them out of the registers the element warps' stage derivatives need)
+struct SlotCold {
+    double e0, j0, ndev, edev, jdev;  // initial E_tot and P_Phi + <J_y>, running deviations
+    double last_dt, r_end, i2m0;      // dt of the phase increments; stop radius; (1/mu)/R^2 at stage 0
+    int status, max_steps, traj, s0;
+    float dtf;
+};
+
+// shared state of one CTA besides the big per-element arrays
+template <int B>
+struct BatchShared {
+    DevSys S;
+    SlotView<B> view[2];
+    SlotCold cold[B];
+    float2 sum[6][B];  // cross-warp sums (hi, lo) of the six partial sums of the last phase B
+    int live;
+};
+
+// dynamic shared memory: inc [NL][B] (u64), C, A, ACC [n][B] float2, PHa, PHb [NL][B] float2,
+// vv, dvv [2][L][B] float, elev [NL] float, red [NE][B][8] float
 template <int B, int T>
 size_t batched_smem(const DevSys &h)
 {
-    return sizeof(float2) * (3 * (size_t)h.n * B + 2 * (size_t)h.n_levels * B) + sizeof(float) * 2 * (size_t)h.L * B +
-           sizeof(double) * (T / 32) * B * 6;
+    constexpr int NE = T / 32 - batch_slot_warps(B);
+    const size_t nl = h.n_levels, n = h.n, L = h.L;
+    return 8 * nl * B + 8 * (3 * n * B + 2 * nl * B) + 4 * (4 * L * B + nl) + 4 * (size_t)NE * B * 8 + 16;
 }
 
-template <int B, int T>
+template <int T>
+constexpr int batched_min_blocks() { return T >= 512 ? 1 : (T >= 256 ? 2 : 4); }
+
+template <int B, int T, int kUpt>  // kUpt: (row, 4-column) units per element thread at most
+__global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(BatchArgs a)
+{
+    static_assert(B % 4 == 0 && B <= 32, "batch width");
+    constexpr int G4 = B / 4;                   // four-column groups per row
+    constexpr int NS = batch_slot_warps(B);     // slot warps (the last NS warps)
+    constexpr int NW = T / 32, NE = NW - NS;    // element warps
+    constexpr int TE = NE * 32;
+    static_assert(NE >= 1, "no element warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ BatchShared<B> sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool slot_warp = warp >= NE;
+    if (tid == 0) sh.S = *a.sys;
+    __syncthreads();
+    const DevSys &S = sh.S;
+    const int n = S.n, NL = S.n_levels, L = S.L;
+    unsigned long long *inc = reinterpret_cast<unsigned long long *>(smraw);
+    float2 *C = reinterpret_cast<float2 *>(inc + (size_t)NL * B);
+    float2 *A = C + (size_t)n * B, *ACC = A + (size_t)n * B;
+    float2 *PHa = ACC + (size_t)n * B, *PHb = PHa + (size_t)NL * B;
+    float *vv = reinterpret_cast<float *>(PHb + (size_t)NL * B), *dvv = vv + 2 * (size_t)L * B;
+    float *elev = dvv + 2 * (size_t)L * B;
+    float *red = elev + NL;  // [NE][B][8]
+    for (int l = tid; l < NL; l += T) elev[l] = (float)S.lev_energy[l];
+
+    // ---------------------------------------------------------------- slot-warp registers
+    // lane 8 c + j: component c of (R, P_R, Phi, P_Phi) of slot b = 8 (warp - NE) + j.  Every
+    // lane of a slot warp runs the same instructions (lanes of slots >= B compute on copies and
+    // store nothing), so that the shuffles between the four component lanes of a slot are
+    // warp-uniform.
+    const int sc = lane >> 3, sj = lane & 7;
+    const int sb = slot_warp ? 8 * (warp - NE) + sj : 0;
+    const bool slot_lane = slot_warp && sb < B;
+    const int sbc = sb < B ? sb : B - 1;   // a valid index for reads of the lanes past B
+    const unsigned full = 0xffffffffu;
+    const unsigned m4 = 0x01010101u << sj;  // the four component lanes of this slot
+    double q = 0.0, qs = 0.0, lacc = 0.0;   // component sc
+    double imu = 1.0 / S.mu, dtd = 1.0, hdt = 0.5, h6 = 1.0 / 6.0;
+    double ir = 0.0, i2m = 0.0, phid = 0.0, t1 = 0.0;  // 1/R, (1/mu)/R^2, dPhi/dt, P_Phi^2/(mu R^3)
+    double ir_n = 0.1, i2m_n = 0.0;                   // look-ahead
+    int steps = 0, state = SLOT_IDLE;
+    bool below_n = false;
+    SlotCold &cs = sh.cold[sbc];
+    if (slot_lane && sc == 0) {
+        cs.last_dt = -1.0;
+        cs.status = 0;
+    }
+    __syncwarp();
+
+    auto comp = [&](double v, int c2) { return __shfl_sync(full, v, 8 * c2 + sj); };
+
+    // publish this slot's view for stage `stage`
+    auto publish = [&](int stage) {
+        if (slot_lane && sc == 0) {
+            SlotView<B> &vw = sh.view[stage & 1];
+            vw.state[sb] = state;
+            vw.traj[sb] = cs.traj;
+            vw.s0[sb] = cs.s0;
+            vw.steps[sb] = steps;
+            vw.dtf[sb] = cs.dtf;
+            vw.hp[sb] = (float)phid * 0.5f;
+        }
+    };
+
+    // claim the next valid trajectory for this slot (its four lanes together, shuffles over m4);
+    // on return the slot is WAIT (column to be initialised at the next stage 3) or IDLE
+    auto claim = [&]() {
+        for (;;) {
+            int item = 0;
+            if (sc == 0) item = atomicAdd(a.queue, 1);
+            item = __shfl_sync(m4, item, sj);
+            if (item >= a.n) {
+                state = SLOT_IDLE;
+                return;
+            }
+            const int t = a.order ? a.order[item] : item;
+            const mqct_traj tr = a.trajs[t];
+            if (!traj_valid(tr, S, a.sys_idx)) {
+                if (a.diag && sc == 0) {
+                    mqct_diag d = {0, MQCT_TRAJ_INVALID, 0.0, 0.0, 0.0, 0.0};
+                    a.diag[t] = d;
+                }
+                __syncwarp(m4);
+                continue;
+            }
+            if (a.t_start && sc == 0) a.t_start[t] = mqct_clock_ns();
+            const int s0 = S.inv[tr.init_state];
+            int k0;
+            double x0;
+            bool bl;
+            locate_interval(S, tr.r0, k0, x0, bl);
+            // initial mean field M_ss(r0): the four lanes split the terms
+            double m = 0.0;
+            for (int l = sc; l < L; l += 4) m += spline_fp64(S, l, k0, x0) * S.diag_g[(size_t)l * n + s0];
+            m += __shfl_xor_sync(m4, m, 8);
+            m += __shfl_xor_sync(m4, m, 16);
+            double q4[4];
+            initial_state(S, tr, m, q4);
+            q = q4[sc];
+            qs = q;
+            lacc = 0.0;
+            dtd = tr.dt;
+            hdt = 0.5 * tr.dt;
+            h6 = tr.dt / 6.0;
+            steps = 0;
+            state = SLOT_WAIT;
+            const bool new_dt = tr.dt != cs.last_dt;
+            __syncwarp(m4);
+            if (sc == 0) {
+                cs.traj = t;
+                cs.s0 = s0;
+                cs.dtf = (float)tr.dt;
+                cs.r_end = tr.r_end;
+                cs.max_steps = tr.max_steps;
+                cs.status = 0;
+                cs.ndev = cs.edev = cs.jdev = 0.0;
+                cs.last_dt = tr.dt;
+            }
+            // fixed-point phase increments of every level for this dt (kept while dt repeats)
+            if (new_dt)
+                for (int l = sc; l < NL; l += 4) inc[(size_t)l * B + sb] = phase_increment(S.lev_energy[l], tr.dt);
+            __syncwarp(m4);
+            return;
+        }
+    };
+
+    // look-ahead for stage s+1 (s = -1: a slot that starts at the next stage 0): R, its interval,
+    // 1/R and the spline values of every term, written to vv / dvv [(s+1) & 1]
+    auto look_ahead = [&](int s) {
+        const int par = (s + 1) & 1;
+        const bool act = slot_lane && state == SLOT_ACTIVE;
+        const bool start = slot_lane && state == SLOT_WAIT && (s == 3 || s == -1);
+        const double q0 = comp(q, 0), pr = comp(qs, 1), la0 = comp(lacc, 0);
+        double qs0 = 0.0, lacc0 = la0;
+        stage_component(s < 0 ? 0 : s, imu, pr, 0.0, hdt, dtd, h6, q0, qs0, lacc0);
+        double Rn = act ? qs0 : (start ? q0 : 10.0);  // any finite R for slots not running
+        int k;
+        double x;
+        locate_interval(S, Rn, k, x, below_n);
+        ir_n = 1.0 / Rn;
+        i2m_n = imu * ir_n * ir_n;
+        const float xf = (float)x;
+        float v0 = 0.f, d0 = 0.f;
+        for (int l = sc; l < L; l += 4) {
+            float v = 0.f, dv = 0.f;
+            if (act || start) {
+                const float4 c = S.vcoef_f[(size_t)l * S.n_int + k];
+                v = fmaf(xf, fmaf(xf, fmaf(xf, c.w, c.z), c.y), c.x);
+                dv = fmaf(xf, fmaf(3.0f * xf, c.w, 2.0f * c.z), c.y);
+            }
+            if (slot_lane) {
+                vv[((size_t)par * L + l) * B + sb] = v;
+                dvv[((size_t)par * L + l) * B + sb] = dv;
+            }
+            if ((S.id_mask >> l) & 1ull) { v0 += v; d0 += dv; }
+        }
+        v0 += __shfl_xor_sync(full, v0, 8);
+        v0 += __shfl_xor_sync(full, v0, 16);
+        d0 += __shfl_xor_sync(full, d0, 8);
+        d0 += __shfl_xor_sync(full, d0, 16);
+        if (slot_lane && sc == 0) {
+            sh.view[par].vid[sb] = v0;
+            sh.view[par].dvid[sb] = d0;
+        }
+    };
+
+    // total energy, P_Phi + <J_y> and norm of the state at the start of a step (or of the final
+    // state) from its stage-0 sums (sh.sum[2..5]): running maxima of their deviations, for the
+    // slots where `apply` holds
+    auto bookkeeping = [&](bool apply) {
+        const float2 pv = sh.sum[2 + sc][sbc];  // lane c converts V, |a|^2, E|a|^2, <J_y>
+        const double val = (double)pv.x + (double)pv.y;
+        const double V = comp(val, 0), NR = comp(val, 1), ER = comp(val, 2), JY = comp(val, 3);
+        const double PR = comp(q, 1), PP = comp(q, 3);
+        const double et = 0.5 * (imu * PR * PR + PP * PP * cs.i2m0) + ER + V;
+        const double jt = PP + 0.5 * JY;
+        const double e0 = steps == 0 ? et : cs.e0, j0 = steps == 0 ? jt : cs.j0;
+        const double nd = fmax(cs.ndev, fabs(NR - 1.0));
+        const double ed = fmax(cs.edev, fabs(et - e0));
+        const double jd = fmax(cs.jdev, fabs(jt - j0));
+        __syncwarp();
+        if (apply && sc == 0) {
+            cs.e0 = e0; cs.j0 = j0;
+            cs.ndev = nd; cs.edev = ed; cs.jdev = jd;
+        }
+        __syncwarp();
+    };
+
+    // ---------------------------------------------------------------- start
+    if (slot_warp) {
+        if (slot_lane) claim();
+        look_ahead(-1);
+        if (slot_lane && state == SLOT_WAIT) {
+            const int ms = cs.max_steps;
+            state = ms > 0 ? SLOT_ACTIVE : SLOT_FINAL;
+            __syncwarp(m4);
+            if (sc == 0) cs.status |= (ms <= 0 ? MQCT_TRAJ_MAX_STEPS : 0) | (below_n ? MQCT_TRAJ_TABLE_RANGE : 0);
+            ir = ir_n;
+            i2m = i2m_n;
+        }
+        const double pp3 = comp(q, 3);
+        if (slot_lane && state != SLOT_IDLE) phid = pp3 * i2m;
+        publish(0);
+    }
+    if (tid == 0) sh.live = 1;
+    __syncthreads();
+    // columns: e_s0, accumulators 0, phases of t = 0 and t = dt/2
+    for (int i = tid; i < n * B; i += T) {
+        const int r = i / B, bb = i % B;
+        const int st = sh.view[0].state[bb];
+        if (st != SLOT_ACTIVE && st != SLOT_FINAL) continue;
+        const float2 v = make_float2(r == sh.view[0].s0[bb] ? 1.0f : 0.0f, 0.0f);
+        A[swz(i)] = v; ACC[swz(i)] = make_float2(0.f, 0.f); C[swz(i)] = v;
+    }
+    for (int i = tid; i < NL * B; i += T) {
+        PHa[swz(i)] = make_float2(1.f, 0.f);
+        const int st = sh.view[0].state[i % B];
+        if (st == SLOT_ACTIVE || st == SLOT_FINAL) PHb[swz(i)] = phase_factor(inc[i], 1u);
+    }
+    __syncthreads();
+
+    // The two roles run separate loops with the same barriers (two per stage), so that the
+    // registers of one role are not kept alive in the other.
+    if (slot_warp) {
+        while (sh.live) {
+            for (int s = 0; s < 4; ++s) {
+                // ================================================================ phase A
+                {
+                // ---- slot warps during the contraction: bookkeeping of stage 0 (a finished slot
+                // at stage 1, before its refill; running slots at stage 2), the diagnostics and
+                // refill of a finished slot, then the look-ahead for stage s+1
+                const bool fin_any = __any_sync(full, slot_lane && state == SLOT_FINAL);
+                if (s == 1 && fin_any) {
+                    bookkeeping(slot_lane && state == SLOT_FINAL);
+                    if (slot_lane && state == SLOT_FINAL) {
+                        if (sc == 0) {
+                            if (a.diag) {
+                                mqct_diag d;
+                                d.steps = steps; d.status = cs.status;
+                                d.norm_dev = cs.ndev; d.energy_dev = cs.edev; d.angmom_dev = cs.jdev;
+                                d.t_final = steps * dtd;
+                                a.diag[cs.traj] = d;
+                            }
+                            if (a.t_done) a.t_done[cs.traj] = mqct_clock_ns();
+                        }
+                        __syncwarp(m4);
+                        claim();  // WAIT or IDLE: phases at stage 2, column at stage 3
+                    }
+                }
+                if (s == 2) bookkeeping(slot_lane && state == SLOT_ACTIVE);
+                const double pp3 = comp(qs, 3);
+                if (slot_lane && state == SLOT_ACTIVE) t1 = pp3 * phid * ir;  // P_Phi^2 / (mu R^3)
+                look_ahead(s);
+                }
+                __syncthreads();
+                // ================================================================ phase B
+                {
+                // ---- slot warps: cross-warp sums (compensated FP32), then the classical stage
+                const int nq = s == 0 ? 6 : 2;
+                const int sid = tid - TE;
+                for (int pidx = sid; pidx < nq * B; pidx += NS * 32) {
+                    const int qq = pidx / B, bb = pidx % B;
+                    float hi = 0.f, lo = 0.f;
+                    for (int w2 = 0; w2 < NE; ++w2) {
+                        float e2;
+                        two_sum(hi, red[((size_t)w2 * B + bb) * 8 + qq], hi, e2);
+                        lo += e2;
+                    }
+                    sh.sum[qq][bb] = make_float2(hi, lo);
+                }
+                if (NS > 1) asm volatile("bar.sync 1, %0;" ::"r"(NS * 32) : "memory");
+                else __syncwarp();
+                // lane c = 1 converts the force, c = 3 the torque (c = 0, 2: unused copies)
+                const float2 pv = sh.sum[sc == 3 ? 1 : 0][sbc];
+                const double X2 = (double)pv.x + (double)pv.y;
+                const double pr = comp(qs, 1);
+                if (s == 0 && slot_lane && sc == 0) cs.i2m0 = i2m;
+                const bool act = slot_lane && state == SLOT_ACTIVE;
+                const bool start = slot_lane && state == SLOT_WAIT && s == 3;
+                {
+                    // derivative l_c: (P_R / mu, F + P_Phi^2/(mu R^3), dPhi/dt, torque) (Eqs. 7-10)
+                    const double X = sc == 0 ? pr : (sc == 2 ? phid : X2);
+                    const double alpha = sc == 0 ? imu : 1.0, beta = sc == 1 ? t1 : 0.0;
+                    double qs2 = qs, lacc2 = lacc;
+                    stage_component(s, alpha, X, beta, hdt, dtd, h6, q, qs2, lacc2);
+                    if (act) { qs = qs2; lacc = lacc2; }
+                }
+                int add_status = 0;
+                if (s == 3) {
+                    const unsigned bad = __ballot_sync(full, act && !finite64(qs));
+                    const double R = comp(qs, 0), PR = comp(qs, 1);
+                    if (act) {
+                        q = qs;
+                        steps += 1;
+                        if ((bad >> sj) & 0x01010101u) {
+                            add_status |= MQCT_TRAJ_NONFINITE;
+                            state = SLOT_FINAL;
+                        } else if (ge_pos(R, cs.r_end) && __double_as_longlong(PR) > 0) {
+                            state = SLOT_FINAL;
+                        } else if (steps >= cs.max_steps) {
+                            add_status |= MQCT_TRAJ_MAX_STEPS;
+                            state = SLOT_FINAL;
+                        }
+                    }
+                }
+                const double pp3 = comp(qs, 3);
+                if ((act && !(add_status & MQCT_TRAJ_NONFINITE)) || start) {
+                    if (below_n) add_status |= MQCT_TRAJ_TABLE_RANGE;
+                    ir = ir_n;
+                    i2m = i2m_n;
+                    phid = pp3 * i2m_n;
+                }
+                if (start) {
+                    const int ms = cs.max_steps;
+                    state = ms > 0 ? SLOT_ACTIVE : SLOT_FINAL;
+                    if (ms <= 0) add_status |= MQCT_TRAJ_MAX_STEPS;
+                }
+                __syncwarp();
+                if (slot_lane && sc == 0 && add_status) cs.status |= add_status;
+                publish(s + 1);
+                if (s == 3) {
+                    const unsigned live = __ballot_sync(full, slot_lane && state != SLOT_IDLE);
+                    if (warp == NE && lane == 0) sh.live = 0;
+                    if (NS > 1) asm volatile("bar.sync 1, %0;" ::"r"(NS * 32) : "memory");
+                    if (lane == 0 && live) atomicOr(&sh.live, 1);
+                }
+                }
+                __syncthreads();
+            }
+        }
+        return;
+    }
+    const int g = tid % G4;
+    float2 kq[kUpt][4];  // stage derivative da/dt of the unit's four columns (Eq. 5)
+    while (sh.live) {
+        for (int s = 0; s < 4; ++s) {
+            const int par = s & 1;
+            const SlotView<B> &vw = sh.view[par];
+            // ================================================================ phase A
+            {
+                // phase factors of the next distinct stage time: t + dt/2 (after stage 0) and
+                // t + dt (after stage 2); a slot that starts at the next stage 0 gets t = 0
+                if (s == 0 || s == 2) {
+                    float2 *dst = s == 0 ? PHb : PHa;
+                    for (int i = tid; i < NL * B; i += TE) {
+                        const int bb = i % B, st = vw.state[bb];
+                        if (st == SLOT_ACTIVE)
+                            dst[swz(i)] = phase_factor(inc[i], 2u * (unsigned)vw.steps[bb] + (s == 0 ? 1u : 2u));
+                        else if (st == SLOT_WAIT && s == 2)
+                            dst[swz(i)] = make_float2(1.f, 0.f);
+                    }
+                }
+                // ---- P3: contraction, derivative, partial sums
+                const float2 *PHc = (s == 0 || s == 3) ? PHa : PHb;
+                const float *vvs = vv + (size_t)par * L * B, *dvvs = dvv + (size_t)par * L * B;
+                int cst[4];
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cst[j] = vw.state[4 * g + j];
+                    any |= cst[j] == SLOT_ACTIVE || cst[j] == SLOT_FINAL;
+                }
+                float fp[4] = {0, 0, 0, 0}, tp[4] = {0, 0, 0, 0}, vp[4] = {0, 0, 0, 0};
+                float np_[4] = {0, 0, 0, 0}, ep[4] = {0, 0, 0, 0}, jp[4] = {0, 0, 0, 0};
+                const float4 hp4 = *reinterpret_cast<const float4 *>(vw.hp + 4 * g);
+                const float hp[4] = {hp4.x, hp4.y, hp4.z, hp4.w};
+                const float4 vi = *reinterpret_cast<const float4 *>(vw.vid + 4 * g);
+                const float4 dvi = *reinterpret_cast<const float4 *>(vw.dvid + 4 * g);
+                const float vi_[4] = {vi.x, vi.y, vi.z, vi.w}, dvi_[4] = {dvi.x, dvi.y, dvi.z, dvi.w};
+#pragma unroll
+                for (int k = 0; k < kUpt; ++k) {
+                    const int u = tid + k * TE, r = u / G4;
+                    if (r >= n || !any) continue;
+                    const F4x2 c = ld4(C, r * B + 4 * g);
+                    F4x2 w, uu;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        w.v[j] = make_float2(vi_[j] * c.v[j].x, vi_[j] * c.v[j].y);
+                        uu.v[j] = make_float2(dvi_[j] * c.v[j].x, dvi_[j] * c.v[j].y);
+                    }
+                    const int sl = r >> 5, rl = r & 31;
+                    for (int f = 0; f < S.n_f; ++f) {
+                        const int *so = S.f_sl_off + (size_t)f * (S.n_slices + 1);
+                        const int off = __ldg(so + sl) + rl, width = (__ldg(so + sl + 1) - __ldg(so + sl)) >> 5;
+                        float2 y[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma unroll 2
+                        for (int e = 0; e < width; ++e) {
+                            const int col = __ldg(S.f_cols + off + e * kSlice);
+                            const float gv = __ldg(S.f_valf + off + e * kSlice);
+                            const F4x2 z = ld4(C, col * B + 4 * g);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                y[j].x = fmaf(gv, z.v[j].x, y[j].x);
+                                y[j].y = fmaf(gv, z.v[j].y, y[j].y);
+                            }
+                        }
+                        const int l = __ldg(S.f_term + f);
+                        const float4 v4 = *reinterpret_cast<const float4 *>(vvs + l * B + 4 * g);
+                        const float4 d4 = *reinterpret_cast<const float4 *>(dvvs + l * B + 4 * g);
+                        const float vl[4] = {v4.x, v4.y, v4.z, v4.w}, dl[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            w.v[j].x = fmaf(vl[j], y[j].x, w.v[j].x); w.v[j].y = fmaf(vl[j], y[j].y, w.v[j].y);
+                            uu.v[j].x = fmaf(dl[j], y[j].x, uu.v[j].x); uu.v[j].y = fmaf(dl[j], y[j].y, uu.v[j].y);
+                        }
+                    }
+                    const float au = __ldg(S.aupf + r), ad = __ldg(S.adnf + r);
+                    const F4x2 cu = ld4(C, __ldg(S.up + r) * B + 4 * g);
+                    const F4x2 cd = ld4(C, __ldg(S.dn + r) * B + 4 * g);
+                    const int lev = __ldg(S.lev + r);
+                    const F4x2 p = ld4(PHc, lev * B + 4 * g);
+                    F4x2 a0;
+                    if (s == 0) a0 = ld4(A, r * B + 4 * g);
+                    const float el = elev[lev];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float2 dc = make_float2(ad * cd.v[j].x - au * cu.v[j].x, ad * cd.v[j].y - au * cu.v[j].y);
+                        const float2 wj = w.v[j], pj = p.v[j];
+                        fp[j] -= c.v[j].x * uu.v[j].x + c.v[j].y * uu.v[j].y;
+                        tp[j] -= dc.x * wj.x + dc.y * wj.y;
+                        // conj(p) Dc = (J+ - J-) a at this stage (partners share the level energy)
+                        const float2 da = make_float2(pj.x * dc.x + pj.y * dc.y, pj.x * dc.y - pj.y * dc.x);
+                        kq[k][j].x = fmaf(hp[j], da.x, pj.x * wj.y - pj.y * wj.x);
+                        kq[k][j].y = fmaf(hp[j], da.y, -(pj.x * wj.x + pj.y * wj.y));
+                        if (s == 0) {
+                            const float2 aj = a0.v[j];
+                            const float pp = aj.x * aj.x + aj.y * aj.y;
+                            vp[j] += c.v[j].x * wj.x + c.v[j].y * wj.y;
+                            np_[j] += pp;
+                            ep[j] += el * pp;
+                            jp[j] += aj.x * da.y - aj.y * da.x;
+                        }
+                    }
+                }
+                // per-column sums over the warp (lanes of one column group), FP32; six quantities
+                // at stage 0, two (force, torque) at the others
+                auto warp_sums = [&](auto nqc) {
+                    constexpr int NQ = decltype(nqc)::value;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float part[NQ];
+                        part[0] = fp[j];
+                        part[1] = tp[j];
+                        if constexpr (NQ == 6) {
+                            part[2] = vp[j]; part[3] = np_[j]; part[4] = ep[j]; part[5] = jp[j];
+                        }
+#pragma unroll
+                        for (int qq = 0; qq < NQ; ++qq) {
+                            float v = part[qq];
+#pragma unroll
+                            for (int off = G4; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                            part[qq] = v;
+                        }
+                        if (lane < G4)
+#pragma unroll
+                            for (int qq = 0; qq < NQ; ++qq) red[((size_t)warp * B + 4 * lane + j) * 8 + qq] = part[qq];
+                    }
+                };
+                if (s == 0) warp_sums(std::integral_constant<int, 6>{});
+                else warp_sums(std::integral_constant<int, 2>{});
+            }
+            __syncthreads();
+            // ================================================================ phase B
+            {
+                // ---- P4: RK4 accumulation and the next stage's input (own units only)
+                const float2 *PHn = (s == 0 || s == 1) ? PHb : PHa;
+                const float4 dt4 = *reinterpret_cast<const float4 *>(vw.dtf + 4 * g);
+                const float dtj[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+                int cst[4];
+                bool all_act = true;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cst[j] = vw.state[4 * g + j];
+                    all_act &= cst[j] == SLOT_ACTIVE;
+                }
+                const float wgt = (s == 1 || s == 2) ? 2.0f : 1.0f;
+#pragma unroll
+                for (int k = 0; k < kUpt; ++k) {
+                    const int u = tid + k * TE, r = u / G4;
+                    if (r >= n) continue;
+                    const int o = r * B + 4 * g;
+                    const int lev = __ldg(S.lev + r);
+                    F4x2 a0 = ld4(A, o), acc = ld4(ACC, o), cn;
+                    // the columns not updated below keep their input; when all four are running,
+                    // every column is written and the old row is not needed
+                    if (!all_act) cn = ld4(C, o);
+                    const F4x2 pn = ld4(PHn, lev * B + 4 * g);
+                    bool wr_a = false;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int stj = cst[j];
+                        if (stj == SLOT_WAIT) {
+                            if (s == 3) {
+                                const float2 v = make_float2(r == vw.s0[4 * g + j] ? 1.0f : 0.0f, 0.0f);
+                                a0.v[j] = v; acc.v[j] = make_float2(0.f, 0.f); cn.v[j] = v;
+                                wr_a = true;
+                            }
+                            continue;
+                        }
+                        if (stj != SLOT_ACTIVE && stj != SLOT_FINAL) continue;
+                        if (stj == SLOT_FINAL && s != 0) continue;
+                        const float2 kk = kq[k][j];
+                        const float2 aj = a0.v[j];
+                        if (s == 0) {
+                            if (stj == SLOT_FINAL) {
+                                const float pp = aj.x * aj.x + aj.y * aj.y;
+                                const size_t oo = (size_t)vw.traj[4 * g + j] * a.nmax + __ldg(S.perm + r);
+                                if (a.pop) a.pop[oo] = (double)pp;
+                                if (a.amp) { a.amp[2 * oo] = aj.x; a.amp[2 * oo + 1] = aj.y; }
+                                continue;
+                            }
+                            // the accumulator enters the step holding the rounding error of the last update
+                            acc.v[j] = make_float2(kk.x + acc.v[j].x, kk.y + acc.v[j].y);
+                        } else {
+                            acc.v[j].x = fmaf(wgt, kk.x, acc.v[j].x);
+                            acc.v[j].y = fmaf(wgt, kk.y, acc.v[j].y);
+                            if (s == 3) {
+                                // compensated a + (dt/6) acc (two-sum): far from the collision the
+                                // interaction-picture amplitudes change by increments a plain FP32 add
+                                // would round away; the error is carried to the next accumulator
+                                const float h6f = dtj[j] * (1.0f / 6.0f), ih6 = 6.0f / dtj[j];
+                                const float ix = h6f * acc.v[j].x, iy = h6f * acc.v[j].y;
+                                float sx, sy, ex, ey;
+                                two_sum(aj.x, ix, sx, ex);
+                                two_sum(aj.y, iy, sy, ey);
+                                a0.v[j] = make_float2(sx, sy);
+                                acc.v[j] = make_float2(ex * ih6, ey * ih6);
+                                const float2 qn = pn.v[j];
+                                cn.v[j] = make_float2(qn.x * sx - qn.y * sy, qn.x * sy + qn.y * sx);
+                                wr_a = true;
+                                continue;
+                            }
+                        }
+                        const float bn = s == 2 ? dtj[j] : 0.5f * dtj[j];
+                        const float2 yn = make_float2(fmaf(bn, kk.x, aj.x), fmaf(bn, kk.y, aj.y));
+                        const float2 qn = pn.v[j];
+                        cn.v[j] = make_float2(qn.x * yn.x - qn.y * yn.y, qn.x * yn.y + qn.y * yn.x);
+                    }
+                    if (wr_a) st4(A, o, a0);
+                    st4(ACC, o, acc);
+                    st4(C, o, cn);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int B, int T, int kUpt>
 bool batched_fits(const DevSys &h, size_t cap)
 {
-    return (size_t)h.n * (B / 4) <= (size_t)kUpt * T && batched_smem<B, T>(h) <= cap;
+    constexpr int TE = (T / 32 - batch_slot_warps(B)) * 32;
+    return (size_t)h.n * (B / 4) <= (size_t)kUpt * TE && batched_smem<B, T>(h) + sizeof(BatchShared<B>) <= cap;
 }
 
-template <int B, int T>
+template <int B, int T, int kUpt>
 cudaError_t launch_batched(const BatchArgs &a, const DevSys &h, int sms, cudaStream_t st)
 {
     if (a.sm_limit > 0) sms = std::min(sms, a.sm_limit);
     const size_t smem = batched_smem<B, T>(h);
-    cudaError_t e = cudaFuncSetAttribute(k_batched_f32<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_batched_f32<B, T, kUpt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_f32<B, T>, T, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_f32<B, T, kUpt>, T, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = std::min(sms * per_sm, (a.n + B - 1) / B);
     grid = std::max(grid, 1);
-    k_batched_f32<B, T><<<grid, T, smem, st>>>(a);
+    k_batched_f32<B, T, kUpt><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// Batch shape: 256-thread CTAs, two per SM, when a CTA's block fits in half the shared
-// memory; otherwise 512-thread CTAs, one per SM.  Widest batch first.
+// Shapes (slots per CTA, threads), kBatchShapes: the automatic choice takes the first of the
+// first six that fits (widest batch first); CTAs of 256 threads leave room for two per SM.
 bool batched_shape_fits(const DevSys &h, int i)
 {
     const size_t half = 110 * 1024, full = 220 * 1024;
     switch (i) {
-        case 0: return batched_fits<32, 256>(h, half);
-        case 1: return batched_fits<16, 256>(h, half);
-        case 2: return batched_fits<8, 256>(h, half);
-        case 3: return batched_fits<16, 512>(h, full);
-        case 4: return batched_fits<8, 512>(h, full);
-        case 5: return batched_fits<4, 512>(h, full);
-        case 6: return batched_fits<4, 256>(h, half);
+        case 0: return batched_fits<32, 512, 4>(h, full);
+        case 1: return batched_fits<16, 512, 4>(h, full);
+        case 2: return batched_fits<8, 256, 4>(h, half);
+        case 3: return batched_fits<8, 512, 2>(h, full);
+        case 4: return batched_fits<4, 512, 4>(h, full);
+        case 5: return batched_fits<16, 256, 4>(h, full);
+        case 6: return batched_fits<4, 256, 2>(h, half);
         default: return false;
     }
 }
 
 int batched_width(const DevSys &h)
 {
-    for (int i = 0; i < 6; ++i)  // automatic choice: the first six, widest first
+    for (int i = 0; i < 6; ++i)
         if (batched_shape_fits(h, i)) return kBatchShapes[i][0] * 1000 + kBatchShapes[i][1];
     return 0;
 }
@@ -540,13 +763,13 @@ cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, in
     if (idx < 0) return cudaErrorInvalidConfiguration;
     if (width) *width = kBatchShapes[idx][0];
     switch (idx) {
-        case 0: return launch_batched<32, 256>(a, h, sms, st);
-        case 1: return launch_batched<16, 256>(a, h, sms, st);
-        case 2: return launch_batched<8, 256>(a, h, sms, st);
-        case 3: return launch_batched<16, 512>(a, h, sms, st);
-        case 4: return launch_batched<8, 512>(a, h, sms, st);
-        case 5: return launch_batched<4, 512>(a, h, sms, st);
-        case 6: return launch_batched<4, 256>(a, h, sms, st);
+        case 0: return launch_batched<32, 512, 4>(a, h, sms, st);
+        case 1: return launch_batched<16, 512, 4>(a, h, sms, st);
+        case 2: return launch_batched<8, 256, 4>(a, h, sms, st);
+        case 3: return launch_batched<8, 512, 2>(a, h, sms, st);
+        case 4: return launch_batched<4, 512, 4>(a, h, sms, st);
+        case 5: return launch_batched<16, 256, 4>(a, h, sms, st);
+        case 6: return launch_batched<4, 256, 2>(a, h, sms, st);
         default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -28,7 +28,7 @@ constexpr int kMaxWarps = 32;
 // so that each block is contiguous; perm[] maps back to the caller's order.
 struct DevSys {
     int n, n_levels, L, n_int, n_slices, P;
-    int path, precision;
+    int path, precision, flags;
     double mu, r_min, h, inv_h;
     const double *lev_energy;  // [n_levels]
     const int *lev;            // [n]  level of each internal state
@@ -55,15 +55,10 @@ struct DevSys {
     const int *f_sl_off;       // [n_f][n_slices+1] offsets into f_cols / f_val
     const int *f_cols;
     const double *f_val;
-    const float *f_valf;
-    // Batched mixed-precision path: CSR of each stored term (rows in internal order) and
-    // FP32 spline coefficients of v_lambda.
-    const int *csr_ptr;        // [n_f][n+1] offsets into csr_col / csr_val
-    const int *csr_col;
-    const float *csr_val;
+    const float *f_valf;       // FP32 copy of f_val (mixed-precision systems)
+    // Batched mixed-precision paths: FP32 spline coefficients of v_lambda, ladder factors
     const float4 *vcoef_f;     // [L][n_int]
     const float *aupf, *adnf;  // [n] FP32 ladder factors
-    int max_row_nnz;           // max over rows of the summed CSR row lengths
     // Tensor-core path (BF16X3): m-blocks packed into row tiles of <= 128 rows; for every
     // stored term f and tile t the 128 x 128 block-diagonal G^f tile as BF16 hi and lo parts in
     // the canonical K-major layout of the MMA A operand (tile-major: [f][t][hi,lo][16384]).

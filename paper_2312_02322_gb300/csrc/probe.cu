@@ -38,7 +38,7 @@ __global__ void k_latency_probe(long long *cycles, int iters, double a, double b
         if (KIND == 0) x = fma(x, b, 1e-7);         // FP64 fused multiply-add
         if (KIND == 1) xf = fmaf(xf, bf, 1e-7f);    // FP32 fused multiply-add
         if (KIND == 2) x = 1.0 / (x + 1.0);         // FP64 division (and one add)
-        if (KIND == 3) x = (double)(float)x;        // FP64 -> FP32 -> FP64 conversions
+        if (KIND == 3) x = (double)((float)x * bf);  // FP64 -> FP32, FP32 multiply, FP32 -> FP64
     }
     __syncwarp();
     const long long t1 = clock64();

@@ -29,6 +29,7 @@ namespace mqct {
 struct Ctl {
     double q[4], qs[4], lacc[4];
     double phidot, x, dt, r_end;
+    double line_b, line_v, line_t0;  // prescribed straight line (MQCT_PRESCRIBED_TRAJ)
     double e0, j0, ndev, edev, jdev;
     double v[kMaxTerms], dv[kMaxTerms];
     double vid, dvid;
@@ -58,12 +59,19 @@ __device__ __forceinline__ void locate(const DevSys &S, double R, int &k, double
     x = R - (S.r_min + kk * S.h);
 }
 
+// prescribed straight line at time t
+__device__ __forceinline__ double line_r(const Ctl &c, double t)
+{
+    const double s = c.line_v * (t - c.line_t0);
+    return sqrt(c.line_b * c.line_b + s * s);
+}
+
 // thread 0: stage quantities at the classical stage state qs
 __device__ void prepare_stage(const DevSys &S, Ctl &c)
 {
     double R = c.qs[0];
     locate(S, R, c.kint, c.x);
-    c.phidot = c.qs[3] / (S.mu * R * R);
+    c.phidot = (S.flags & MQCT_PRESCRIBED_TRAJ) ? c.line_b * c.line_v / (R * R) : c.qs[3] / (S.mu * R * R);
     if (R < S.r_min) c.status |= MQCT_TRAJ_TABLE_RANGE;
     if (S.path == MQCT_PATH_FACTORISED) {
         double vid = 0.0, dvid = 0.0;
@@ -194,6 +202,14 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
             const double lz = tr.b * sqrt(2.0 * S.mu * tr.e_coll);
             c.q[0] = tr.r0; c.q[2] = 0.0; c.q[3] = lz;
             c.q[1] = -sqrt(2.0 * S.mu * (tr.e_coll - m00) - lz * lz / (tr.r0 * tr.r0));
+            if (S.flags & MQCT_PRESCRIBED_TRAJ) {
+                // the straight line R(t) = sqrt(b^2 + v^2 (t - t_0)^2), time-symmetric about t_0
+                c.line_b = tr.b;
+                c.line_v = sqrt(2.0 * tr.e_coll / S.mu);
+                c.line_t0 = 0.5 * tr.max_steps * tr.dt;
+                c.q[0] = line_r(c, 0.0);
+                c.q[1] = c.q[2] = c.q[3] = 0.0;
+            }
             for (int i = 0; i < 4; ++i) c.qs[i] = c.q[i];
             c.dt = tr.dt; c.r_end = tr.r_end; c.max_steps = tr.max_steps;
             c.status = 0; c.steps = 0; c.done = tr.max_steps <= 0;
@@ -293,6 +309,8 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
                     }
                     const double R = c.qs[0], PR = c.qs[1], PP = c.qs[3], mu = S.mu;
                     double l[4] = {PR / mu, F + PP * PP / (mu * R * R * R), c.phidot, T};
+                    const bool presc = S.flags & MQCT_PRESCRIBED_TRAJ;
+                    if (presc) l[0] = l[1] = l[2] = l[3] = 0.0;  // the motion is prescribed
                     if (s == 0) {
                         const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + ER + V;
                         const double jt = PP + 0.5 * JY;
@@ -311,8 +329,14 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
                         c.steps = step + 1;
                         bool fin = isfinite(c.q[0]) && isfinite(c.q[1]) && isfinite(c.q[2]) && isfinite(c.q[3]);
                         if (!fin) { c.status |= MQCT_TRAJ_NONFINITE; c.done = 1; }
-                        else if (c.q[0] >= c.r_end && c.q[1] > 0.0) c.done = 1;
-                        else if (c.steps >= c.max_steps) { c.status |= MQCT_TRAJ_MAX_STEPS; c.done = 1; }
+                        else if (!presc && c.q[0] >= c.r_end && c.q[1] > 0.0) c.done = 1;
+                        else if (c.steps >= c.max_steps) { c.status |= presc ? 0 : MQCT_TRAJ_MAX_STEPS; c.done = 1; }
+                    }
+                    if (presc) {
+                        // R of the next stage on the line (stage times as in the phase factors)
+                        const double tn = s == 3 ? c.steps * dt : (s == 2 ? t0 + dt : t0 + 0.5 * dt);
+                        c.qs[0] = line_r(c, tn);
+                        if (s == 3) c.q[0] = c.qs[0];
                     }
                     if (!(c.status & MQCT_TRAJ_NONFINITE)) prepare_stage(S, c);
                 }

@@ -167,7 +167,9 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         return fail(MQCT_ERR_INVALID_ARG, "unknown precision");
     if (d->precision != MQCT_FP64 && d->path != MQCT_PATH_FACTORISED)
         return fail(MQCT_ERR_UNSUPPORTED, "mixed precision runs on the factorised (batched) path only");
-    if (d->flags != 0) return fail(MQCT_ERR_INVALID_ARG, "flags must be 0");
+    if (d->flags & ~MQCT_PRESCRIBED_TRAJ) return fail(MQCT_ERR_INVALID_ARG, "unknown flags");
+    if ((d->flags & MQCT_PRESCRIBED_TRAJ) && d->precision != MQCT_FP64)
+        return fail(MQCT_ERR_UNSUPPORTED, "MQCT_PRESCRIBED_TRAJ needs precision MQCT_FP64");
     if (P < 0 || (P > 0 && (!d->dv_dparam || !d->ddv_ends))) return fail(MQCT_ERR_INVALID_ARG, "bad parameter tables");
     if (!d->G && d->g_nnz > 0 && (!d->g_term || !d->g_row || !d->g_col || !d->g_val))
         return fail(MQCT_ERR_INVALID_ARG, "NULL triplet array");
@@ -302,7 +304,7 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     DevSys &D = S.h;
     std::memset(&D, 0, sizeof(D));
     D.n = n; D.n_levels = n_levels; D.L = L; D.n_int = n_int; D.n_slices = n_slices; D.P = P;
-    D.path = d->path; D.precision = d->precision;
+    D.path = d->path; D.precision = d->precision; D.flags = d->flags;
     D.mu = d->mu; D.r_min = d->r_min; D.h = h; D.inv_h = 1.0 / h;
 
     mqct_status st = MQCT_OK;
@@ -411,34 +413,17 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         up_(fcols, &D.f_cols);
         up_(fval, &D.f_val);
         if (d->precision != MQCT_FP64) {
-            // CSR per stored term for the batched kernel, FP32 values and spline coefficients
-            std::vector<int> cptr, ccol;
-            std::vector<float> cval;
-            int max_row = 0;
-            std::vector<int> row_tot(n, 0);
-            for (int l : fterm) {
-                for (int r = 0; r < n; ++r) {
-                    cptr.push_back((int)ccol.size());
-                    for (auto &e : grows[l][r]) {
-                        ccol.push_back(e.c);
-                        cval.push_back((float)e.v);
-                    }
-                    row_tot[r] += (int)grows[l][r].size();
-                }
-                cptr.push_back((int)ccol.size());
-            }
-            for (int r = 0; r < n; ++r) max_row = std::max(max_row, row_tot[r]);
+            // FP32 copies for the mixed-precision kernels: the sliced-ELL values, the spline
+            // coefficients of v_lambda and the Coriolis ladder factors
+            std::vector<float> fvalf(fval.begin(), fval.end());
             std::vector<float4> vf(vcoef.size());
             for (size_t i = 0; i < vcoef.size(); ++i)
                 vf[i] = make_float4((float)vcoef[i].x, (float)vcoef[i].y, (float)vcoef[i].z, (float)vcoef[i].w);
             std::vector<float> aupf(aup.begin(), aup.end()), adnf(adn.begin(), adn.end());
+            up_(fvalf, &D.f_valf);
             up_(aupf, &D.aupf);
             up_(adnf, &D.adnf);
-            up_(cptr, &D.csr_ptr);
-            up_(ccol, &D.csr_col);
-            up_(cval, &D.csr_val);
             up_(vf, &D.vcoef_f);
-            D.max_row_nnz = max_row;
         }
         if (d->precision == MQCT_BF16X3) {
             // pack whole m-blocks (contiguous in the internal order) into row tiles of <= 128 rows

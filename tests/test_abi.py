@@ -156,12 +156,23 @@ def test_builder_pes_matches_oracle(L, ora):
     api.lib().mqct_free_desc(C.byref(d))
 
 
+def test_prescribed_flag_needs_fp64(L):
+    d, _ = build_desc(2, path="factorised")
+    d.flags = api.PRESCRIBED_TRAJ
+    d.precision = api.FP32
+    h = C.c_void_p()
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == api.ERR_UNSUPPORTED
+    assert b"PRESCRIBED" in L.mqct_last_error()
+    assert not h.value
+    api.lib().mqct_free_desc(C.byref(d))
+
+
 @pytest.mark.parametrize("field,value,needle", [
     ("n_grid", 3, b"n_grid"),
     ("mu", -1.0, b"mu"),
     ("n_terms", 0, b"n_terms"),
     ("path", 7, b"path"),
-    ("flags", 1, b"flags"),
+    ("flags", 6, b"flags"),
 ])
 def test_create_validation_rejects_before_gpu(L, field, value, needle):
     d, _ = build_desc(2)
