@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16x3"])
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP64 comparison run (throughput and max |dP| against it)")
-    ap.add_argument("--adjoint", type=int, default=0,
-                    help="also time the adjoint on this many trajectories of the gradient workload")
+    ap.add_argument("--adjoint", type=int, default=1024,
+                    help="time the FP64 and the mixed adjoint on this many trajectories of the gradient workload "
+                         "(N = 441, E = 1000 cm^-1; 1024 = all of it; 0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-traj", type=int, default=0,
@@ -378,6 +379,42 @@ def n1600_block(api, args, dev, stream, flush, ws, runs=3):
             "launch_option": tune, "comparison": comp}
 
 
+def adjoint_block(api, n_traj):
+    """The gradient workload (N = 441, E = 1000 cm^-1, checkpoints every 64 steps): gradients of every
+    j = 0 -> j' cross section, combined with seeded random weights, with respect to the 10 PES parameters,
+    by the FP64 adjoint and the mixed (FP32-amplitude) adjoint; each timed once after a short
+    warm-up call."""
+    import torch
+
+    pa, ta = W.workload5()
+    if n_traj < ta.n:
+        ta = ta.subset(np.linspace(0, ta.n - 1, n_traj).astype(int))
+    s64 = api.System.diatom(pa, path="factorised", precision="fp64", with_params=True)
+    tra = api.make_trajs(ta, s64)
+    _, _, dga = api.propagate(s64, tra, device=False)
+    wa = api.sigma_weights(ta, dga["status"])
+    # seeded random upstream weights: unit weights would ask for the gradient of the total
+    # probability, which unitarity makes zero
+    dls = np.random.default_rng(W.DEFAULT_SEED).standard_normal((ta.n_groups, s64.n_levels))
+    steps = float(dga["steps"].sum())
+    out = {"workload": f"{ta.n} of the 1024 trajectories of the N=441, E=1000 cm^-1 gradient workload",
+           "params": int(s64.n_params), "ckpt": 64, "traj_steps": steps}
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        sa = s64 if prec == "fp64" else api.System.diatom(pa, path="factorised", precision=prec, with_params=True)
+        few = np.arange(min(4, ta.n))
+        api.adjoint(sa, tra[few], wa[few], ta.group[few], ta.n_groups, dls, ckpt=64)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = api.adjoint(sa, tra, wa, ta.group, ta.n_groups, dls, ckpt=64)
+        sec = time.perf_counter() - t0
+        grads[prec] = g
+        out[prec] = {"seconds": sec, "traj_steps_per_s": steps / sec, "gradients_per_s": 1.0 / sec,
+                     "dL_dtheta_norm": float(np.linalg.norm(g))}
+    out["mixed_vs_fp64_max_rel"] = float(np.max(np.abs(grads["fp32"] - grads["fp64"])) / np.max(np.abs(grads["fp64"])))
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def gpu_arm(args):
     import torch
@@ -550,22 +587,7 @@ def gpu_arm(args):
 
     adj = None
     if args.adjoint:
-        pa, ta = W.workload5()
-        ta = ta.subset(np.linspace(0, ta.n - 1, args.adjoint).astype(int))
-        sa = api.System.diatom(pa, path="factorised", precision="fp64", with_params=True)
-        tra = api.make_trajs(ta, sa)
-        _, _, dga = api.propagate(sa, tra, device=False)
-        wa = api.sigma_weights(ta, dga["status"])
-        dls = np.ones((ta.n_groups, sa.n_levels))
-        api.adjoint(sa, tra, wa, ta.group, ta.n_groups, dls, ckpt=64)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        grad = api.adjoint(sa, tra, wa, ta.group, ta.n_groups, dls, ckpt=64)
-        t_adj = time.perf_counter() - t0
-        adj = {"workload": f"{ta.n} of the 1024 trajectories of the N=441, E=1000 cm^-1 gradient workload",
-               "params": int(sa.n_params), "ckpt": 64, "seconds": t_adj,
-               "traj_steps_per_s": float(dga["steps"].sum()) / t_adj,
-               "gradients_per_s": 1.0 / t_adj, "dL_dtheta_norm": float(np.linalg.norm(grad))}
+        adj = adjoint_block(api, args.adjoint)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

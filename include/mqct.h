@@ -247,10 +247,10 @@ mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out);
  *   diag       [n] mqct_diag; or NULL
  * Work order: trajectories are claimed from a device work queue, longest estimated
  * first.  Scratch memory is taken with stream-ordered allocation on `cuda_stream`.
- * With device output pointers the FP64 and single-system FP32 calls only enqueue work and
- * return MQCT_OK; the BF16X3 path synchronises the stream between chunks of 16 steps (it
- * checks on the host whether trajectories are still running), and FP32 / BF16X3 calls with
- * several systems synchronise it once to size the per-system launches.  With any host
+ * With device output pointers the FP64 and FP32 calls only enqueue work and return MQCT_OK;
+ * the BF16X3 path synchronises the stream between chunks of 16 steps (it checks on the host
+ * whether trajectories are still running), and BF16X3 calls with several systems synchronise
+ * it once to size the per-system launches.  With any host
  * output the call synchronises the stream and returns MQCT_ERR_TRAJ if a trajectory status
  * is non-zero.  Errors: MQCT_ERR_INVALID_ARG, MQCT_ERR_UNSUPPORTED, MQCT_ERR_OOM,
  * MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
@@ -263,10 +263,13 @@ typedef struct {
     int64_t *t_start_ns;  /* [n] GPU global-timer value (ns) when each trajectory was started, or NULL;
                              host or device pointer                                               */
     int64_t *t_done_ns;   /* [n] GPU global-timer value (ns) when its results were written, or NULL */
-    const int32_t *batch_shape; /* [n_systems] HOST array or NULL: FP32 batched kernel shape of each
-                             system, 0 = automatic (widest of the first six that fits), 1..7 =
-                             (slots per CTA, threads) of (32,512) (16,512) (8,256) (8,512) (4,512)
-                             (16,256) (4,256); a shape that does not fit the system's basis
+    const int32_t *batch_shape; /* [n_systems] HOST array or NULL: shape of the FP32 batched kernel.
+                             The call runs one launch for all its systems, whose shape is the first
+                             non-zero entry; 0 everywhere = automatic (the first of the first six
+                             that every system fits).  1..7 = (slots per CTA at most, threads) of
+                             (32,512) (16,512) (8,256) (8,512) (4,512) (16,256) (4,256); each system
+                             gets the widest slot count (32, 16, 8 or 4, at most the shape's) its
+                             basis fits; a shape that some system does not fit
                              -> MQCT_ERR_UNSUPPORTED                                             */
     const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: BF16X3 trajectories in flight per
                              system (rounded up to a multiple of 64, at most 8192), 0 = automatic
@@ -274,10 +277,12 @@ typedef struct {
 } mqct_propagate_opts;
 
 /* mqct_propagate with options (opts may be NULL).  Uneven batches: the trajectories of several
- * systems of one call run together -- FP64: in one persistent launch; FP32: one persistent
- * batched launch per system, all concurrent, each on a share of the SMs proportional to its
- * estimated work; BF16X3: one system after the other.  Errors as for mqct_propagate, plus
- * MQCT_ERR_INVALID_ARG for out-of-range options. */
+ * systems of one call run together -- FP64: in one persistent launch (each CTA takes the system
+ * of the trajectory it claims); FP32: in one persistent launch (up to 16 systems per launch),
+ * whose CTAs bind to a system on the device -- at the start in proportion to the systems'
+ * estimated work, later to the system with the most work left once theirs is exhausted;
+ * BF16X3: one system after the other.  Errors as for mqct_propagate, plus MQCT_ERR_INVALID_ARG
+ * for out-of-range options. */
 mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_systems, const mqct_traj *trajs, int32_t n,
                               double *final_pop, double *final_amp, mqct_diag *diag, const mqct_propagate_opts *opts,
                               void *cuda_stream);
@@ -322,8 +327,14 @@ mqct_status mqct_cross_sections(mqct_system sys, const double *final_pop, const 
  * by a discrete adjoint of the same RK4 map (the number of steps of every trajectory is
  * held at its forward value), recomputing the forward pass from checkpoints taken every
  * `ckpt` steps.  Arguments as for mqct_propagate / mqct_cross_sections; dL_dsigma
- * [n_groups][n_levels]; dL_dparam [P].  Single system.  Errors: MQCT_ERR_INVALID_ARG,
- * MQCT_ERR_UNSUPPORTED (no parameter tables), MQCT_ERR_OOM, MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
+ * [n_groups][n_levels]; dL_dparam [P].  Single system, factorised path, P <= 128, L <= 64.
+ * Precision follows the system: MQCT_FP64 -> amplitudes and cotangents in FP64; MQCT_FP32 or
+ * MQCT_BF16X3 -> the mixed adjoint: FP32 amplitudes, contraction and cotangents (the step update
+ * compensated), phase arguments as fixed-point turn counts, FP64 classical motion, classical
+ * cotangents and parameter gradient.  Work vectors live in shared memory when they fit (N up to
+ * ~800 in FP64, ~1500 in FP32), else in global memory.  Errors: MQCT_ERR_INVALID_ARG,
+ * MQCT_ERR_UNSUPPORTED (no parameter tables, plain path, prescribed trajectories, limits above),
+ * MQCT_ERR_OOM, MQCT_ERR_CUDA, MQCT_ERR_TRAJ. */
 mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int32_t n, const double *weight,
                          const int32_t *group, int32_t n_groups, const double *dL_dsigma, int32_t ckpt,
                          double *dL_dparam, void *cuda_stream);

@@ -385,9 +385,10 @@ def _diatom_with(p, theta):
     return q
 
 
-def cross_section_fn():
+def cross_section_fn(precision="fp64"):
     """torch.autograd.Function computing the cross sections of a diatom workload as a function
-    of theta = (A, beta); backward runs the adjoint kernel (FP64).
+    of theta = (A, beta); backward runs the adjoint kernel (FP64, or the mixed adjoint with
+    precision="fp32").
 
         sigma = CrossSection.apply(theta, params, trajset, ckpt)
     theta: float64 CPU tensor [2L]; returns sigma [n_groups][n_levels] (float64, CPU)."""
@@ -397,7 +398,7 @@ def cross_section_fn():
         @staticmethod
         def forward(ctx, theta, params, ts, ckpt=64):
             p = _diatom_with(params, theta.detach().cpu().numpy())
-            sys_ = System.diatom(p, path="factorised", precision="fp64", with_params=True)
+            sys_ = System.diatom(p, path="factorised", precision=precision, with_params=True)
             tr = make_trajs(ts, sys_)
             pop, _, diag = propagate(sys_, tr, device=False)
             w = sigma_weights(ts, diag["status"])

@@ -80,9 +80,41 @@ def tune(system, trajs: np.ndarray, probe_steps: int = 300, max_sample: int = 81
             "sample": int(len(tr))}
 
 
+def tune_joint(systems, trajs: np.ndarray, probe_steps: int = 300, max_sample: int = 8192, repeats: int = 2,
+               stream=None) -> dict:
+    """FP32 uneven batch: the whole call runs one persistent launch whose shape every system
+    shares, so the candidates are timed on a sample of the mixed trajectories together."""
+    import torch
+
+    tr = _sample(trajs, max_sample)
+    tr["max_steps"] = np.minimum(tr["max_steps"], probe_steps)
+    tr_dev = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+    _, _, dg = api.propagate(systems, tr, want_pop=False, device=False)
+    steps = float(dg["steps"].sum())
+    table = []
+    for k in range(1, len(api.BATCH_SHAPES) + 1):
+        opt = {"batch_shape": [k] * len(systems)}
+        try:
+            ms = _time(systems, tr_dev, opt, repeats, stream)
+        except api.MQCTError as err:
+            if err.status == api.ERR_UNSUPPORTED:
+                continue  # this shape does not fit every basis
+            raise
+        table.append({"option": {"batch_shape": k}, "ms": ms, "rate": steps / (ms * 1e-3)})
+    best = max(table, key=lambda r: r["rate"])
+    return {"option": best["option"], "rate": best["rate"], "table": table, "probe_steps": probe_steps,
+            "sample": int(len(tr))}
+
+
 def tune_batch(systems, trajs: np.ndarray, **kw) -> dict:
-    """Tune each system of an uneven batch on its own trajectories; returns the per-system
-    option lists {"batch_shape": [...], "tc_slots": [...]} for api.propagate and the reports."""
+    """Launch options of a batch over one or several systems: the per-system option lists
+    {"batch_shape": [...], "tc_slots": [...]} for api.propagate and the reports.  FP32: one shape for
+    the single launch of the call (tune_joint); BF16X3: each system tuned on its own trajectories
+    (the tensor-core path runs the systems one after another)."""
+    if len(systems) > 1 and systems[0].info["precision"] == api.FP32:
+        r = tune_joint(systems, trajs, **kw)
+        k = int(r["option"]["batch_shape"])
+        return {"batch_shape": [k] * len(systems), "tc_slots": [0] * len(systems), "reports": [r]}
     shapes, slots, reports = [], [], []
     for i, s in enumerate(systems):
         sub = trajs[trajs["system_idx"] == i]

@@ -25,6 +25,13 @@
 //     FP64 instructions); the bookkeeping of norm, total energy and P_Phi + <J_y>, the stop
 //     rule's outputs and the refill of a finished slot run during the next contraction.
 //
+// Uneven batches (trajectories of several systems, i.e. basis sizes, in one call) run in this one
+// persistent launch: a CTA binds to a system (its share of the grid at the start is proportional
+// to the systems' estimated work), takes trajectories from that system's work list (longest
+// first) with as many slots as the system's basis allows in the CTA's shared memory, and when the
+// list is exhausted and its slots have drained it binds to the system with the most estimated
+// work left.
+//
 // On this GPU an FP64 instruction holds its sub-partition's FP64 pipe for tens of cycles
 // whatever the number of active lanes, so the kernel keeps FP64 off the per-element work:
 // the phase arguments are 64-bit fixed-point turn counts (traj_common.cuh), the partial sums
@@ -34,6 +41,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "internal.h"
 #include "traj_common.cuh"
@@ -133,14 +141,15 @@ struct BatchShared {
     SlotCold cold[B];
     float2 sum[6][B];  // cross-warp sums (hi, lo) of the six partial sums of the last phase B
     int live;
+    int cur;           // system the CTA is bound to (-1: no work left)
 };
 
-// dynamic shared memory: inc [NL][B] (u64), C, A, ACC [n][B] float2, PHa, PHb [NL][B] float2,
-// vv, dvv [2][L][B] float, elev [NL] float, red [NE][B][8] float
-template <int B, int T>
-size_t batched_smem(const DevSys &h)
+// dynamic shared memory of a CTA bound to a system with B slots: inc [NL][B] (u64), C, A, ACC [n][B]
+// float2, PHa, PHb [NL][B] float2, vv, dvv [2][L][B] float, elev [NL] float, red [NE][B][8] float
+template <int BMAX, int T>
+size_t batched_smem(const DevSys &h, int B)
 {
-    constexpr int NE = T / 32 - batch_slot_warps(B);
+    constexpr int NE = T / 32 - batch_slot_warps(BMAX);
     const size_t nl = h.n_levels, n = h.n, L = h.L;
     return 8 * nl * B + 8 * (3 * n * B + 2 * nl * B) + 4 * (4 * L * B + nl) + 4 * (size_t)NE * B * 8 + 16;
 }
@@ -148,23 +157,62 @@ size_t batched_smem(const DevSys &h)
 template <int T>
 constexpr int batched_min_blocks() { return T >= 512 ? 1 : (T >= 256 ? 2 : 4); }
 
-template <int B, int T, int kUpt>  // kUpt: (row, 4-column) units per element thread at most
-__global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(BatchArgs a)
+// the system a CTA binds to next: at the start, the CTA's share of the grid by estimated work;
+// afterwards the system with the most estimated work left (-1: none)
+__device__ int pick_system(const BatchMultiArgs &a, bool first)
 {
-    static_assert(B % 4 == 0 && B <= 32, "batch width");
-    constexpr int G4 = B / 4;                   // four-column groups per row
-    constexpr int NS = batch_slot_warps(B);     // slot warps (the last NS warps)
+    const int ns = a.n_systems;
+    auto count_of = [&](int s) { return a.counts ? a.counts[s] : a.n; };
+    if (first && ns > 1 && a.work) {
+        double tot = 0.0;
+        for (int s = 0; s < ns; ++s) tot += a.work[s];
+        const double target = (blockIdx.x + 0.5) / gridDim.x * tot;
+        double acc = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            acc += a.work[s];
+            if (acc >= target && count_of(s) > 0) return s;
+        }
+    }
+    int best = -1;
+    double best_score = -1.0;
+    for (int s = 0; s < ns; ++s) {
+        const int c = count_of(s);
+        const int q = *((volatile const int *)(a.queues + s));
+        const int rem = c - (q < c ? q : c);
+        if (rem <= 0) continue;
+        const double score = rem * (a.work ? a.work[s] / c : 1.0);
+        if (score > best_score) {
+            best_score = score;
+            best = s;
+        }
+    }
+    return best;
+}
+
+// everything a CTA does while bound to system `cur`: with BC > 0 its slot count is the compile-time
+// constant BC, with BC = 0 the system's entry of a.slots
+template <int BC, int BMAX, int T, int kUpt>
+__device__ __forceinline__ void batched_system(const BatchMultiArgs &a, BatchShared<BMAX> &sh, int cur,
+                                               unsigned char *smraw)
+{
+    static_assert(BC % 4 == 0 && BC <= BMAX, "slots per CTA");
+    constexpr int NS = batch_slot_warps(BMAX);  // slot warps (the last NS warps)
     constexpr int NW = T / 32, NE = NW - NS;    // element warps
     constexpr int TE = NE * 32;
-    static_assert(NE >= 1, "no element warps");
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ BatchShared<B> sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool slot_warp = warp >= NE;
-    if (tid == 0) sh.S = *a.sys;
-    __syncthreads();
+    const int sc = lane >> 3, sj = lane & 7;
+    const int sb = slot_warp ? 8 * (warp - NE) + sj : 0;
+    const unsigned full = 0xffffffffu;
+    const unsigned m4 = 0x01010101u << sj;  // the four component lanes of this slot
     const DevSys &S = sh.S;
+    const int B = BC > 0 ? BC : a.slots[cur];    // slots (4, 8, 16 or 32)
+    const int G4 = B / 4;                        // four-column groups per row
+    const int lg4 = G4 == 1 ? 0 : (G4 == 2 ? 1 : (G4 == 4 ? 2 : 3));
     const int n = S.n, NL = S.n_levels, L = S.L;
+    const int *order = a.lists + (size_t)cur * a.n;
+    int *queue = a.queues + cur;
+    const int count = a.counts ? a.counts[cur] : a.n;
     unsigned long long *inc = reinterpret_cast<unsigned long long *>(smraw);
     float2 *C = reinterpret_cast<float2 *>(inc + (size_t)NL * B);
     float2 *A = C + (size_t)n * B, *ACC = A + (size_t)n * B;
@@ -173,24 +221,40 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
     float *elev = dvv + 2 * (size_t)L * B;
     float *red = elev + NL;  // [NE][B][8]
     for (int l = tid; l < NL; l += T) elev[l] = (float)S.lev_energy[l];
+    // columns of the slots that start at the first stage 0: e_s0, accumulators 0, phases of t = 0
+    // and t = dt/2 (after the slot warps' first claims; both roles share the work)
+    auto init_columns = [&]() {
+        for (int i = tid; i < n * B; i += T) {
+            const int r = i / B, bb = i % B;
+            const int st = sh.view[0].state[bb];
+            if (st != SLOT_ACTIVE && st != SLOT_FINAL) continue;
+            const float2 v = make_float2(r == sh.view[0].s0[bb] ? 1.0f : 0.0f, 0.0f);
+            A[swz(i)] = v; ACC[swz(i)] = make_float2(0.f, 0.f); C[swz(i)] = v;
+        }
+        for (int i = tid; i < NL * B; i += T) {
+            PHa[swz(i)] = make_float2(1.f, 0.f);
+            const int st = sh.view[0].state[i % B];
+            if (st == SLOT_ACTIVE || st == SLOT_FINAL) PHb[swz(i)] = phase_factor(inc[i], 1u);
+        }
+    };
+    if (tid == 0) sh.live = 1;
 
-    // ---------------------------------------------------------------- slot-warp registers
-    // lane 8 c + j: component c of (R, P_R, Phi, P_Phi) of slot b = 8 (warp - NE) + j.  Every
-    // lane of a slot warp runs the same instructions (lanes of slots >= B compute on copies and
-    // store nothing), so that the shuffles between the four component lanes of a slot are
-    // warp-uniform.
-    const int sc = lane >> 3, sj = lane & 7;
-    const int sb = slot_warp ? 8 * (warp - NE) + sj : 0;
-    const bool slot_lane = slot_warp && sb < B;
-    const int sbc = sb < B ? sb : B - 1;   // a valid index for reads of the lanes past B
-    const unsigned full = 0xffffffffu;
-    const unsigned m4 = 0x01010101u << sj;  // the four component lanes of this slot
-    double q = 0.0, qs = 0.0, lacc = 0.0;   // component sc
+    // The two roles run separate code with the same barriers (two per stage), so that the
+    // registers of one role are not kept alive in the other.
+    if (slot_warp) {
+    // slot-warp registers (lane 8 c + j: component c of (R, P_R, Phi, P_Phi) of slot 8 (warp - NE) + j)
+    double q = 0.0, qs = 0.0, lacc = 0.0;
     double imu = 1.0 / S.mu, dtd = 1.0, hdt = 0.5, h6 = 1.0 / 6.0;
     double ir = 0.0, i2m = 0.0, phid = 0.0, t1 = 0.0;  // 1/R, (1/mu)/R^2, dPhi/dt, P_Phi^2/(mu R^3)
     double ir_n = 0.1, i2m_n = 0.0;                   // look-ahead
     int steps = 0, state = SLOT_IDLE;
     bool below_n = false;
+
+    // Every lane of a slot warp runs the same instructions (lanes of slots >= B compute on copies
+    // and store nothing), so that the shuffles between the four component lanes of a slot are
+    // warp-uniform.
+    const bool slot_lane = slot_warp && sb < B;
+    const int sbc = sb < B ? sb : B - 1;   // a valid index for reads of the lanes past B
     SlotCold &cs = sh.cold[sbc];
     if (slot_lane && sc == 0) {
         cs.last_dt = -1.0;
@@ -203,7 +267,7 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
     // publish this slot's view for stage `stage`
     auto publish = [&](int stage) {
         if (slot_lane && sc == 0) {
-            SlotView<B> &vw = sh.view[stage & 1];
+            SlotView<BMAX> &vw = sh.view[stage & 1];
             vw.state[sb] = state;
             vw.traj[sb] = cs.traj;
             vw.s0[sb] = cs.s0;
@@ -218,15 +282,15 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
     auto claim = [&]() {
         for (;;) {
             int item = 0;
-            if (sc == 0) item = atomicAdd(a.queue, 1);
+            if (sc == 0) item = atomicAdd(queue, 1);
             item = __shfl_sync(m4, item, sj);
-            if (item >= a.n) {
+            if (item >= count) {
                 state = SLOT_IDLE;
                 return;
             }
-            const int t = a.order ? a.order[item] : item;
+            const int t = order ? order[item] : item;
             const mqct_traj tr = a.trajs[t];
-            if (!traj_valid(tr, S, a.sys_idx)) {
+            if (!traj_valid(tr, S, a.sys_base + cur)) {
                 if (a.diag && sc == 0) {
                     mqct_diag d = {0, MQCT_TRAJ_INVALID, 0.0, 0.0, 0.0, 0.0};
                     a.diag[t] = d;
@@ -338,7 +402,7 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
     };
 
     // ---------------------------------------------------------------- start
-    if (slot_warp) {
+    {
         if (slot_lane) claim();
         look_ahead(-1);
         if (slot_lane && state == SLOT_WAIT) {
@@ -353,26 +417,10 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
         if (slot_lane && state != SLOT_IDLE) phid = pp3 * i2m;
         publish(0);
     }
-    if (tid == 0) sh.live = 1;
     __syncthreads();
-    // columns: e_s0, accumulators 0, phases of t = 0 and t = dt/2
-    for (int i = tid; i < n * B; i += T) {
-        const int r = i / B, bb = i % B;
-        const int st = sh.view[0].state[bb];
-        if (st != SLOT_ACTIVE && st != SLOT_FINAL) continue;
-        const float2 v = make_float2(r == sh.view[0].s0[bb] ? 1.0f : 0.0f, 0.0f);
-        A[swz(i)] = v; ACC[swz(i)] = make_float2(0.f, 0.f); C[swz(i)] = v;
-    }
-    for (int i = tid; i < NL * B; i += T) {
-        PHa[swz(i)] = make_float2(1.f, 0.f);
-        const int st = sh.view[0].state[i % B];
-        if (st == SLOT_ACTIVE || st == SLOT_FINAL) PHb[swz(i)] = phase_factor(inc[i], 1u);
-    }
+    init_columns();
     __syncthreads();
-
-    // The two roles run separate loops with the same barriers (two per stage), so that the
-    // registers of one role are not kept alive in the other.
-    if (slot_warp) {
+    {
         while (sh.live) {
             for (int s = 0; s < 4; ++s) {
                 // ================================================================ phase A
@@ -479,14 +527,17 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
                 __syncthreads();
             }
         }
-        return;
     }
-    const int g = tid % G4;
+    } else {
+    __syncthreads();
+    init_columns();
+    __syncthreads();
+    const int g = tid & (G4 - 1);
     float2 kq[kUpt][4];  // stage derivative da/dt of the unit's four columns (Eq. 5)
     while (sh.live) {
         for (int s = 0; s < 4; ++s) {
             const int par = s & 1;
-            const SlotView<B> &vw = sh.view[par];
+            const SlotView<BMAX> &vw = sh.view[par];
             // ================================================================ phase A
             {
                 // phase factors of the next distinct stage time: t + dt/2 (after stage 0) and
@@ -520,7 +571,7 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
                 const float vi_[4] = {vi.x, vi.y, vi.z, vi.w}, dvi_[4] = {dvi.x, dvi.y, dvi.z, dvi.w};
 #pragma unroll
                 for (int k = 0; k < kUpt; ++k) {
-                    const int u = tid + k * TE, r = u / G4;
+                    const int u = tid + k * TE, r = u >> lg4;
                     if (r >= n || !any) continue;
                     const F4x2 c = ld4(C, r * B + 4 * g);
                     F4x2 w, uu;
@@ -627,7 +678,7 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
                 const float wgt = (s == 1 || s == 2) ? 2.0f : 1.0f;
 #pragma unroll
                 for (int k = 0; k < kUpt; ++k) {
-                    const int u = tid + k * TE, r = u / G4;
+                    const int u = tid + k * TE, r = u >> lg4;
                     if (r >= n) continue;
                     const int o = r * B + 4 * g;
                     const int lev = __ldg(S.lev + r);
@@ -695,46 +746,90 @@ __global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(Batc
             __syncthreads();
         }
     }
+    }
 }
 
-template <int B, int T, int kUpt>
-bool batched_fits(const DevSys &h, size_t cap)
+// EXACT: every system of the launch runs BMAX slots per CTA (compile-time slot count); otherwise
+// each system runs the slot count of a.slots
+template <int BMAX, int T, int kUpt, bool EXACT>  // kUpt: (row, 4-column) units per element thread at most
+__global__ void __launch_bounds__(T, batched_min_blocks<T>()) k_batched_f32(BatchMultiArgs a)
 {
-    constexpr int TE = (T / 32 - batch_slot_warps(B)) * 32;
-    return (size_t)h.n * (B / 4) <= (size_t)kUpt * TE && batched_smem<B, T>(h) + sizeof(BatchShared<B>) <= cap;
+    static_assert(BMAX % 4 == 0 && BMAX <= 32, "batch width");
+    static_assert(T / 32 - batch_slot_warps(BMAX) >= 1, "no element warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ BatchShared<BMAX> sh;
+    bool first = true;
+    for (;;) {
+        // bind to a system
+        if (threadIdx.x == 0) {
+            const int s = pick_system(a, first);
+            sh.cur = s;
+            if (s >= 0) sh.S = a.sys[s];
+        }
+        __syncthreads();
+        first = false;
+        const int cur = sh.cur;
+        if (cur < 0) break;
+        batched_system<EXACT ? BMAX : 0, BMAX, T, kUpt>(a, sh, cur, smraw);
+        __syncthreads();  // both roles are done with this system before the CTA binds to the next
+    }
 }
 
-template <int B, int T, int kUpt>
-cudaError_t launch_batched(const BatchArgs &a, const DevSys &h, int sms, cudaStream_t st)
+// the largest slot count (4, 8, 16 or 32, at most BMAX) with which a system fits a CTA of the shape
+// in `cap` bytes of shared memory; 0 if none
+template <int BMAX, int T, int kUpt>
+int batched_slots(const DevSys &h, size_t cap)
 {
-    if (a.sm_limit > 0) sms = std::min(sms, a.sm_limit);
-    const size_t smem = batched_smem<B, T>(h);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_batched_f32<B, T, kUpt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int TE = (T / 32 - batch_slot_warps(BMAX)) * 32;
+    for (int b = BMAX; b >= 4; b >>= 1)
+        if ((size_t)h.n * (b / 4) <= (size_t)kUpt * TE && batched_smem<BMAX, T>(h, b) + sizeof(BatchShared<BMAX>) <= cap)
+            return b;
+    return 0;
+}
+
+template <int BMAX, int T, int kUpt>
+cudaError_t launch_batched(BatchMultiArgs a, const std::vector<const DevSys *> &hs, size_t cap, int sms,
+                           cudaStream_t st)
+{
+    size_t smem = 0;
+    int minb = BMAX;
+    for (size_t i = 0; i < hs.size(); ++i) {
+        const int b = batched_slots<BMAX, T, kUpt>(*hs[i], cap);
+        if (b == 0) return cudaErrorInvalidConfiguration;
+        a.slots[i] = b;
+        minb = std::min(minb, b);
+        smem = std::max(smem, batched_smem<BMAX, T>(*hs[i], b));
+    }
+    const bool exact = minb == BMAX;
+    const void *kern = exact ? (const void *)k_batched_f32<BMAX, T, kUpt, true>
+                             : (const void *)k_batched_f32<BMAX, T, kUpt, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_f32<B, T, kUpt>, T, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int grid = std::min(sms * per_sm, (a.n + B - 1) / B);
-    grid = std::max(grid, 1);
-    k_batched_f32<B, T, kUpt><<<grid, T, smem, st>>>(a);
+    const int grid = std::max(1, std::min(sms * per_sm, (a.n + minb - 1) / minb));
+    if (exact) k_batched_f32<BMAX, T, kUpt, true><<<grid, T, smem, st>>>(a);
+    else k_batched_f32<BMAX, T, kUpt, false><<<grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// Shapes (slots per CTA, threads), kBatchShapes: the automatic choice takes the first of the
-// first six that fits (widest batch first); CTAs of 256 threads leave room for two per SM.
+// Shapes (slots per CTA at most, threads), kBatchShapes; a CTA of 256 threads leaves room for two
+// per SM (half the shared memory each).
+static size_t shape_cap(int i) { return (i == 2 || i == 6) ? 110 * 1024 : 220 * 1024; }
+
 bool batched_shape_fits(const DevSys &h, int i)
 {
-    const size_t half = 110 * 1024, full = 220 * 1024;
+    const size_t cap = shape_cap(i);
     switch (i) {
-        case 0: return batched_fits<32, 512, 4>(h, full);
-        case 1: return batched_fits<16, 512, 4>(h, full);
-        case 2: return batched_fits<8, 256, 4>(h, half);
-        case 3: return batched_fits<8, 512, 2>(h, full);
-        case 4: return batched_fits<4, 512, 4>(h, full);
-        case 5: return batched_fits<16, 256, 4>(h, full);
-        case 6: return batched_fits<4, 256, 2>(h, half);
+        case 0: return batched_slots<32, 512, 4>(h, cap) > 0;
+        case 1: return batched_slots<16, 512, 4>(h, cap) > 0;
+        case 2: return batched_slots<8, 256, 4>(h, cap) > 0;
+        case 3: return batched_slots<8, 512, 2>(h, cap) > 0;
+        case 4: return batched_slots<4, 512, 4>(h, cap) > 0;
+        case 5: return batched_slots<16, 256, 4>(h, cap) > 0;
+        case 6: return batched_slots<4, 256, 2>(h, cap) > 0;
         default: return false;
     }
 }
@@ -746,30 +841,37 @@ int batched_width(const DevSys &h)
     return 0;
 }
 
-// launch with the requested shape (a.shape = index + 1) or the automatic one
-cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width)
+// one persistent launch over every system of the call, with the requested shape (index + 1) or
+// the automatic one: the first of the first six that every system fits
+cudaError_t run_batched(BatchMultiArgs a, const std::vector<const DevSys *> &hs, int shape, cudaStream_t st)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (hs.empty() || (int)hs.size() > kBatchMaxSystems) return cudaErrorInvalidValue;
+    auto all_fit = [&](int i) {
+        for (const DevSys *h : hs)
+            if (!batched_shape_fits(*h, i)) return false;
+        return true;
+    };
     int idx = -1;
-    if (a.shape > 0) {
-        if (a.shape > 7 || !batched_shape_fits(h, a.shape - 1)) return cudaErrorInvalidConfiguration;
-        idx = a.shape - 1;
+    if (shape > 0) {
+        if (shape > 7 || !all_fit(shape - 1)) return cudaErrorInvalidConfiguration;
+        idx = shape - 1;
     } else {
         for (int i = 0; i < 6 && idx < 0; ++i)
-            if (batched_shape_fits(h, i)) idx = i;
+            if (all_fit(i)) idx = i;
     }
     if (idx < 0) return cudaErrorInvalidConfiguration;
-    if (width) *width = kBatchShapes[idx][0];
+    const size_t cap = shape_cap(idx);
     switch (idx) {
-        case 0: return launch_batched<32, 512, 4>(a, h, sms, st);
-        case 1: return launch_batched<16, 512, 4>(a, h, sms, st);
-        case 2: return launch_batched<8, 256, 4>(a, h, sms, st);
-        case 3: return launch_batched<8, 512, 2>(a, h, sms, st);
-        case 4: return launch_batched<4, 512, 4>(a, h, sms, st);
-        case 5: return launch_batched<16, 256, 4>(a, h, sms, st);
-        case 6: return launch_batched<4, 256, 2>(a, h, sms, st);
+        case 0: return launch_batched<32, 512, 4>(a, hs, cap, sms, st);
+        case 1: return launch_batched<16, 512, 4>(a, hs, cap, sms, st);
+        case 2: return launch_batched<8, 256, 4>(a, hs, cap, sms, st);
+        case 3: return launch_batched<8, 512, 2>(a, hs, cap, sms, st);
+        case 4: return launch_batched<4, 512, 4>(a, hs, cap, sms, st);
+        case 5: return launch_batched<16, 256, 4>(a, hs, cap, sms, st);
+        case 6: return launch_batched<4, 256, 2>(a, hs, cap, sms, st);
         default: return cudaErrorInvalidConfiguration;
     }
 }

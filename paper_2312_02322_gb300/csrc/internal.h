@@ -39,6 +39,7 @@ struct DevSys {
     const double *diag_g;      // [L][n] G^lambda_ss (initial mean-field energy)
     const dbl4 *vcoef;      // [L][n_int] spline coefficients of v_lambda (c0..c3)
     const dbl4 *dvcoef;     // [P][L][n_int] spline coefficients of dv_lambda/dtheta_p
+    const float4 *dvcoef_f; // FP32 copy (mixed-precision systems with parameters)
     // PLAIN path: sliced-ELL (32-row slices) spline table of the non-zero M_nm(R)
     const int *sl_off;         // [n_slices+1] entry offsets (multiples of 32)
     const int *cols;           // [nnz_pad] internal column (padding: row itself, zero coefficients)
@@ -108,7 +109,7 @@ __device__ __forceinline__ long long mqct_clock_ns()
 }
 #endif
 
-// arguments of the batched mixed-precision launch (batched.cu)
+// arguments of the tensor-core launch sequence (tc_batched.cu): one system
 struct BatchArgs {
     const DevSys *sys;
     const mqct_traj *trajs;
@@ -121,20 +122,40 @@ struct BatchArgs {
     long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
     int nmax;
     int sys_idx;   // trajectories must name this system
-    int shape;     // FP32 batched kernel: 0 = automatic, else a kBatchShapes index + 1
-    int sm_limit;  // FP32 batched kernel: SMs its persistent grid may fill (0 = all)
-    int tc_slots;  // tensor-core path: trajectories in flight (0 = automatic)
+    int tc_slots;  // trajectories in flight (0 = automatic)
 };
-// the (slots per CTA, threads) instances of the FP32 batched kernel; the automatic choice takes
-// the first that fits (the last one is only ever chosen on request, e.g. by the autotuner)
-constexpr int kBatchShapes[7][2] = {{32, 256}, {16, 256}, {8, 256}, {16, 512}, {8, 512}, {4, 512}, {4, 256}};
-// true when shape index i (0-based) fits the system's basis
+
+// arguments of the FP32 batched launch over one or several systems (batched.cu)
+constexpr int kBatchMaxSystems = 16;
+struct BatchMultiArgs {
+    const DevSys *sys;            // [n_systems] device views
+    const mqct_traj *trajs;
+    const int *lists;             // [n_systems][n] work list of each system (trajectory indices, longest first)
+    const int *counts;            // [n_systems] lengths of the lists, or nullptr (one system, length n)
+    int *queues;                  // [n_systems] work counters, zero at launch
+    const double *work;           // [n_systems] estimated work of each system, or nullptr
+    int n, n_systems;
+    int sys_base;                 // trajectories name system sys_base + s
+    int slots[kBatchMaxSystems];  // slots per CTA of each system (set by run_batched)
+    double *pop;
+    double *amp;
+    mqct_diag *diag;
+    long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
+    int nmax;
+};
+// the (slots per CTA at most, threads) instances of the FP32 batched kernel; the automatic choice
+// takes the first of the first six that fits (the last one is only ever chosen on request, e.g. by
+// the autotuner)
+constexpr int kBatchShapes[7][2] = {{32, 512}, {16, 512}, {8, 256}, {8, 512}, {4, 512}, {16, 256}, {4, 256}};
+// true when shape index i (0-based) fits the system's basis with at least four slots
 bool batched_shape_fits(const DevSys &h, int i);
-cudaError_t run_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st, int *width);
+int batched_width(const DevSys &h);
+// one persistent FP32 launch over the systems hs (device views a.sys; at most kBatchMaxSystems);
+// shape 0 = automatic, else a kBatchShapes index + 1
+cudaError_t run_batched(BatchMultiArgs a, const std::vector<const DevSys *> &hs, int shape, cudaStream_t st);
 // stage-synchronous tensor-core launch sequence (tc_batched.cu); allocates its scratch with
 // stream-ordered allocation and synchronises `st` between chunks of steps
 mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st);
-int batched_width(const DevSys &h);
 
 mqct_status fail(mqct_status st, const std::string &msg);
 mqct_status cuda_fail(cudaError_t e, const char *what);

@@ -579,23 +579,11 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
     if ((e = cudaMemsetAsync(queue, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     if (prec != MQCT_FP64) {
-        BatchArgs ba{};
-        ba.trajs = dtr; ba.pop = dpop; ba.amp = damp; ba.diag = ddiag; ba.nmax = nmax;
-        ba.t_start = dts; ba.t_done = dtd;
-        if (n_systems == 1) {
-            ba.sys = systems[0]->s.d; ba.order = order; ba.n = n; ba.queue = queue; ba.sys_idx = 0;
-            ba.shape = shape_of(0); ba.tc_slots = slots_of(0);
-            if (prec == MQCT_BF16X3) {
-                const mqct_status ts = run_tc_batched(ba, systems[0]->s.h, st);
-                if (ts != MQCT_OK) return ts;
-            } else if ((e = run_batched(ba, systems[0]->s.h, st, nullptr)) != cudaSuccess) {
-                return cuda_fail(e, "batched launch");
-            }
-        } else {
-            // uneven batch of several systems: the work order split per system (stable, so each
-            // list stays longest first) and the estimated work of each system
-            int *lists = nullptr, *counts = nullptr, *queues = nullptr;
-            double *work = nullptr;
+        // uneven batch of several systems: the work order split per system (stable, so each list
+        // stays longest first) and the estimated work of each system, all on the device
+        int *lists = order, *counts = nullptr, *queues = queue;
+        double *work = nullptr;
+        if (n_systems > 1) {
             if ((e = sa.get((void **)&lists, sizeof(int) * (size_t)n * n_systems)) != cudaSuccess ||
                 (e = sa.get((void **)&counts, sizeof(int) * n_systems)) != cudaSuccess ||
                 (e = sa.get((void **)&queues, sizeof(int) * n_systems)) != cudaSuccess ||
@@ -612,14 +600,38 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
                 if ((e = cub::DeviceSelect::If(sel_tmp, sel_bytes, order, lists + (size_t)i * n, counts + i, n,
                                                IsSystem{dtr, i}, st)) != cudaSuccess)
                     return cuda_fail(e, "cub::DeviceSelect");
-            std::vector<int> hc(n_systems);
-            std::vector<double> hw(n_systems);
-            if ((e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * n_systems, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(hw.data(), work, sizeof(double) * n_systems, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(st)) != cudaSuccess)
-                return cuda_fail(e, "work partition");
-            if (prec == MQCT_BF16X3) {
+        }
+        if (prec == MQCT_FP32) {
+            // one persistent launch over every system of the call (at most kBatchMaxSystems per
+            // launch): CTAs bind to systems on the device
+            BatchMultiArgs ma{};
+            ma.trajs = dtr; ma.pop = dpop; ma.amp = damp; ma.diag = ddiag; ma.nmax = nmax;
+            ma.t_start = dts; ma.t_done = dtd; ma.n = n;
+            int shape = 0;
+            for (int i = 0; i < n_systems && !shape; ++i) shape = shape_of(i);
+            for (int g0 = 0; g0 < n_systems; g0 += kBatchMaxSystems) {
+                const int ng = std::min(kBatchMaxSystems, n_systems - g0);
+                ma.sys = dsys + g0; ma.lists = lists + (size_t)g0 * n; ma.counts = counts ? counts + g0 : nullptr;
+                ma.queues = queues + g0; ma.work = work ? work + g0 : nullptr; ma.n_systems = ng; ma.sys_base = g0;
+                std::vector<const DevSys *> hs;
+                for (int i = 0; i < ng; ++i) hs.push_back(&systems[g0 + i]->s.h);
+                if ((e = run_batched(ma, hs, shape, st)) != cudaSuccess) return cuda_fail(e, "batched launch");
+            }
+        } else {
+            BatchArgs ba{};
+            ba.trajs = dtr; ba.pop = dpop; ba.amp = damp; ba.diag = ddiag; ba.nmax = nmax;
+            ba.t_start = dts; ba.t_done = dtd;
+            if (n_systems == 1) {
+                ba.sys = systems[0]->s.d; ba.order = order; ba.n = n; ba.queue = queue; ba.sys_idx = 0;
+                ba.tc_slots = slots_of(0);
+                const mqct_status ts = run_tc_batched(ba, systems[0]->s.h, st);
+                if (ts != MQCT_OK) return ts;
+            } else {
                 // the stage-synchronous path fills the GPU with one system at a time
+                std::vector<int> hc(n_systems);
+                if ((e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * n_systems, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                    return cuda_fail(e, "work partition");
                 for (int i = 0; i < n_systems; ++i) {
                     if (hc[i] == 0) continue;
                     BatchArgs bi = ba;
@@ -628,36 +640,6 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
                     const mqct_status ts = run_tc_batched(bi, systems[i]->s.h, st);
                     if (ts != MQCT_OK) return ts;
                 }
-            } else {
-                // one persistent batched kernel per system, concurrently on forked streams, each
-                // on a share of the SMs proportional to its estimated work
-                int dev = 0, sms = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                double tot = 0.0;
-                for (int i = 0; i < n_systems; ++i) tot += hc[i] ? hw[i] : 0.0;
-                std::vector<cudaStream_t> ss(n_systems, nullptr);
-                std::vector<cudaEvent_t> ev(n_systems + 1, nullptr);
-                for (auto &x : ev)
-                    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-                if (e == cudaSuccess) e = cudaEventRecord(ev[n_systems], st);
-                for (int i = 0; i < n_systems && e == cudaSuccess; ++i) {
-                    if (hc[i] == 0) continue;
-                    e = cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking);
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss[i], ev[n_systems], 0);
-                    BatchArgs bi = ba;
-                    bi.sys = systems[i]->s.d; bi.order = lists + (size_t)i * n; bi.n = hc[i]; bi.queue = queues + i;
-                    bi.sys_idx = i; bi.shape = shape_of(i);
-                    bi.sm_limit = std::max(1, (int)std::lround(sms * (tot > 0 ? hw[i] / tot : 1.0 / n_systems)));
-                    if (e == cudaSuccess) e = run_batched(bi, systems[i]->s.h, ss[i], nullptr);
-                    if (e == cudaSuccess) e = cudaEventRecord(ev[i], ss[i]);
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[i], 0);
-                }
-                for (int i = 0; i < n_systems; ++i)
-                    if (ss[i]) cudaStreamDestroy(ss[i]);
-                for (auto &x : ev)
-                    if (x) cudaEventDestroy(x);
-                if (e != cudaSuccess) return cuda_fail(e, "batched launch (several systems)");
             }
         }
     } else {

@@ -320,6 +320,13 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     up_(diag_g, &D.diag_g);
     up_(vcoef, &D.vcoef);
     if (P > 0) up_(dvcoef, &D.dvcoef);
+    if (P > 0 && d->precision != MQCT_FP64) {
+        // FP32 copy for the mixed-precision adjoint
+        std::vector<float4> dvf(dvcoef.size());
+        for (size_t i = 0; i < dvcoef.size(); ++i)
+            dvf[i] = make_float4((float)dvcoef[i].x, (float)dvcoef[i].y, (float)dvcoef[i].z, (float)dvcoef[i].w);
+        up_(dvf, &D.dvcoef_f);
+    }
 
     S.info.n_states = n;
     S.info.n_levels = n_levels;

@@ -117,3 +117,78 @@ def test_autograd_function(mq):
         lm = float((CS.apply(torch.tensor(tm), p, ts, 32) * wts).sum())
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[k]) <= 1e-5 * max(abs(g[k]), 1e-3 * np.max(np.abs(g))), (k, fd, g[k])
+
+
+def test_mixed_adjoint_matches_fp64_adjoint(mq):
+    """The mixed adjoint (FP32 amplitudes and cotangents, compensated step update, FP64 classical
+    motion and parameter gradient) against the FP64 adjoint of the same trajectories and weights."""
+    p, ts = case(jmax=4, n_b=3, energies=(700.0,), init_js=(0, 1))
+    s64 = mq.System.diatom(p, path="factorised", precision="fp64", with_params=True)
+    s32 = mq.System.diatom(p, path="factorised", precision="fp32", with_params=True)
+    tr = mq.make_trajs(ts, s64)
+    _, _, diag = mq.propagate(s64, tr, device=False)
+    w = mq.sigma_weights(ts, diag["status"])
+    rng = np.random.default_rng(11)
+    dls = rng.standard_normal((ts.n_groups, s64.n_levels))
+    g64 = mq.adjoint(s64, tr, w, ts.group, ts.n_groups, dls, ckpt=16)
+    g32 = mq.adjoint(s32, tr, w, ts.group, ts.n_groups, dls, ckpt=16)
+    err = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
+    assert err < 1e-3, err
+
+
+def test_adjoint_28_terms_matches_oracle_tangent(mq, ora):
+    """More than 16 expansion terms: the atom + asymmetric top with all cos-type terms lam <= 6
+    (28 terms, 56 parameters), FP64 adjoint against the oracle's forward tangent (1e-8)."""
+    p, ts = W.small_asym_workload(jmax=4, max_states=60, lam_max=6, energies=(1500.0,), n_per_e=3, b_max=6.0)
+    ts.r0 = ts.r_end = 14.0
+    assert p.n_terms == 28
+    sys_ = mq.System.asym_top(p, path="factorised", with_params=True)
+    tr = mq.make_trajs(ts, sys_)
+    _, _, diag = mq.propagate(sys_, tr, device=False)
+    assert np.all(diag["status"] == 0)
+    w = mq.sigma_weights(ts, diag["status"])
+    rng = np.random.default_rng(12)
+    dls = rng.standard_normal((ts.n_groups, sys_.n_levels))
+    g = mq.adjoint(sys_, tr, w, ts.group, ts.n_groups, dls, ckpt=32)
+    osys = ora.asym_system(p, with_params=True)
+    lab = {(int(l), int(m)): i for i, (l, m) in enumerate(zip(osys.level, osys.mq))}
+    init = [lab[(int(l), int(m))] for l, m in zip(ts.init_j, ts.init_m)]
+    amp, dpop, res = ora.tangent(osys, ts.e_coll, ts.b, init, r0=ts.r0, r_end=ts.r_end, dt=ts.dt)
+    assert np.array_equal(res["steps"], diag["steps"])
+    want = np.zeros(dpop.shape[1])
+    for t in range(ts.n):
+        for s in range(osys.n):
+            want += w[t] * dpop[t, :, s] * dls[ts.group[t], osys.level[s]]
+    assert np.max(np.abs(g - want)) < 1e-8 * np.max(np.abs(want))
+
+
+def test_adjoint_with_work_vectors_in_global_memory(mq):
+    """N = 784 (j <= 27): the FP64 adjoint's work vectors exceed shared memory and live in global
+    memory; central differences (h = 1e-5 relative) of the forward path agree to 1e-5."""
+    p = W.diatom_pes_params(jmax=27, n_grid=200)
+    ts = W.regular_set([3000.0], [0], n_b=2, b_max=6.0, m_avg="one", r0=14.0)
+    sys_ = mq.System.diatom(p, path="factorised", with_params=True)
+    tr = mq.make_trajs(ts, sys_)
+    _, _, diag = mq.propagate(sys_, tr, device=False)
+    assert np.all(diag["status"] == 0)
+    w = mq.sigma_weights(ts, diag["status"])
+    rng = np.random.default_rng(13)
+    dls = rng.standard_normal((ts.n_groups, sys_.n_levels))
+    g = mq.adjoint(sys_, tr, w, ts.group, ts.n_groups, dls, ckpt=64)
+    th0 = np.concatenate([p.A, p.beta])
+
+    def loss(th):
+        s2 = mq.System.diatom(mq._diatom_with(p, th), path="factorised")
+        pop, _, d2 = mq.propagate(s2, mq.make_trajs(ts, s2), device=False)
+        return float(np.sum(dls * mq.cross_sections(s2, pop, w, ts.group, ts.n_groups))), d2["steps"]
+
+    for k in (1, len(p.A) + 1):
+        h = 1e-5 * abs(th0[k])
+        tp, tm = th0.copy(), th0.copy()
+        tp[k] += h
+        tm[k] -= h
+        lp, sp = loss(tp)
+        lm, sm = loss(tm)
+        assert np.array_equal(sp, sm) and np.array_equal(sp, diag["steps"])
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-5 * max(abs(g[k]), 1e-3 * np.max(np.abs(g))), (k, fd, g[k])
