@@ -101,14 +101,6 @@ __device__ __forceinline__ R wsum(R v)
     return v;
 }
 
-// error-free sum of two FP32 numbers: s + e == a + b exactly
-__device__ __forceinline__ void adj_two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
 // sum over the warps of per-warp values wred[w * kAdjRed + i] (i < m) into c.red[i] (FP64); the
 // FP32 variant sums compensated and converts once
 template <class R>
@@ -124,7 +116,7 @@ __device__ void cross_warp(int m, AdjCtl<R> &c, const R *wred)
             float hi = 0.f, lo = 0.f;
             for (int w = 0; w < nw; ++w) {
                 float e;
-                adj_two_sum(hi, wred[w * kAdjRed + i], hi, e);
+                two_sum(hi, wred[w * kAdjRed + i], hi, e);
                 lo += e;
             }
             c.red[i] = (double)hi + (double)lo;
@@ -569,8 +561,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjArgs a)
                         const float h6 = (float)(dt / 6.0);
                         const V a0 = m.A[r], e0 = m.E[r];
                         float sx, sy, ex, ey;
-                        adj_two_sum(a0.x, fmaf(h6, acc.x, e0.x), sx, ex);
-                        adj_two_sum(a0.y, fmaf(h6, acc.y, e0.y), sy, ey);
+                        two_sum(a0.x, fmaf(h6, acc.x, e0.x), sx, ex);
+                        two_sum(a0.y, fmaf(h6, acc.y, e0.y), sy, ey);
                         m.A[r] = make_float2(sx, sy);
                         m.E[r] = make_float2(ex, ey);
                     } else {

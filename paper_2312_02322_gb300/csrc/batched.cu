@@ -82,37 +82,6 @@ __device__ __forceinline__ void st4(float2 *p, int e0, const F4x2 &r)
     *reinterpret_cast<float4 *>(p + swz(e0 + 2)) = make_float4(r.v[2].x, r.v[2].y, r.v[3].x, r.v[3].y);
 }
 
-// error-free sum of two FP32 numbers: s + e == a + b exactly
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// double without the FP64 pipe: for positive finite x, x >= y (y > 0) compares the bit patterns
-__device__ __forceinline__ bool ge_pos(double x, double y)
-{
-    return __double_as_longlong(x) >= __double_as_longlong(y);
-}
-__device__ __forceinline__ bool finite64(double x)
-{
-    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
-}
-
-// the stage update of one classical component (lane layout of the slot warps): derivative
-// l = alpha X + beta, accumulator, next stage input (s < 3) or step update (s = 3).  The look-ahead
-// of R calls the same function, so both produce the same bits.
-__device__ __forceinline__ void stage_component(int s, double alpha, double X, double beta, double hdt, double dt,
-                                                double h6, double q, double &qs, double &lacc)
-{
-    const double l = fma(alpha, X, beta);
-    if (s == 0) lacc = l;
-    else lacc = fma((s == 1 || s == 2) ? 2.0 : 1.0, l, lacc);
-    if (s < 3) qs = fma(s == 2 ? dt : hdt, l, q);
-    else qs = fma(h6, lacc, q);
-}
-
 // per-slot values the element warps read during one stage, written by the slot warps during the
 // stage before (double-buffered by stage parity, so that writer and readers never overlap)
 template <int B>

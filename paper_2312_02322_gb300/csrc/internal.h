@@ -31,6 +31,7 @@ struct DevSys {
     int path, precision, flags;
     double mu, r_min, h, inv_h;
     const double *lev_energy;  // [n_levels]
+    const float *lev_energy_f; // [n_levels] FP32 copy (mixed-precision systems)
     const int *lev;            // [n]  level of each internal state
     const int *perm;           // [n]  internal -> caller index
     const int *inv;            // [n]  caller -> internal index

@@ -310,6 +310,10 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     mqct_status st = MQCT_OK;
     auto up_ = [&](auto &v, auto **dst) { if (st == MQCT_OK) st = upload(S, v, dst); };
     up_(lev_e, &D.lev_energy);
+    if (d->precision != MQCT_FP64) {
+        std::vector<float> lev_ef(lev_e.begin(), lev_e.end());
+        up_(lev_ef, &D.lev_energy_f);
+    }
     up_(S.lev, &D.lev);
     up_(S.perm, &D.perm);
     up_(S.inv, &D.inv);

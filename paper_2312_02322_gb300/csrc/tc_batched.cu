@@ -10,10 +10,14 @@
 //               then per element the Coriolis stencil, da/dt = -i exp(iEt) w + (dPhi/dt/2)
 //               exp(iEt) D c (Eq. 5), the compensated RK4 accumulation and the next stage input,
 //               with per-slot partial sums of force, torque and (stage 0) diagnostics;
-//   k_tc_slots  one warp per slot, FP64: classical stage update (Eqs. 7-10), bookkeeping, stop
-//               rule, refill, the spline values and phase factors of the next stage.
-// The host runs chunks of steps as one CUDA graph and checks the number of live slots between
-// chunks.
+//   k_tc_slots  one warp per eight slots (one lane per classical component and slot), FP64:
+//               classical stage update (Eqs. 7-10), bookkeeping, stop rule, refill, the spline
+//               values and phase factors of the next stage.
+// The classical state lives in global memory with one lane per (component, slot) in k_tc_slots
+// (eight slots per warp), phase arguments are 64-bit fixed-point turn counts and the partial sums
+// are compensated FP32, so that neither kernel runs FP64 per element or per level.  Chunks of steps
+// run inside a CUDA graph's conditional WHILE node whose condition the last kernel of each chunk
+// sets from the number of live slots: one graph launch runs every trajectory to its end.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -25,6 +29,7 @@
 
 #include "internal.h"
 #include "tc_ptx.cuh"
+#include "traj_common.cuh"
 
 namespace mqct {
 
@@ -35,10 +40,11 @@ constexpr long long kTcWait = 1ll << 24;
 
 enum { TS_IDLE = 0, TS_ACTIVE = 1, TS_FINAL = 2, TS_WAIT = 3 };
 
+// per-slot values that are not per component (the four component lanes of a slot read them)
 struct TSlot {
-    double q[4], qs[4], lacc[4];
-    double dt, r_end, e0, j0, ndev, edev, jdev, x, phidot, inv_mu;
-    int kint, status, steps, max_steps, traj, state, s0;
+    double dt, h6, r_end, e0, j0, ndev, edev, jdev;
+    double ir, i2m, phid, last_dt;  // 1/R, (1/mu)/R^2 and dPhi/dt of the current stage; dt of inc
+    int status, steps, max_steps, traj, state, s0;
 };
 
 struct TcState {
@@ -47,11 +53,12 @@ struct TcState {
     const int *order;
     int n, S;                 // trajectories, slots
     int *queue;
-    int *live;                // live slots after the last step
+    int *live;                // live slots after the last step; [1]: error flag
     double *pop, *amp;
     mqct_diag *diag;
     long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
     int nmax, sys_idx;
+    double inv_mu;
     float2 *C[2];             // [n][S] stage amplitudes (phase rotated), double buffered
     float2 *A, *ACC;          // [n][S]
     float *coef;              // [2][L][S] v_l and v_l' at each slot's stage R
@@ -59,21 +66,11 @@ struct TcState {
     float *hp, *dtf;          // [S] dPhi/dt / 2 and dt (FP32 views)
     int *state;               // [S]
     float2 *PHa, *PHb;        // [n_levels][S]
-    double *part;             // [n_tiles][S][6] per-row-tile partial sums
+    unsigned long long *inc;  // [n_levels][S] fixed-point phase increments
+    float2 *part;             // [n_tiles][6][S] per-row-tile partial sums (hi, lo)
+    double *Q, *QS, *LACC;    // [4][S] classical state, stage input, RK4 accumulator
     TSlot *slot;              // [S]
 };
-
-__device__ __forceinline__ float2 tc_phase(double e, double t)
-{
-    const double two_pi_hi = 6.283185307179586232, two_pi_lo = 2.4492935982947064e-16;
-    const double th = e * t;
-    const double k = rint(th * 0.15915494309189535);
-    double r = fma(-k, two_pi_hi, th);
-    r = fma(-k, two_pi_lo, r);
-    float s, c;
-    sincosf((float)r, &s, &c);
-    return make_float2(c, -s);
-}
 
 __device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
@@ -136,7 +133,7 @@ __device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S,
         const float pp = a0.x * a0.x + a0.y * a0.y;
         part[2] += c.x * w.x + c.y * w.y;
         part[3] += pp;
-        part[4] += (float)S.lev_energy[in.lev] * pp;
+        part[4] += S.lev_energy_f[in.lev] * pp;
         part[5] += a0.x * da.y - a0.y * da.x;
     }
     if (st == TS_FINAL) {
@@ -354,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
     __syncthreads();
     // stage w and u through shared memory (the ring and B buffers are free now)
     float2 *Wst = reinterpret_cast<float2 *>(sm), *Ust = Wst + 128 * kTcWs;
-    double *red = reinterpret_cast<double *>(Ust + 128 * kTcWs);  // [8][64][6]
+    float *red = reinterpret_cast<float *>(Ust + 128 * kTcWs);  // [8][64][6]
     if (!err && warp < kTcEpiWarps) {
         const int row = 32 * (warp & 3) + lane, j0 = 16 * (warp >> 2);
 #pragma unroll
@@ -393,15 +390,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
                     tc_elem_apply(T, S, s, cur, r0 + row, sl, st, in[k], wt, ut, part);
                 }
             }
-            for (int k = 0; k < 6; ++k) red[(g * kTcSlotsPerTile + j) * 6 + k] = (double)part[k];
+            for (int k = 0; k < 6; ++k) red[(g * kTcSlotsPerTile + j) * 6 + k] = part[k];
         }
         __syncthreads();
         if (tid < kTcSlotsPerTile) {
-            double acc6[6] = {0, 0, 0, 0, 0, 0};
-            for (int g = 0; g < 8; ++g)
-                for (int k = 0; k < 6; ++k) acc6[k] += red[(g * kTcSlotsPerTile + tid) * 6 + k];
-            double *o = T.part + ((size_t)rt * T.S + s0 + tid) * 6;
-            for (int k = 0; k < 6; ++k) o[k] = acc6[k];
+            // the eight row groups of the tile, compensated
+            for (int k = 0; k < 6; ++k) {
+                float hi = 0.f, lo = 0.f;
+                for (int g = 0; g < 8; ++g) {
+                    float e2;
+                    two_sum(hi, red[(g * kTcSlotsPerTile + tid) * 6 + k], hi, e2);
+                    lo += e2;
+                }
+                T.part[((size_t)rt * 6 + k) * T.S + s0 + tid] = make_float2(hi, lo);
+            }
         }
     } else if (tid == 0) {
         atomicOr(T.live + 1, 1);  // error flag: a bounded wait ran out
@@ -412,225 +414,333 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
 }
 
 // ---------------------------------------------------------------------------------------------
-// per-slot work, FP64
-__device__ void tc_locate(const DevSys &S, TSlot &m)
+// per-slot work: one warp per eight slots, lane 8 c + j carries component c of (R, P_R, Phi, P_Phi)
+// of slot j, so one FP64 instruction advances four components of eight trajectories; every lane
+// of the warp runs the same instructions (lanes of slots >= S compute on copies and store nothing)
+struct SlotLane {
+    int sc, sj, sl, slc;
+    bool valid;
+    unsigned m4;  // the four lanes of this slot
+};
+
+__device__ __forceinline__ SlotLane slot_lane(const TcState &T)
 {
-    const double R = m.qs[0];
-    int k = (int)floor((R - S.r_min) * S.inv_h);
-    k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
-    m.kint = k;
-    m.x = R - (S.r_min + k * S.h);
-    const double ir = 1.0 / R;
-    m.phidot = m.qs[3] * m.inv_mu * ir * ir;
-    if (R < S.r_min) m.status |= MQCT_TRAJ_TABLE_RANGE;
+    SlotLane L;
+    const int lane = threadIdx.x & 31, warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    L.sc = lane >> 3;
+    L.sj = lane & 7;
+    L.sl = 8 * warp + L.sj;
+    L.valid = L.sl < T.S;
+    L.slc = L.valid ? L.sl : T.S - 1;
+    L.m4 = 0x01010101u << L.sj;
+    return L;
 }
 
-// spline values of the next stage, FP32 views, identity-term sums (one warp per slot; the
-// slot record is final when the warp calls this)
-__device__ void tc_publish(const TcState &T, const DevSys &S, int sl, int lane)
+// claim the next valid trajectory for slot L.sl (its four lanes together); returns the new state
+// (WAIT: column initialised at the next stage 3, or IDLE) and sets the lane's component q
+__device__ int tc_claim(const TcState &T, const DevSys &S, const SlotLane &L, double &q)
 {
-    const TSlot &m = T.slot[sl];
-    const int state = m.state;
-    if (lane == 0) T.state[sl] = state;
-    if (state == TS_IDLE) {
-        for (int l = lane; l < S.L; l += 32) T.coef[(size_t)l * T.S + sl] = T.coef[((size_t)S.L + l) * T.S + sl] = 0.f;
-        if (lane == 0) {
-            T.vid[sl] = T.vid[T.S + sl] = 0.f;
-            T.hp[sl] = 0.f;
-            T.dtf[sl] = 1.f;
-        }
-        return;
-    }
-    float v0 = 0.f, d0 = 0.f;
-    const float x = (float)m.x;
-    const int kint = m.kint;
-    for (int l = lane; l < S.L; l += 32) {
-        const float4 c = S.vcoef_f[(size_t)l * S.n_int + kint];
-        const float v = fmaf(x, fmaf(x, fmaf(x, c.w, c.z), c.y), c.x);
-        const float dv = fmaf(x, fmaf(3.0f * x, c.w, 2.0f * c.z), c.y);
-        T.coef[(size_t)l * T.S + sl] = v;
-        T.coef[((size_t)S.L + l) * T.S + sl] = dv;
-        if ((S.id_mask >> l) & 1ull) { v0 += v; d0 += dv; }
-    }
-    for (int o = 16; o; o >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-    }
-    if (lane == 0) {
-        T.vid[sl] = v0;
-        T.vid[T.S + sl] = d0;
-        T.hp[sl] = (float)(0.5 * m.phidot);
-        T.dtf[sl] = (float)m.dt;
-    }
-}
-
-// phase factors exp(-i E_l t) of every level for one slot (one warp): kind 1 -> PHa at t,
-// kind 2 -> PHb at t, kind 3 -> start of a trajectory: PHa = 1, PHb at t = dt/2
-__device__ void tc_phases(const TcState &T, const DevSys &S, int sl, int lane, int kind, double t)
-{
-    for (int l = lane; l < S.n_levels; l += 32) {
-        const float2 ph = tc_phase(S.lev_energy[l], t);
-        if (kind == 1) T.PHa[(size_t)l * T.S + sl] = ph;
-        else {
-            T.PHb[(size_t)l * T.S + sl] = ph;
-            if (kind == 3) T.PHa[(size_t)l * T.S + sl] = make_float2(1.f, 0.f);
-        }
-    }
-}
-
-__device__ void tc_claim(const TcState &T, const DevSys &S, int sl)
-{
-    TSlot &m = T.slot[sl];
+    TSlot &m = T.slot[L.sl];
     for (;;) {
-        const int item = atomicAdd(T.queue, 1);
-        if (item >= T.n) {
-            m.state = TS_IDLE;
-            return;
-        }
+        int item = 0;
+        if (L.sc == 0) item = atomicAdd(T.queue, 1);
+        item = __shfl_sync(L.m4, item, L.sj);
+        if (item >= T.n) return TS_IDLE;
         const int t = T.order ? T.order[item] : item;
         const mqct_traj tr = T.trajs[t];
-        const bool ok = tr.system_idx == T.sys_idx && tr.dt > 0.0 && tr.e_coll > 0.0 && tr.b >= 0.0 && tr.r0 > 0.0 &&
-                        tr.b < tr.r0 && isfinite(tr.r_end) && tr.max_steps >= 0 && tr.init_state >= 0 &&
-                        tr.init_state < S.n;
-        if (!ok) {
-            if (T.diag) {
+        if (!traj_valid(tr, S, T.sys_idx)) {
+            if (T.diag && L.sc == 0) {
                 mqct_diag d = {0, MQCT_TRAJ_INVALID, 0.0, 0.0, 0.0, 0.0};
                 T.diag[t] = d;
             }
+            __syncwarp(L.m4);
             continue;
         }
-        if (T.t_start) T.t_start[t] = mqct_clock_ns();
+        if (T.t_start && L.sc == 0) T.t_start[t] = mqct_clock_ns();
         const int s0 = S.inv[tr.init_state];
-        int k = (int)floor((tr.r0 - S.r_min) * S.inv_h);
-        k = k < 0 ? 0 : (k > S.n_int - 1 ? S.n_int - 1 : k);
-        const double x = tr.r0 - (S.r_min + k * S.h);
-        double m00 = 0.0;
-        for (int l = 0; l < S.L; ++l) {
-            const dbl4 c = S.vcoef[(size_t)l * S.n_int + k];
-            m00 += (c.x + x * (c.y + x * (c.z + x * c.w))) * S.diag_g[(size_t)l * S.n + s0];
+        int k0;
+        double x0;
+        bool bl;
+        locate_interval(S, tr.r0, k0, x0, bl);
+        double mm = 0.0;  // initial mean field M_ss(r0): the four lanes split the terms
+        for (int l = L.sc; l < S.L; l += 4) mm += spline_fp64(S, l, k0, x0) * S.diag_g[(size_t)l * S.n + s0];
+        mm += __shfl_xor_sync(L.m4, mm, 8);
+        mm += __shfl_xor_sync(L.m4, mm, 16);
+        double q4[4];
+        initial_state(S, tr, mm, q4);
+        q = q4[L.sc];
+        const bool new_dt = tr.dt != m.last_dt;
+        __syncwarp(L.m4);
+        if (L.sc == 0) {
+            m.dt = tr.dt; m.h6 = tr.dt / 6.0; m.r_end = tr.r_end; m.max_steps = tr.max_steps;
+            m.ndev = m.edev = m.jdev = 0.0;
+            m.status = 0; m.steps = 0; m.traj = t; m.s0 = s0;
+            m.last_dt = tr.dt;
         }
-        const double lz = tr.b * sqrt(2.0 * S.mu * tr.e_coll);
-        m.q[0] = tr.r0; m.q[2] = 0.0; m.q[3] = lz;
-        m.q[1] = -sqrt(2.0 * S.mu * (tr.e_coll - m00) - lz * lz / (tr.r0 * tr.r0));
-        for (int i = 0; i < 4; ++i) m.qs[i] = m.q[i];
-        m.dt = tr.dt; m.r_end = tr.r_end; m.max_steps = tr.max_steps;
-        m.ndev = m.edev = m.jdev = 0.0;
-        m.inv_mu = 1.0 / S.mu;
-        m.status = 0; m.steps = 0; m.traj = t; m.s0 = s0;
-        m.state = TS_WAIT;
-        m.kint = k; m.x = x; m.phidot = 0.0;
-        return;
+        if (new_dt)
+            for (int l = L.sc; l < S.n_levels; l += 4) T.inc[(size_t)l * T.S + L.sl] = phase_increment(S.lev_energy[l], tr.dt);
+        __syncwarp(L.m4);
+        return TS_WAIT;
     }
 }
 
-// one warp per slot: claim the first trajectory and initialise its column
+// the quantities of the next stage at the slot's stage input qs: interval, spline values of every
+// term (FP32 views), 1/R, (1/mu)/R^2, dPhi/dt; returns the TABLE_RANGE bit.  Called by every lane
+// of the warp (publish: write the views of this slot).
+__device__ int tc_next_stage(const TcState &T, const DevSys &S, const SlotLane &L, double qs, bool publish,
+                             double &ir, double &i2m, double &phid)
+{
+    const unsigned full = 0xffffffffu;
+    const double R = __shfl_sync(full, qs, L.sj), PP = __shfl_sync(full, qs, 24 + L.sj);
+    int k;
+    double x;
+    bool below;
+    locate_interval(S, R, k, x, below);
+    ir = 1.0 / R;
+    i2m = T.inv_mu * ir * ir;
+    phid = PP * i2m;
+    const float xf = (float)x;
+    float v0 = 0.f, d0 = 0.f;
+    for (int l = L.sc; l < S.L; l += 4) {
+        const float4 c = S.vcoef_f[(size_t)l * S.n_int + k];
+        const float v = fmaf(xf, fmaf(xf, fmaf(xf, c.w, c.z), c.y), c.x);
+        const float dv = fmaf(xf, fmaf(3.0f * xf, c.w, 2.0f * c.z), c.y);
+        if (publish) {
+            T.coef[(size_t)l * T.S + L.sl] = v;
+            T.coef[((size_t)S.L + l) * T.S + L.sl] = dv;
+        }
+        if ((S.id_mask >> l) & 1ull) { v0 += v; d0 += dv; }
+    }
+    v0 += __shfl_xor_sync(full, v0, 8);
+    v0 += __shfl_xor_sync(full, v0, 16);
+    d0 += __shfl_xor_sync(full, d0, 8);
+    d0 += __shfl_xor_sync(full, d0, 16);
+    if (publish && L.sc == 0) {
+        T.vid[L.sl] = v0;
+        T.vid[T.S + L.sl] = d0;
+        T.hp[L.sl] = (float)phid * 0.5f;
+    }
+    return below ? MQCT_TRAJ_TABLE_RANGE : 0;
+}
+
+// an idle slot's published views
+__device__ void tc_publish_idle(const TcState &T, const DevSys &S, const SlotLane &L)
+{
+    for (int l = L.sc; l < S.L; l += 4) T.coef[(size_t)l * T.S + L.sl] = T.coef[((size_t)S.L + l) * T.S + L.sl] = 0.f;
+    if (L.sc == 0) {
+        T.vid[L.sl] = T.vid[T.S + L.sl] = 0.f;
+        T.hp[L.sl] = 0.f;
+        T.dtf[L.sl] = 1.f;
+    }
+}
+
+// phase factors exp(-i E_l t) of the slot at stage time t = n_half dt / 2 into PH (the four lanes
+// split the levels)
+__device__ void tc_phases(const TcState &T, const DevSys &S, const SlotLane &L, float2 *PH, unsigned n_half)
+{
+    for (int l = L.sc; l < S.n_levels; l += 4)
+        PH[(size_t)l * T.S + L.sl] = phase_factor(T.inc[(size_t)l * T.S + L.sl], n_half);
+}
+
+// claim the first trajectory of every slot, initialise its column and views
 __global__ void __launch_bounds__(128) k_tc_init(TcState T)
 {
     const DevSys &S = *T.sys;
-    const int lane = threadIdx.x & 31, sl = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (sl >= T.S) return;
-    TSlot &m = T.slot[sl];
-    if (lane == 0) tc_claim(T, S, sl);
+    const SlotLane L = slot_lane(T);
+    const int lane = threadIdx.x & 31;
+    double q = 0.0;
+    int state = TS_IDLE;
+    if (L.valid) {
+        if (L.sc == 0) T.slot[L.sl].last_dt = -1.0;
+        __syncwarp(L.m4);
+        state = tc_claim(T, S, L, q);
+    }
+    double ir = 0.1, i2m = 0.0, phid = 0.0;
+    const bool go = L.valid && state == TS_WAIT;
+    const int tr = tc_next_stage(T, S, L, go ? q : 10.0, go, ir, i2m, phid);
+    if (go) {
+        TSlot &m = T.slot[L.sl];
+        const int ms = m.max_steps;
+        state = ms > 0 ? TS_ACTIVE : TS_FINAL;
+        __syncwarp(L.m4);
+        if (L.sc == 0) {
+            m.status |= tr | (ms <= 0 ? MQCT_TRAJ_MAX_STEPS : 0);
+            m.ir = ir; m.i2m = i2m; m.phid = phid;
+            T.dtf[L.sl] = (float)m.dt;
+        }
+        tc_phases(T, S, L, T.PHb, 1u);
+        for (int l = L.sc; l < S.n_levels; l += 4) T.PHa[(size_t)l * T.S + L.sl] = make_float2(1.f, 0.f);
+    } else if (L.valid) {
+        tc_publish_idle(T, S, L);
+    }
+    if (L.valid) {
+        T.Q[(size_t)L.sc * T.S + L.sl] = q;
+        T.QS[(size_t)L.sc * T.S + L.sl] = q;
+        T.LACC[(size_t)L.sc * T.S + L.sl] = 0.0;
+        if (L.sc == 0) {
+            T.slot[L.sl].state = state;
+            T.state[L.sl] = state;
+        }
+    }
     __syncwarp();
-    if (m.state == TS_WAIT) {
+    // the columns of the warp's eight slots: e_s0, accumulator 0, input e_s0
+    for (int j = 0; j < 8; ++j) {
+        const int sl = 8 * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) + j;
+        if (sl >= T.S) break;
+        const int st = T.slot[sl].state;
+        if (st != TS_ACTIVE && st != TS_FINAL) continue;
+        const int s0 = T.slot[sl].s0;
         for (int r = lane; r < S.n; r += 32) {
-            const float2 v = make_float2(r == m.s0 ? 1.0f : 0.0f, 0.0f);
+            const float2 v = make_float2(r == s0 ? 1.0f : 0.0f, 0.0f);
             const size_t e = (size_t)r * T.S + sl;
             T.A[e] = v; T.ACC[e] = make_float2(0.f, 0.f); T.C[0][e] = v;
         }
-        __syncwarp();
-        if (lane == 0) {
-            m.state = m.max_steps > 0 ? TS_ACTIVE : TS_FINAL;
-            if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
-            tc_locate(S, m);
-        }
-        __syncwarp();
-        tc_phases(T, S, sl, lane, 3, 0.5 * m.dt);
     }
-    __syncwarp();
-    tc_publish(T, S, sl, lane);
 }
 
-// one warp per slot: sum the row-block partials of force, torque and diagnostics, then (lane 0,
-// FP64) the classical stage update (Eqs. 7-10), bookkeeping, stop rule and refill; the lanes
-// share the phase factors and spline values of the next stage
+// after the stage kernel of stage s: the row-tile partial sums of force, torque and diagnostics
+// (compensated FP32, FP64 once per slot), bookkeeping (stage 0), the classical stage update
+// (Eqs. 7-10), stop rule and refill, then the next stage's spline values, dPhi/dt and phase factors
 __global__ void __launch_bounds__(128) k_tc_slots(TcState T, int s, int n_rowblocks)
 {
     const DevSys &S = *T.sys;
-    const int lane = threadIdx.x & 31, sl = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (sl >= T.S) return;
-    TSlot &m = T.slot[sl];
-    if (m.state == TS_IDLE) return;  // published as idle when it became idle
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = lane; b < n_rowblocks; b += 32) {
-        const double *p = T.part + ((size_t)b * T.S + sl) * 6;
-        for (int q = 0; q < 6; ++q) acc[q] += p[q];
-    }
-    for (int o = 16; o; o >>= 1)
-        for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    int kind = 0;
-    double tph = 0.0;
-    if (lane == 0) {
-        const double F = acc[0], Tq = acc[1], V = acc[2], NR = acc[3], ER = acc[4], JY = acc[5];
-        if (m.state == TS_ACTIVE || m.state == TS_FINAL) {
-            const double R = m.qs[0], PR = m.qs[1], PP = m.qs[3], imu = m.inv_mu;
-            const double ir = 1.0 / R, ir2 = ir * ir;
-            if (s == 0) {
-                const double et = 0.5 * imu * (PR * PR + PP * PP * ir2) + ER + V;
-                const double jt = PP + 0.5 * JY;
-                if (m.steps == 0) { m.e0 = et; m.j0 = jt; }
-                m.ndev = fmax(m.ndev, fabs(NR - 1.0));
-                m.edev = fmax(m.edev, fabs(et - m.e0));
-                m.jdev = fmax(m.jdev, fabs(jt - m.j0));
-            }
-            if (m.state == TS_FINAL) {
-                if (s == 0) {
-                    if (T.diag) {
-                        mqct_diag d;
-                        d.steps = m.steps; d.status = m.status;
-                        d.norm_dev = m.ndev; d.energy_dev = m.edev; d.angmom_dev = m.jdev;
-                        d.t_final = m.steps * m.dt;
-                        T.diag[m.traj] = d;
-                    }
-                    if (T.t_done) T.t_done[m.traj] = mqct_clock_ns();
-                    tc_claim(T, S, sl);  // WAIT (column initialised at stage 3) or IDLE
+    const unsigned full = 0xffffffffu;
+    const SlotLane L = slot_lane(T);
+    TSlot &m = T.slot[L.slc];
+    int state = m.state;
+    if (__all_sync(full, !L.valid || state == TS_IDLE)) return;  // published as idle when they became idle
+    const size_t ci = (size_t)L.sc * T.S + L.slc;
+    double q = T.Q[ci], qs = T.QS[ci], lacc = T.LACC[ci];
+    auto comp = [&](double v, int c2) { return __shfl_sync(full, v, 8 * c2 + L.sj); };
+    // row-tile sums: lane c sums quantity c (F, T, V, |a|^2), lanes c < 2 also c + 4 (E|a|^2, <J_y>)
+    auto tsum = [&](int qq) {
+        float hi = 0.f, lo = 0.f;
+        for (int b = 0; b < n_rowblocks; ++b) {
+            const float2 p = T.part[((size_t)b * 6 + qq) * T.S + L.slc];
+            float e2;
+            two_sum(hi, p.x, hi, e2);
+            lo += e2 + p.y;
+        }
+        return (double)hi + (double)lo;
+    };
+    const double v1 = tsum(L.sc), v2 = (s == 0 && L.sc < 2) ? tsum(4 + L.sc) : 0.0;
+    const double F = comp(v1, 0), Tq = comp(v1, 1);
+    const bool act = L.valid && state == TS_ACTIVE;
+    int add_status = 0;
+    if (s == 0) {
+        // total energy, P_Phi + <J_y> and norm at the start of the step (or of the final state)
+        const double V = comp(v1, 2), NR = comp(v1, 3), ER = comp(v2, 0), JY = comp(v2, 1);
+        const double PR = comp(q, 1), PP = comp(q, 3);
+        const double et = 0.5 * (T.inv_mu * PR * PR + PP * PP * m.i2m) + ER + V;
+        const double jt = PP + 0.5 * JY;
+        const int st0 = m.steps;
+        const double e0 = st0 == 0 ? et : m.e0, j0 = st0 == 0 ? jt : m.j0;
+        const double nd = fmax(m.ndev, fabs(NR - 1.0)), ed = fmax(m.edev, fabs(et - e0)),
+                     jd = fmax(m.jdev, fabs(jt - j0));
+        __syncwarp();
+        if (L.valid && L.sc == 0 && (state == TS_ACTIVE || state == TS_FINAL)) {
+            m.e0 = e0; m.j0 = j0; m.ndev = nd; m.edev = ed; m.jdev = jd;
+        }
+        __syncwarp();
+        if (L.valid && state == TS_FINAL) {
+            if (L.sc == 0) {
+                if (T.diag) {
+                    mqct_diag d;
+                    d.steps = m.steps; d.status = m.status;
+                    d.norm_dev = m.ndev; d.energy_dev = m.edev; d.angmom_dev = m.jdev;
+                    d.t_final = m.steps * m.dt;
+                    T.diag[m.traj] = d;
                 }
-            } else {
-                const double l4[4] = {PR * imu, F + PP * PP * imu * ir2 * ir, m.phidot, Tq};
-                const double wg = (s == 1 || s == 2) ? 2.0 : 1.0;
-                for (int i = 0; i < 4; ++i) m.lacc[i] = s == 0 ? l4[i] : fma(wg, l4[i], m.lacc[i]);
-                if (s < 3) {
-                    const double bnd = s == 2 ? m.dt : 0.5 * m.dt;
-                    for (int i = 0; i < 4; ++i) m.qs[i] = fma(bnd, l4[i], m.q[i]);
-                } else {
-                    for (int i = 0; i < 4; ++i) { m.q[i] = fma(m.dt / 6.0, m.lacc[i], m.q[i]); m.qs[i] = m.q[i]; }
-                    m.steps += 1;
-                    const bool fin = isfinite(m.q[0]) && isfinite(m.q[1]) && isfinite(m.q[2]) && isfinite(m.q[3]);
-                    if (!fin) m.status |= MQCT_TRAJ_NONFINITE;
-                    if (!fin || (m.q[0] >= m.r_end && m.q[1] > 0.0)) m.state = TS_FINAL;
-                    else if (m.steps >= m.max_steps) { m.status |= MQCT_TRAJ_MAX_STEPS; m.state = TS_FINAL; }
-                }
-                if (!(m.status & MQCT_TRAJ_NONFINITE)) tc_locate(S, m);
-                // phase factors needed ahead: after stage 1 the integer time t + dt, after stage 3
-                // the half time of the next step
-                if (s == 1) { kind = 1; tph = m.steps * m.dt + m.dt; }
-                if (s == 3 && m.state == TS_ACTIVE) { kind = 2; tph = m.steps * m.dt + 0.5 * m.dt; }
+                if (T.t_done) T.t_done[m.traj] = mqct_clock_ns();
             }
-        } else if (m.state == TS_WAIT && s == 3) {
-            m.state = m.max_steps > 0 ? TS_ACTIVE : TS_FINAL;
-            if (m.max_steps <= 0) m.status |= MQCT_TRAJ_MAX_STEPS;
-            tc_locate(S, m);
-            kind = 3;
-            tph = 0.5 * m.dt;
+            __syncwarp(L.m4);
+            state = tc_claim(T, S, L, q);  // WAIT (column initialised at stage 3) or IDLE
+            qs = q;
+            lacc = 0.0;
         }
     }
+    {
+        // derivative l_c: (P_R / mu, F + P_Phi^2/(mu R^3), dPhi/dt, torque)
+        const double pr = comp(qs, 1), pp = comp(qs, 3);
+        const double t1 = pp * m.phid * m.ir;
+        const double X = L.sc == 0 ? pr : (L.sc == 1 ? F : (L.sc == 2 ? m.phid : Tq));
+        const double alpha = L.sc == 0 ? T.inv_mu : 1.0, beta = L.sc == 1 ? t1 : 0.0;
+        double qs2 = qs, lacc2 = lacc;
+        stage_component(s, alpha, X, beta, 0.5 * m.dt, m.dt, m.h6, q, qs2, lacc2);
+        if (act) { qs = qs2; lacc = lacc2; }
+    }
+    int steps = m.steps;
+    if (s == 3) {
+        const unsigned bad = __ballot_sync(full, act && !finite64(qs));
+        const double R = comp(qs, 0), PR = comp(qs, 1);
+        if (act) {
+            q = qs;
+            steps += 1;
+            if ((bad >> L.sj) & 0x01010101u) {
+                add_status |= MQCT_TRAJ_NONFINITE;
+                state = TS_FINAL;
+            } else if (ge_pos(R, m.r_end) && __double_as_longlong(PR) > 0) {
+                state = TS_FINAL;
+            } else if (steps >= m.max_steps) {
+                add_status |= MQCT_TRAJ_MAX_STEPS;
+                state = TS_FINAL;
+            }
+        }
+    }
+    const bool start = L.valid && state == TS_WAIT && s == 3;
+    const bool next = (act && !(add_status & MQCT_TRAJ_NONFINITE)) || start;
+    double ir = 0.1, i2m = 0.0, phid = 0.0;
+    const int trng = tc_next_stage(T, S, L, next ? qs : 10.0, next, ir, i2m, phid);
+    if (next) add_status |= trng;
+    if (start) {
+        const int ms = m.max_steps;
+        state = ms > 0 ? TS_ACTIVE : TS_FINAL;
+        if (ms <= 0) add_status |= MQCT_TRAJ_MAX_STEPS;
+    }
+    // phase factors needed ahead: after stage 1 the integer time t + dt, after stage 3 the half
+    // time of the next step; a slot that starts at the next stage 0 gets t = 0 and t = dt/2
+    if (start) {
+        tc_phases(T, S, L, T.PHb, 1u);
+        for (int l = L.sc; l < S.n_levels; l += 4) T.PHa[(size_t)l * T.S + L.sl] = make_float2(1.f, 0.f);
+    } else if (act && state == TS_ACTIVE && s == 1) {
+        tc_phases(T, S, L, T.PHa, 2u * steps + 2u);
+    } else if (act && state == TS_ACTIVE && s == 3) {
+        tc_phases(T, S, L, T.PHb, 2u * steps + 1u);
+    }
+    if (L.valid && state == TS_IDLE) tc_publish_idle(T, S, L);
     __syncwarp();
-    kind = __shfl_sync(0xffffffffu, kind, 0);
-    tph = __shfl_sync(0xffffffffu, tph, 0);
-    if (kind) tc_phases(T, S, sl, lane, kind, tph);
-    __syncwarp();
-    tc_publish(T, S, sl, lane);
-    if (lane == 0 && s == 3 && m.state != TS_IDLE) atomicAdd(T.live, 1);
+    if (L.valid) {
+        T.Q[ci] = q;
+        T.QS[ci] = qs;
+        T.LACC[ci] = lacc;
+        if (L.sc == 0) {
+            if (next) { m.ir = ir; m.i2m = i2m; m.phid = phid; }
+            m.status |= add_status;
+            m.steps = steps;
+            m.state = state;
+            T.state[L.sl] = state;
+            T.dtf[L.sl] = (float)m.dt;
+        }
+    }
+    if (s == 3) {
+        const unsigned live = __ballot_sync(full, L.valid && L.sc == 0 && state != TS_IDLE);
+        if ((threadIdx.x & 31) == 0 && live) atomicAdd(T.live, __popc(live));
+    }
+}
+
+// the condition of the graph's WHILE node at the end of a chunk of steps: run another chunk while
+// trajectories are live and no bounded wait has run out
+__global__ void k_tc_continue(TcState T, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x == 0) {
+        const int live = *((volatile int *)T.live), err = *((volatile int *)(T.live + 1));
+        cudaGraphSetConditional(h, live > 0 && !err ? 1u : 0u);
+    }
+}
+
+__global__ void k_tc_reset_live(TcState T)
+{
+    if (threadIdx.x == 0) T.live[0] = 0;
 }
 
 }  // namespace
@@ -665,6 +775,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     T.sys = a.sys; T.trajs = a.trajs; T.order = a.order; T.n = a.n; T.S = S; T.queue = a.queue;
     T.pop = a.pop; T.amp = a.amp; T.diag = a.diag; T.nmax = a.nmax; T.sys_idx = a.sys_idx;
     T.t_start = a.t_start; T.t_done = a.t_done;
+    T.inv_mu = 1.0 / h.mu;
     const size_t ns = (size_t)n * S;
     get((void **)&T.live, 2 * sizeof(int));
     get((void **)&T.C[0], sizeof(float2) * ns);
@@ -678,7 +789,11 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     get((void **)&T.state, sizeof(int) * S);
     get((void **)&T.PHa, sizeof(float2) * (size_t)h.n_levels * S);
     get((void **)&T.PHb, sizeof(float2) * (size_t)h.n_levels * S);
-    get((void **)&T.part, sizeof(double) * 6 * (size_t)n_rowblocks * S);
+    get((void **)&T.part, sizeof(float2) * 6 * (size_t)n_rowblocks * S);
+    get((void **)&T.inc, sizeof(unsigned long long) * (size_t)h.n_levels * S);
+    get((void **)&T.Q, sizeof(double) * 4 * (size_t)S);
+    get((void **)&T.QS, sizeof(double) * 4 * (size_t)S);
+    get((void **)&T.LACC, sizeof(double) * 4 * (size_t)S);
     get((void **)&T.slot, sizeof(TSlot) * (size_t)S);
     if (e != cudaSuccess) {
         cleanup();
@@ -690,44 +805,54 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         return cuda_fail(e, "cudaFuncSetAttribute");
     }
     cudaMemsetAsync(T.live, 0, 2 * sizeof(int), st);
-    k_tc_init<<<(S + 3) / 4, 128, 0, st>>>(T);
+    const int slot_blocks = (S / 8 + 3) / 4;  // four warps of eight slots per block
+    k_tc_init<<<slot_blocks, 128, 0, st>>>(T);
     const int n_ct = S / kTcSlotsPerTile;
-    // one chunk of steps, captured once as a graph
-    const int chunk = 16;
-    cudaGraph_t graph = nullptr;
+    // chunks of steps inside a WHILE node: the body (one chunk) ends with k_tc_continue, which
+    // sets the condition from the live-slot count; one launch of the graph runs every trajectory
+    const int chunk = 4;
+    cudaGraph_t graph = nullptr, body = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap;
-    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
-        cleanup();
-        return cuda_fail(e, "cudaStreamCreate");
-    }
-    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaStream_t cap = nullptr;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNode_t wnode;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(T.live, 0, sizeof(int), cap);
+        alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        k_tc_reset_live<<<1, 32, 0, cap>>>(T);
         for (int k = 0; k < chunk; ++k)
             for (int s = 0; s < 4; ++s) {
                 const int cur = s & 1;
                 k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, cap>>>(T, s, cur);
-                k_tc_slots<<<(S + 3) / 4, 128, 0, cap>>>(T, s, n_rowblocks);
+                k_tc_slots<<<slot_blocks, 128, 0, cap>>>(T, s, n_rowblocks);
             }
-        e = cudaStreamEndCapture(cap, &graph);
+        k_tc_continue<<<1, 32, 0, cap>>>(T, cond);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cap, &captured);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    int live[2] = {1, 0};
-    long long chunks = 0;
-    while (e == cudaSuccess && live[0] > 0 && !live[1]) {
-        e = cudaGraphLaunch(exec, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(live, T.live, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        ++chunks;
-    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    int live[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(live, T.live, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    cudaStreamDestroy(cap);
+    if (cap) cudaStreamDestroy(cap);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core path");
     if (live[1]) return fail(MQCT_ERR_TIMEOUT, "tensor-core path: a bounded MMA completion wait ran out");
-    (void)chunks;
     return MQCT_OK;
 }
 

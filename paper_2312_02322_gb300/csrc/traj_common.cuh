@@ -71,4 +71,36 @@ __device__ __forceinline__ double spline_fp64(const DevSys &S, int l, int k, dou
     return c.x + x * (c.y + x * (c.z + x * c.w));
 }
 
+// error-free sum of two FP32 numbers: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// comparisons that keep off the FP64 pipe: for a finite x >= 0 and y >= 0, x >= y compares the bit
+// patterns; a double is finite unless its exponent bits are all ones
+__device__ __forceinline__ bool ge_pos(double x, double y)
+{
+    return __double_as_longlong(x) >= __double_as_longlong(y);
+}
+__device__ __forceinline__ bool finite64(double x)
+{
+    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+// RK4 stage update of one classical component (Eqs. 7-10): derivative l = alpha X + beta,
+// accumulator (weights 1, 2, 2, 1), next stage input (s < 3: step hdt, hdt, dt) or the step update
+// (s = 3: q + dt/6 lacc).  A look-ahead that calls it with the same operands gets the same bits.
+__device__ __forceinline__ void stage_component(int s, double alpha, double X, double beta, double hdt, double dt,
+                                                double h6, double q, double &qs, double &lacc)
+{
+    const double l = fma(alpha, X, beta);
+    if (s == 0) lacc = l;
+    else lacc = fma((s == 1 || s == 2) ? 2.0 : 1.0, l, lacc);
+    if (s < 3) qs = fma(s == 2 ? dt : hdt, l, q);
+    else qs = fma(h6, lacc, q);
+}
+
 }  // namespace mqct
