@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--batch-shape", type=int, default=0,
                     help="FP32 batched kernel shape 1..7 for every system (see mqct_propagate_opts); implies "
                          "--no-autotune")
+    ap.add_argument("--no-rates", dest="rates", action="store_false",
+                    help="skip the post-processing (Eq. 20 and rate coefficients) timing")
     ap.add_argument("--no-n1600", dest="n1600", action="store_false",
                     help="skip the N = 1600 block (the metric's second basis size, timed after the headline)")
     ap.add_argument("--energy", type=float, default=0.0,
@@ -415,6 +417,30 @@ def adjoint_block(api, n_traj):
     return out
 
 
+def rates_block(api, n_levels=1032, reps=5):
+    """Post-processing at the paper's scale: Eq. 20 and the Maxwell-Boltzmann rates of both directions
+    of every pair of 1032 levels (the paper's count of non-degenerate channels) on its ten collision
+    energies, at five temperatures; cross sections resident on the device, timed with CUDA events."""
+    import torch
+
+    rs = W.rate_set(n_levels=n_levels)
+    sig = torch.from_numpy(rs.sigma).cuda()
+    api.rate_coefficients(sig, rs.u, rs.energy, rs.g, rs.mu, rs.kT)  # warm-up
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    ev[0].record(stream)
+    for _ in range(reps):
+        api.rate_coefficients(sig, rs.u, rs.energy, rs.g, rs.mu, rs.kT, stream=stream.cuda_stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    L, T = n_levels, len(rs.kT)
+    n_rates = L * L * T
+    return {"workload": f"{L} levels x {len(rs.u)} energies x {T} temperatures (synthetic cross sections)",
+            "ms": ms, "rate_coefficients_per_s": n_rates / (ms * 1e-3), "transitions": L * (L - 1) // 2}
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def gpu_arm(args):
     import torch
@@ -512,10 +538,13 @@ def gpu_arm(args):
                          torch.from_numpy(sub.group.astype(np.int32)).to(dev), sub.n_groups))
     one_sys = len(systems) == 1 and len(groups) == 1 and len(groups[0][1]) == ts.n
 
+    n_launch = [0]
+
     def sigma(pop_):
         for s_, rows_d, nn, w_d, g_d, ng in sig_args:
             pp = pop_ if one_sys else pop_.index_select(0, rows_d)[:, :nn].contiguous()
             api.cross_sections(s_, pp, w_d, g_d, ng, stream=stream)
+            n_launch[0] += api.last_launch_count()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     for _ in range(max(0, args.warmup - 1)):
@@ -526,11 +555,13 @@ def gpu_arm(args):
         dist.barrier()
     # events: step start, after the propagation call (dominant kernel), step end
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    n_launch[0] = 0  # only the timed steps
     with Clocks(local) as clk:
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
             pop, _, _ = api.propagate(systems, trd, want_diag=False, device=True, stream=stream, **tune)
+            n_launch[0] += api.last_launch_count()
             ev[k][1].record(stream)
             sigma(pop)
             ev[k][2].record(stream)
@@ -588,6 +619,7 @@ def gpu_arm(args):
     adj = None
     if args.adjoint:
         adj = adjoint_block(api, args.adjoint)
+    rates = rates_block(api) if args.rates else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -609,16 +641,6 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if rank != 0:
         return
-    # order keys, CUB radix sort passes, the propagation launch(es), level and group sums per system
-    launches_per_step = 3 + len(systems) + 2 * len(groups)
-    if args.precision == "bf16x3":
-        # the stage-synchronous path: graphs of 16 steps x 4 stages x (stage + slot kernel) per
-        # system, run until the longest trajectory ends, plus the slot initialisation
-        launches_per_step = 3 + 2 * len(groups)
-        for i in range(len(systems)):
-            rows = sidx == i
-            if rows.any():
-                launches_per_step += 1 + 128 * int(np.ceil((int(dg["steps"][rows].max()) + 1) / 16.0))
     sigma_sets = sum(sub.n_groups for _, _, sub in groups)
     cfg = {"workload": workload, "path": args.path, "precision": args.precision,
            "n_states": [inf["n_states"] for inf in infos] if len(infos) > 1 else infos[0]["n_states"],
@@ -632,10 +654,10 @@ def gpu_arm(args):
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[args.precision],
         "data": "synthetic", "config": cfg,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps, "latency": latency, "comparison": compare, "adjoint": adj,
+        "gpu_launches": n_launch[0], "latency": latency, "comparison": compare, "adjoint": adj,
         "sigma_sets_per_s": sigma_sets * ws / (ms * 1e-3 / args.steps),
         "sigma_set": "all cross sections out of one (collision energy, initial level) group",
-        "n1600": n1600,
+        "n1600": n1600, "rates": rates,
     }))
 
 

@@ -321,6 +321,49 @@ mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_t n_systems
 mqct_status mqct_cross_sections(mqct_system sys, const double *final_pop, const double *weight, const int32_t *group,
                                 int32_t n, int32_t n_groups, double *sigma_out, void *cuda_stream);
 
+/* Symmetrised cross sections and Maxwell-Boltzmann rate coefficients (Sec. III).
+ *
+ * Eq. 20, for every pair of levels (a, b) and every computed energy U_k:
+ *   sigma_sym[k][a][b] = ( g_a sigma[k][a][b] + g_b sigma[k][b][a] ) / 2,
+ * with sigma[k][a][b] = sigma_{a->b}(U_k) (bohr^2) and g the rotational degeneracy of Eq. 19
+ * (2j+1 for an atom + rotor).  sigma_sym is symmetric in (a, b).
+ *
+ * Rates of both directions of every pair (the paper defers the integration to its ref. [44];
+ * the readings taken here):
+ *   k_{a->b}(T) = (8/(pi mu))^(1/2) (kT)^(-3/2) exp(-(E_b - E_a)/(2 kT)) / g_a
+ *                 * integral_{u0}^inf sigma~_ab(U) U exp(-U/kT) dU,
+ * U being the mean of the incoming and outgoing translational energies, so that
+ * g_a k_{a->b} = g_b k_{b->a} exp(-(E_b - E_a)/kT) exactly.  sigma~_ab(U) is the natural cubic
+ * spline through (U_k, sigma_sym[k][a][b]) (negative values taken as zero); below U_1 it falls
+ * linearly to zero at the threshold u0 = |E_b - E_a|/2 (or the spline is cut at u0 when
+ * u0 >= U_1); above U_K it continues as sigma_sym[K-1] (U/U_K)^p, p the log-log slope of the
+ * last two points clipped to [-1, 0].  The finite pieces are integrated by Gauss-Legendre
+ * panels no wider than 4 kT (relative error below ~1e-13), the tail in closed form.
+ *
+ * sigma [K][L][L] (host or device); sigma_sym [K][L][L] output, or NULL to skip it;
+ * rate [n_temps][L][L] output, rate[t][a][b] = k_{a->b}(T_t) in bohr^3 per atomic unit of time
+ * (x 6.126e-9 for cm^3/s).  The descriptor's arrays are host memory.  Every pair of levels is
+ * processed: sigma must hold both directions of each pair whose rates are used.  Outputs in
+ * device memory are written asynchronously on `cuda_stream`; host outputs are complete when the
+ * call returns.  Errors: MQCT_ERR_INVALID_ARG (sizes, non-increasing or non-positive U, kT <= 0,
+ * g <= 0, mu <= 0, reserved != 0, device arrays in the descriptor), MQCT_ERR_OOM, MQCT_ERR_CUDA. */
+#define MQCT_RATE_MAX_ENERGIES 32
+#define MQCT_RATE_MAX_TEMPS 256
+typedef struct {
+    int32_t n_levels;            /* L >= 1                                                    */
+    int32_t n_energies;          /* K, 2 <= K <= MQCT_RATE_MAX_ENERGIES                       */
+    int32_t n_temps;             /* 1 <= n_temps <= MQCT_RATE_MAX_TEMPS                       */
+    int32_t reserved;            /* must be 0                                                 */
+    double mu;                   /* reduced mass (electron masses), > 0                       */
+    const double *u;             /* [K] U_k (hartree), 0 < U_1 < ... < U_K                    */
+    const double *kT;            /* [n_temps] k_B T (hartree), > 0                            */
+    const double *level_energy;  /* [L] E_l (hartree)                                         */
+    const double *degeneracy;    /* [L] g_l > 0                                               */
+} mqct_rate_desc;
+
+mqct_status mqct_rate_coefficients(const mqct_rate_desc *desc, const double *sigma, double *sigma_sym, double *rate,
+                                   void *cuda_stream);
+
 /* Vector-Jacobian product of the cross sections with respect to the P parameters whose
  * tables were given at create time:
  *   dL_dparam[p] = sum_{g,l''} dL_dsigma[g][l''] * d sigma[g][l''] / d theta_p,
@@ -341,6 +384,14 @@ mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int32_t n, con
 
 /* Thread-local message describing the last failure of a call on this thread. */
 const char *mqct_last_error(void);
+
+/* Number of this library's kernel launches made by the last mqct_propagate, mqct_propagate_ex,
+ * mqct_propagate_noalloc, mqct_cross_sections, mqct_adjoint or mqct_rate_coefficients call on
+ * this thread (reset at the start of each of these calls).  Kernels of a CUDA graph that the call
+ * runs are counted once per execution (the number of chunks a graph's loop ran is read back from
+ * the device); kernels of other libraries the call uses (CUB's sort and select) are not counted.
+ * Calls that return asynchronously have issued all their launches when they return. */
+int64_t mqct_last_launch_count(void);
 
 /* Library version string. */
 const char *mqct_version(void);

@@ -75,6 +75,16 @@ class PropagateOpts(C.Structure):
                 ("tc_slots", C.c_void_p)]
 
 
+class RateDesc(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_energies", C.c_int32), ("n_temps", C.c_int32), ("reserved", C.c_int32),
+                ("mu", C.c_double), ("u", C.c_void_p), ("kT", C.c_void_p), ("level_energy", C.c_void_p),
+                ("degeneracy", C.c_void_p)]
+
+
+# Boltzmann constant (hartree per kelvin) and bohr^3 per atomic unit of time in cm^3/s (CODATA 2018)
+KB_HARTREE_PER_K = 3.1668115634556e-6
+RATE_AU_TO_CM3_S = 0.529177210903e-8 ** 3 / 2.4188843265857e-17
+
 # (slots per CTA, threads) of the FP32 batched kernel for batch_shape = index + 1
 BATCH_SHAPES = [(32, 512), (16, 512), (8, 256), (8, 512), (4, 512), (16, 256), (4, 256)]
 
@@ -108,14 +118,17 @@ def lib():
             L.mqct_propagate_ex.argtypes = [C.POINTER(vp), i32, vp, i32, vp, vp, vp, C.POINTER(PropagateOpts), vp]
             L.mqct_cross_sections.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp]
             L.mqct_adjoint.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, vp]
+            L.mqct_rate_coefficients.argtypes = [C.POINTER(RateDesc), vp, vp, vp, vp]
             L.mqct_probe_fma_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
             L.mqct_probe_fma_rate.restype = C.c_int
             L.mqct_probe_op_latency.argtypes = [i32, i32, C.POINTER(C.c_double), vp]
             L.mqct_probe_op_latency.restype = C.c_int
             L.mqct_last_error.restype = C.c_char_p
+            L.mqct_last_launch_count.restype = C.c_int64
             L.mqct_version.restype = C.c_char_p
             for f in ("mqct_build_diatom", "mqct_build_asym_top", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
-                      "mqct_propagate", "mqct_propagate_ex", "mqct_cross_sections", "mqct_adjoint"):
+                      "mqct_propagate", "mqct_propagate_ex", "mqct_cross_sections", "mqct_adjoint",
+                      "mqct_rate_coefficients"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -358,6 +371,40 @@ def sigma_weights(ts: "_inputs.TrajSet", status=None) -> np.ndarray:
         bad = (np.asarray(status) & (TRAJ_MAX_STEPS | TRAJ_NONFINITE | TRAJ_INVALID | TRAJ_TIMEOUT)) != 0
         w = np.where(bad, 0.0, w)
     return w
+
+
+def last_launch_count() -> int:
+    """Kernel launches of the library made by the last propagate / cross-section / adjoint / rate call
+    on this thread (mqct_last_launch_count)."""
+    return int(lib().mqct_last_launch_count())
+
+
+def rate_coefficients(sigma, u, level_energy, degeneracy, mu: float, kT, sigma_sym: bool = True, stream=None):
+    """Eq. 20 and the Maxwell-Boltzmann rate coefficients of both directions of every pair of levels
+    (mqct_rate_coefficients).  sigma[k][a][b] = sigma_{a->b}(U_k) in bohr^2 (numpy or a CUDA tensor);
+    u [K], kT [n_T] in hartree; level_energy [L] (hartree), degeneracy [L].  Returns (sigma_sym or
+    None, rate) with rate[t][a][b] = k_{a->b}(T_t) in bohr^3 per atomic unit of time, on the
+    device of sigma."""
+    u = np.ascontiguousarray(u, np.float64)
+    kT = np.ascontiguousarray(np.atleast_1d(kT), np.float64)
+    E = np.ascontiguousarray(level_energy, np.float64)
+    g = np.ascontiguousarray(degeneracy, np.float64)
+    K, L = len(u), len(E)
+    if tuple(sigma.shape) != (K, L, L) or len(g) != L:
+        raise ValueError("sigma must be [K][L][L] with K energies and L levels")
+    if isinstance(sigma, np.ndarray):
+        sigma = np.ascontiguousarray(sigma, np.float64)
+        sym = np.zeros((K, L, L)) if sigma_sym else None
+        rate = np.zeros((len(kT), L, L))
+    else:
+        import torch
+
+        sigma = sigma.contiguous().to(torch.float64)
+        sym = torch.empty((K, L, L), dtype=torch.float64, device=sigma.device) if sigma_sym else None
+        rate = torch.empty((len(kT), L, L), dtype=torch.float64, device=sigma.device)
+    d = RateDesc(L, K, len(kT), 0, float(mu), u.ctypes.data, kT.ctypes.data, E.ctypes.data, g.ctypes.data)
+    _check(lib().mqct_rate_coefficients(C.byref(d), _ptr(sigma), _ptr(sym), _ptr(rate), _stream(stream)))
+    return sym, rate
 
 
 def adjoint(system: System, trajs: np.ndarray, weight, group, n_groups: int, dL_dsigma, ckpt: int = 64,

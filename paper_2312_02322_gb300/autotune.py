@@ -3,8 +3,9 @@
 The FP32 batched kernel exists in seven (slots per CTA, threads) instances and the BF16X3 path
 runs a chosen number of trajectories in flight; which is fastest depends on the basis size, the
 density of the coupling terms and the GPU.  ``tune`` times short probe runs of every candidate
-on a sample of the caller's trajectories, each capped at ``probe_steps`` RK4 steps so that a
-probe costs milliseconds, and returns the fastest option together with the measured table.
+on a sample of the caller's trajectories, each capped at ``probe_steps`` (E_min/E)^(1/2) RK4
+steps (in proportion to its expected length, so that the probe keeps the mix of long and short
+trajectories) so that a probe costs milliseconds, and returns the fastest option together with the measured table.
 The options change launch shapes only, never the arithmetic of a trajectory beyond the order
 of its FP32 partial sums.
 """
@@ -48,7 +49,8 @@ def candidates(system, n_traj: int) -> list[dict]:
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         nt = max(1, info["n_row_tiles"])
         top = min(8192, 64 * ((n_traj + 63) // 64))
-        out = sorted({min(top, 64 * max(1, (k * sms) // nt)) for k in (1, 2, 3, 4)})
+        # whole waves of (row tile, 64-slot tile) CTAs, and every trajectory in a slot at once
+        out = sorted({min(top, 64 * max(1, (k * sms) // nt)) for k in (1, 2)} | {top})
         return [{"tc_slots": s} for s in out]
     return [{}]
 
@@ -56,12 +58,16 @@ def candidates(system, n_traj: int) -> list[dict]:
 def tune(system, trajs: np.ndarray, probe_steps: int = 300, max_sample: int = 8192, repeats: int = 2,
          stream=None) -> dict:
     """Time every candidate option on a sample of `trajs` (TRAJ_DTYPE, all naming this system as
-    system 0) with each trajectory capped at probe_steps steps.  Returns
+    system 0) with each trajectory capped at probe_steps (E_min/E)^(1/2) steps.  Returns
     {"option": best options (keywords of api.propagate), "rate": traj-steps/s, "table": [...]}."""
     import torch
 
     tr = _sample(trajs, max_sample)
-    tr["max_steps"] = np.minimum(tr["max_steps"], probe_steps)
+    # caps in proportion to each trajectory's expected length (1/velocity ~ E^-1/2), so that the
+    # probe keeps the mix of long and short trajectories that decides how slots refill
+    e = np.maximum(tr["e_coll"], 1e-300)
+    cap = np.maximum(10, np.round(probe_steps * np.sqrt(e.min() / e))).astype(np.int32)
+    tr["max_steps"] = np.minimum(tr["max_steps"], cap)
     tr["system_idx"] = 0
     tr_dev = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
     _, _, dg = api.propagate(system, tr, want_pop=False, device=False)
@@ -87,7 +93,11 @@ def tune_joint(systems, trajs: np.ndarray, probe_steps: int = 300, max_sample: i
     import torch
 
     tr = _sample(trajs, max_sample)
-    tr["max_steps"] = np.minimum(tr["max_steps"], probe_steps)
+    # caps in proportion to each trajectory's expected length (1/velocity ~ E^-1/2), so that the
+    # probe keeps the mix of long and short trajectories that decides how slots refill
+    e = np.maximum(tr["e_coll"], 1e-300)
+    cap = np.maximum(10, np.round(probe_steps * np.sqrt(e.min() / e))).astype(np.int32)
+    tr["max_steps"] = np.minimum(tr["max_steps"], cap)
     tr_dev = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
     _, _, dg = api.propagate(systems, tr, want_pop=False, device=False)
     steps = float(dg["steps"].sum())

@@ -720,6 +720,7 @@ extern "C" mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int
                                     const int32_t *group, int32_t n_groups, const double *dL_dsigma, int32_t ckpt,
                                     double *dL_dparam, void *cuda_stream)
 {
+    reset_launches();
     if (!sys || n < 0 || n_groups < 0 || ckpt < 1 || !dL_dparam) return fail(MQCT_ERR_INVALID_ARG, "mqct_adjoint: bad argument");
     const DevSys &h = sys->s.h;
     if (h.P < 1 || !h.dvcoef) return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: the system has no parameter tables");
@@ -840,6 +841,7 @@ extern "C" mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int
     if (fp32) k_adjoint<float><<<grid, kAdjThreads, smem, st>>>(aa);
     else k_adjoint<double><<<grid, kAdjThreads, smem, st>>>(aa);
     k_sum_theta<<<(h.P + 63) / 64, 64, 0, st>>>(theta, n, h.P, out);
+    count_launches(2);
     if ((e = cudaGetLastError()) != cudaSuccess) { cleanup(); return cuda_fail(e, "adjoint kernels"); }
     std::vector<int> hst(n);
     e = cudaMemcpyAsync(dL_dparam, out, sizeof(double) * h.P, adj_is_dev(dL_dparam) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);

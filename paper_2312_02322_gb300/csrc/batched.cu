@@ -781,6 +781,7 @@ cudaError_t launch_batched(BatchMultiArgs a, const std::vector<const DevSys *> &
     const int grid = std::max(1, std::min(sms * per_sm, (a.n + minb - 1) / minb));
     if (exact) k_batched_f32<BMAX, T, kUpt, true><<<grid, T, smem, st>>>(a);
     else k_batched_f32<BMAX, T, kUpt, false><<<grid, T, smem, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -160,6 +160,9 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
 
 mqct_status fail(mqct_status st, const std::string &msg);
 mqct_status cuda_fail(cudaError_t e, const char *what);
+// launches of this library's kernels made by the current C-ABI call on this thread
+void reset_launches();
+void count_launches(long long n);
 
 // host helpers of the built-in system builders (diatom.cpp)
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);

@@ -118,6 +118,7 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
                                               int32_t n, double *final_pop, double *final_amp, mqct_diag *diag,
                                               void *cuda_stream)
 {
+    reset_launches();
     if (!systems || n_systems < 1) return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate_noalloc: no systems");
     if (n_systems > kNoallocMaxSystems)
         return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate_noalloc: more than 16 systems (size of its static scratch)");
@@ -149,6 +150,7 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
     NoallocViews views;
     for (int i = 0; i < n_systems; ++i) views.v[i] = systems[i]->s.h;
     k_noalloc_setup<<<1, 32, 0, st>>>(views, n_systems, dsys, queue);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_noalloc_setup launch");
 
     const int maxw = kPropThreads / 32;
@@ -167,6 +169,7 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
     pa.sys = dsys; pa.trajs = trajs; pa.order = nullptr; pa.n = n; pa.n_systems = n_systems; pa.queue = queue;
     pa.pop = final_pop; pa.amp = final_amp; pa.diag = diag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
     k_propagate_fp64<<<std::min(n, sms * per_sm), threads, smem, st>>>(pa);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");
     return MQCT_OK;
 }

@@ -479,6 +479,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
                                          int32_t n, double *final_pop, double *final_amp, mqct_diag *diag,
                                          const mqct_propagate_opts *opts, void *cuda_stream)
 {
+    reset_launches();
     const mqct_propagate_opts no_opts{};
     const mqct_propagate_opts &op = opts ? *opts : no_opts;
     auto shape_of = [&](int i) { return op.batch_shape ? op.batch_shape[i] : 0; };
@@ -570,6 +571,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
         (e = sa.get((void **)&queue, sizeof(int))) != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync");
     k_order_keys<<<(n + 255) / 256, 256, 0, st>>>(dsys, n_systems, dtr, n, keys, idx);
+    count_launches(1);
     size_t tmp_bytes = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, order, n, 0, 32, st);
     void *tmp = nullptr;
@@ -592,6 +594,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
             cudaMemsetAsync(queues, 0, sizeof(int) * n_systems, st);
             cudaMemsetAsync(work, 0, sizeof(double) * n_systems, st);
             k_system_work<<<(n + 255) / 256, 256, 0, st>>>(dtr, order, keys2, n, n_systems, work);
+            count_launches(1);
             size_t sel_bytes = 0;
             cub::DeviceSelect::If(nullptr, sel_bytes, order, lists, counts, n, IsSystem{dtr, 0}, st);
             void *sel_tmp = nullptr;
@@ -663,6 +666,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
     pa.pop = dpop; pa.amp = damp; pa.diag = ddiag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
     pa.t_start = dts; pa.t_done = dtd;
     k_propagate_fp64<<<grid, threads, smem, st>>>(pa);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");
     }
 

@@ -23,7 +23,11 @@ namespace mqct {
 
 namespace {
 thread_local std::string g_err;
+thread_local long long g_launches = 0;
 }
+
+void reset_launches() { g_launches = 0; }
+void count_launches(long long n) { g_launches += n; }
 
 void set_error(const std::string &msg) { g_err = msg; }
 const char *last_error_cstr() { return g_err.c_str(); }
@@ -531,5 +535,7 @@ extern "C" mqct_status mqct_system_info(mqct_system sys, mqct_system_info_t *out
 }
 
 extern "C" const char *mqct_last_error(void) { return last_error_cstr(); }
+
+extern "C" int64_t mqct_last_launch_count(void) { return g_launches; }
 
 extern "C" const char *mqct_version(void) { return "mqct-gb300 0.1 (sm_103a)"; }

@@ -734,6 +734,7 @@ __global__ void k_tc_continue(TcState T, cudaGraphConditionalHandle h)
 {
     if (threadIdx.x == 0) {
         const int live = *((volatile int *)T.live), err = *((volatile int *)(T.live + 1));
+        T.live[2] += 1;  // chunks run (launch accounting)
         cudaGraphSetConditional(h, live > 0 && !err ? 1u : 0u);
     }
 }
@@ -748,16 +749,23 @@ __global__ void k_tc_reset_live(TcState T)
 mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
 {
     const int n = h.n;
-    // slot count: the contraction runs one CTA per SM per (row tile, 64-slot tile), so the slots
-    // fill whole waves -- one wave when the trajectories fit in it, else two (more slots only
-    // lengthen the tail of uneven trajectories); a.tc_slots overrides (rounded up to 64)
+    // slot count: the contraction runs one CTA per SM per (row tile, 64-slot tile), and a stage
+    // lasts about one CTA time per wave of CTAs, so the count of 64-slot tiles c maximises the
+    // trajectories in flight per wave, min(want, c) / ceil(c * row tiles / SMs), over c up to two
+    // full waves (the largest c among equals; trajectories beyond the slots wait for a refill);
+    // a.tc_slots overrides (rounded up to 64)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nt = std::max(1, h.n_tiles);
-    const int one_wave = std::max(1, sms / nt), two_waves = std::max(1, 2 * sms / nt);
+    const int two_waves = std::max(1, 2 * sms / nt);
     const int want = (a.n + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
-    int n_slot_tiles = want <= one_wave ? want : std::min(want, two_waves);
+    int n_slot_tiles = 1;
+    double best = 0.0;
+    for (int c = 1; c <= std::max(1, std::min(want, two_waves)); ++c) {
+        const double waves = std::ceil((double)c * nt / sms), rate = std::min(want, c) / waves;
+        if (rate >= best) { best = rate; n_slot_tiles = c; }
+    }
     if (a.tc_slots > 0) n_slot_tiles = (a.tc_slots + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
     n_slot_tiles = std::max(1, std::min(n_slot_tiles, 8192 / kTcSlotsPerTile));
     const int S = n_slot_tiles * kTcSlotsPerTile;
@@ -777,7 +785,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     T.t_start = a.t_start; T.t_done = a.t_done;
     T.inv_mu = 1.0 / h.mu;
     const size_t ns = (size_t)n * S;
-    get((void **)&T.live, 2 * sizeof(int));
+    get((void **)&T.live, 4 * sizeof(int));
     get((void **)&T.C[0], sizeof(float2) * ns);
     get((void **)&T.C[1], sizeof(float2) * ns);
     get((void **)&T.A, sizeof(float2) * ns);
@@ -804,7 +812,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         cleanup();
         return cuda_fail(e, "cudaFuncSetAttribute");
     }
-    cudaMemsetAsync(T.live, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(T.live, 0, 4 * sizeof(int), st);
     const int slot_blocks = (S / 8 + 3) / 4;  // four warps of eight slots per block
     k_tc_init<<<slot_blocks, 128, 0, st>>>(T);
     const int n_ct = S / kTcSlotsPerTile;
@@ -844,14 +852,16 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
-    int live[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(live, T.live, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    int live[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(live, T.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core path");
+    // k_tc_init, then per chunk: reset, chunk x 4 x (stage, slots), continue
+    count_launches(1 + (long long)live[2] * (2 + 8 * chunk));
     if (live[1]) return fail(MQCT_ERR_TIMEOUT, "tensor-core path: a bounded MMA completion wait ran out");
     return MQCT_OK;
 }

@@ -65,6 +65,7 @@ extern "C" mqct_status mqct_cross_sections(mqct_system sys, const double *final_
                                            const int32_t *group, int32_t n, int32_t n_groups, double *sigma_out,
                                            void *cuda_stream)
 {
+    reset_launches();
     if (!sys || !sigma_out) return fail(MQCT_ERR_INVALID_ARG, "mqct_cross_sections: NULL argument");
     if (n < 0 || n_groups < 0) return fail(MQCT_ERR_INVALID_ARG, "mqct_cross_sections: negative size");
     if (n > 0 && (!final_pop || !weight || !group)) return fail(MQCT_ERR_INVALID_ARG, "mqct_cross_sections: NULL input");
@@ -128,6 +129,7 @@ extern "C" mqct_status mqct_cross_sections(mqct_system sys, const double *final_
         k_level_sums<<<blocks, threads, smem, st>>>(sys->s.d, dpop, dw, n, Q);
     }
     k_group_sums<<<(n_groups * NL + 127) / 128, 128, 0, st>>>(Q, dg, n, n_groups, NL, dsig);
+    count_launches(n > 0 ? 2 : 1);
     if ((e = cudaGetLastError()) != cudaSuccess) { cleanup(); return cuda_fail(e, "cross-section kernels"); }
     if (host_out) {
         if ((e = cudaMemcpyAsync(sigma_out, dsig, sizeof(double) * (size_t)n_groups * NL, cudaMemcpyDeviceToHost, st)) != cudaSuccess) {

@@ -255,3 +255,43 @@ def small_workload(jmax=3, n_b=6, energies=(500.0,), init_js=(0, 1), b_max=8.0, 
     """A reduced diatom case that the oracle finishes in seconds (used by parity tests)."""
     return (diatom_pes_params(jmax=jmax, n_grid=n_grid),
             regular_set(list(energies), list(init_js), n_b=n_b, b_max=b_max, m_avg=m_avg))
+
+
+# the ten collision energies U of the paper's production run (Sec. III), cm^-1
+PAPER_ENERGIES_CM = (20.00, 41.28, 84.00, 170.47, 346.41, 703.89, 1430.0, 2906.3, 5906.0, 12000.0)
+
+
+@dataclass
+class RateSet:
+    u: np.ndarray           # [K] collision energies (hartree)
+    energy: np.ndarray      # [L] level energies (hartree)
+    g: np.ndarray           # [L] degeneracies
+    sigma: np.ndarray       # [K][L][L] sigma_{a->b}(U_k) (bohr^2)
+    kT: np.ndarray          # [T] k_B T (hartree)
+    mu: float               # reduced mass (electron masses)
+
+
+def rate_set(n_levels=30, temps_k=(10.0, 50.0, 100.0, 300.0, 1000.0), emax_cm=8000.0, mu_amu=1.8,
+             mismatch=0.3, seed=DEFAULT_SEED) -> RateSet:
+    """Synthetic state-to-state cross sections on the paper's ten energies: levels with energies
+    uniform on [0, emax] cm^-1 (sorted; the first at 0) and degeneracies 2j+1, j uniform on 0..28;
+    sigma_{a->b}(U) = s0 exp(-|dE| / 300 cm^-1) U / (U + |dE|) / g_a, s0 log-uniform on 0.1-30 bohr^2
+    per pair (so that Eq. 19 holds before the perturbation), times an independent factor
+    1 + mismatch * r, r uniform on [-1, 1], per direction and energy (the scatter of Fig. 1);
+    elastic sigma_{a->a} = 50 bohr^2 / (1 + U / 1000 cm^-1).  kB = 3.1668115634556e-6 hartree/K."""
+    rng = np.random.default_rng(seed)
+    L = n_levels
+    E = np.sort(rng.uniform(0.0, emax_cm, L))
+    E[0] = 0.0
+    j = rng.integers(0, 29, L)
+    g = (2 * j + 1).astype(np.float64)
+    U = np.asarray(PAPER_ENERGIES_CM, np.float64)
+    dE = np.abs(E[None, :] - E[:, None])
+    s0 = np.exp(rng.uniform(np.log(0.1), np.log(30.0), (L, L)))
+    s0 = np.sqrt(s0 * s0.T)
+    base = s0[None] * np.exp(-dE / 300.0)[None] * (U[:, None, None] / (U[:, None, None] + dE[None])) / g[None, :, None]
+    sig = base * (1.0 + mismatch * rng.uniform(-1.0, 1.0, base.shape))
+    for a in range(L):
+        sig[:, a, a] = 50.0 / (1.0 + U / 1000.0)
+    kT = np.asarray(temps_k, np.float64) * 3.1668115634556e-6
+    return RateSet(u=cm(U), energy=cm(E), g=g, sigma=sig, kT=kT, mu=float(mu_amu * AMU_ME))

@@ -111,3 +111,26 @@ def test_autotune_picks_a_valid_shape(mq, prec):
     pop_a, _, _ = mq.propagate(s, tr, device=False)
     pop_t, _, _ = mq.propagate(s, tr, device=False, **r["option"])
     assert np.max(np.abs(pop_a - pop_t)) < 1e-5  # shapes change only the order of FP32 partial sums
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_launch_count(mq, prec):
+    """mqct_last_launch_count: order keys + the persistent launch (FP64); order keys, the per-system
+    work estimate and one persistent launch (FP32, three systems); order keys, the work estimate and
+    per system the slot initialisation and 34 launches per graph chunk of four steps (BF16X3); the
+    cross-section call launches two kernels."""
+    ps, ts = mix(n_per=4)
+    systems = [mq.System.diatom(p, path="factorised", precision=prec) for p in ps]
+    tr = mq.make_trajs(ts, systems)
+    pop, _, dg = mq.propagate(systems, tr, device=False)
+    c = mq.last_launch_count()
+    if prec == "fp64":
+        assert c == 2
+    elif prec == "fp32":
+        assert c == 3
+    else:
+        assert c > 5 + 3 * 34 and (c - 5) % 34 == 0
+    rows = np.flatnonzero(ts.system == 0)
+    mq.cross_sections(systems[0], np.ascontiguousarray(pop[rows, :systems[0].n]), np.ones(rows.size),
+                      np.zeros(rows.size, np.int32), 1)
+    assert mq.last_launch_count() == 2
