@@ -69,7 +69,11 @@ typedef enum {
 typedef enum { MQCT_PATH_PLAIN = 0, MQCT_PATH_FACTORISED = 1 } mqct_path;
 
 /* Precision of the amplitudes and of the coupling contraction.  Phase arguments E_n t,
- * the classical variables and the conserved-quantity bookkeeping are FP64 in every mode. */
+ * the classical variables and the conserved-quantity bookkeeping are FP64 in every mode.
+ * MQCT_BF16X3 runs the stage-synchronous tensor-core path: one CUDA graph with a conditional
+ * loop runs every trajectory; with the environment variable MQCT_TC_HOST_LOOP=1 the same
+ * kernels are launched from a host loop instead (for profilers that do not follow
+ * conditional graph nodes; same arithmetic). */
 typedef enum { MQCT_FP64 = 0, MQCT_FP32 = 1, MQCT_BF16X3 = 2 } mqct_precision;
 
 /* per-trajectory status bits (mqct_diag.status) */

@@ -55,6 +55,9 @@ class _Desc(C.Structure):
         ("energy", C.c_void_p), ("level", C.c_void_p), ("jq", C.c_void_p), ("mq", C.c_void_p),
         ("G", C.c_void_p), ("v", C.c_void_p), ("dv_ends", C.c_void_p),
         ("n_params", C.c_int), ("dvp", C.c_void_p), ("dvp_ends", C.c_void_p),
+        ("grid_log", C.c_int), ("trunc_thr", C.c_double), ("trunc_r", C.c_double * 2),
+        ("g_nnz", C.c_longlong), ("g_term", C.c_void_p), ("g_row", C.c_void_p), ("g_col", C.c_void_p),
+        ("g_val", C.c_void_p),
     ]
 
 
@@ -83,6 +86,10 @@ def lib():
             L.ora_num_threads.restype = C.c_int
             L.ora_asym_levels.restype = C.c_int
             L.ora_asym_basis.restype = C.c_int
+            L.ora_sys_terms.restype = C.c_int
+            L.ora_sys_kept.restype = C.c_int
+            L.ora_diatom_G_triplets.restype = C.c_longlong
+            L.ora_diatom_G_triplets.argtypes = [C.c_int, C.c_int, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -104,26 +111,37 @@ class System:
     """Atom + rigid-rotor system in the oracle's own representation (atomic units).
 
     energy[n], level[n], jq[n], mq[n] label the states (jq < 0 disables the Coriolis
-    term for that state); G[L][n][n] are the angular coupling matrices of Eq. 12;
-    v[L][n_grid] and dv_ends[L][2] define the clamped splines of v_lambda(R).
+    term for that state); G[L][n][n] are the angular coupling matrices of Eq. 12, or, for
+    large bases, a tuple of triplet arrays (term, row, col, value) with n_terms L;
+    v[L][n_grid] and dv_ends[L][2] (dv/dR) define the clamped splines of v_lambda(R) --
+    in ln R on a logarithmic grid when grid_log (Sec. III).  trunc = (threshold, R_a, R_b)
+    drops every M_rc with |M_rc| <= threshold at both R_a and R_b (Sec. III).
     """
 
-    def __init__(self, energy, level, jq, mq, G, v, dv_ends, mu, r_min, r_max, dvp=None, dvp_ends=None):
+    def __init__(self, energy, level, jq, mq, G, v, dv_ends, mu, r_min, r_max, dvp=None, dvp_ends=None,
+                 grid_log=False, trunc=None, n_terms=None):
         self.energy = np.ascontiguousarray(energy, np.float64)
         self.level = np.ascontiguousarray(level, np.int32)
         self.jq = np.ascontiguousarray(jq, np.int32)
         self.mq = np.ascontiguousarray(mq, np.int32)
-        self.G = np.ascontiguousarray(G, np.float64)
+        if isinstance(G, tuple):
+            self.G = None
+            self.trip = tuple(np.ascontiguousarray(a, t) for a, t in zip(G, (np.int32, np.int32, np.int32, np.float64)))
+        else:
+            self.G = np.ascontiguousarray(G, np.float64)
+            self.trip = None
         self.v = np.ascontiguousarray(v, np.float64)
         self.dv_ends = np.ascontiguousarray(dv_ends, np.float64)
         self.mu, self.r_min, self.r_max = float(mu), float(r_min), float(r_max)
         self.n = self.energy.shape[0]
-        self.L = self.G.shape[0]
+        self.L = self.G.shape[0] if self.G is not None else int(n_terms if n_terms is not None else self.v.shape[0])
+        self.grid_log = bool(grid_log)
+        self.trunc = None if trunc is None else tuple(float(x) for x in trunc)
         self.n_grid = self.v.shape[1]
         self.n_levels = int(self.level.max()) + 1
         self.dvp = None if dvp is None else np.ascontiguousarray(dvp, np.float64)
         self.dvp_ends = None if dvp_ends is None else np.ascontiguousarray(dvp_ends, np.float64)
-        assert self.G.shape == (self.L, self.n, self.n)
+        assert self.G is None or self.G.shape == (self.L, self.n, self.n)
         assert self.v.shape == (self.L, self.n_grid) and self.dv_ends.shape == (self.L, 2)
 
     def _desc(self):
@@ -131,7 +149,15 @@ class System:
         d.n, d.n_terms, d.n_grid = self.n, self.L, self.n_grid
         d.mu, d.r_min, d.r_max = self.mu, self.r_min, self.r_max
         d.energy, d.level, d.jq, d.mq = _p(self.energy), _p(self.level), _p(self.jq), _p(self.mq)
-        d.G, d.v, d.dv_ends = _p(self.G), _p(self.v), _p(self.dv_ends)
+        d.G = _p(self.G) if self.G is not None else None
+        d.v, d.dv_ends = _p(self.v), _p(self.dv_ends)
+        if self.trip is not None:
+            d.g_nnz = self.trip[0].shape[0]
+            d.g_term, d.g_row, d.g_col, d.g_val = (_p(a) for a in self.trip)
+        d.grid_log = 1 if self.grid_log else 0
+        if self.trunc is not None:
+            d.trunc_thr = self.trunc[0]
+            d.trunc_r[0], d.trunc_r[1] = self.trunc[1], self.trunc[2]
         if self.dvp is not None:
             d.n_params = self.dvp.shape[0]
             d.dvp, d.dvp_ends = _p(self.dvp), _p(self.dvp_ends)
@@ -154,9 +180,40 @@ def diatom_G(jmax: int, lam: int) -> np.ndarray:
     return G
 
 
-def diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params=False):
-    """Grid tables of v_l(R) = A_l exp(-beta_l R) (+ damped -C6 R^-6 on term 0), end slopes and,
-    with with_params, their derivatives with respect to (A_0.., beta_0..)."""
+def sys_terms(sys: System, R):
+    """v_lambda(R), dv/dR, d2v/dR2 from the system's splines: arrays [len(R)][L]."""
+    R = np.ascontiguousarray(np.atleast_1d(R), np.float64)
+    out = [np.zeros((R.size, sys.L)) for _ in range(3)]
+    d = sys._desc()
+    st = lib().ora_sys_terms(C.byref(d), C.c_int(R.size), _p(R), *(_p(o) for o in out))
+    assert st == 0, st
+    return tuple(out)
+
+
+def sys_kept(sys: System) -> np.ndarray:
+    """The truncation's keep mask [n][n] (1: M_rc retained; 0 also between different m)."""
+    keep = np.zeros((sys.n, sys.n), np.uint8)
+    d = sys._desc()
+    st = lib().ora_sys_kept(C.byref(d), _p(keep))
+    assert st == 0, st
+    return keep.astype(bool)
+
+
+def diatom_G_triplets(jmax: int, lam: int):
+    """The non-zero <j'' m | P_lambda | j' m> (Eq. 15) as (row, col, value) arrays."""
+    n = lib().ora_diatom_n(jmax)
+    cap = n * (2 * lam + 1) + 16
+    row, col = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    val = np.zeros(cap)
+    k = lib().ora_diatom_G_triplets(jmax, lam, cap, _p(row), _p(col), _p(val))
+    assert k >= 0
+    return row[:k], col[:k], val[:k]
+
+
+def diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params=False, grid_log=False):
+    """Grid tables of v_l(R) = A_l exp(-beta_l R) (+ damped -C6 R^-6 on term 0), end slopes dv/dR
+    and, with with_params, their derivatives with respect to (A_0.., beta_0..); grid uniform in R,
+    or in ln R with grid_log."""
     A = np.ascontiguousarray(A, np.float64)
     beta = np.ascontiguousarray(beta, np.float64)
     L = A.shape[0]
@@ -164,19 +221,30 @@ def diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params=False):
     ends = np.zeros((L, 2))
     dvp = np.zeros((2 * L, L, n_grid)) if with_params else None
     dvpe = np.zeros((2 * L, L, 2)) if with_params else None
-    lib().ora_diatom_pes(C.c_int(L), _p(A), _p(beta), C.c_double(c6), C.c_double(rd), C.c_int(n_grid),
-                         C.c_double(r_min), C.c_double(r_max), _p(v), _p(ends),
-                         _p(dvp) if with_params else None, _p(dvpe) if with_params else None)
+    lib().ora_diatom_pes_grid(C.c_int(L), _p(A), _p(beta), C.c_double(c6), C.c_double(rd), C.c_int(n_grid),
+                              C.c_double(r_min), C.c_double(r_max), C.c_int(1 if grid_log else 0), _p(v), _p(ends),
+                              _p(dvp) if with_params else None, _p(dvpe) if with_params else None)
     return v, ends, dvp, dvpe
 
 
-def diatom_system(jmax, bconst, mu, A, beta, c6, rd, n_grid, r_min, r_max, with_params=False) -> System:
-    """Atom + linear rotor (Eq. 2 basis, Eq. 15 coupling, PES of the form used in the tests)."""
+def diatom_system(jmax, bconst, mu, A, beta, c6, rd, n_grid, r_min, r_max, with_params=False, grid_log=False,
+                  trunc=None, sparse=None) -> System:
+    """Atom + linear rotor (Eq. 2 basis, Eq. 15 coupling, PES of the form used in the tests);
+    sparse (default: N > 2000) passes G as triplets."""
     e, lev, jq, mq = diatom_basis(jmax, bconst)
     L = len(A)
-    G = np.stack([diatom_G(jmax, l) for l in range(L)])
-    v, ends, dvp, dvpe = diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params)
-    return System(e, lev, jq, mq, G, v, ends, mu, r_min, r_max, dvp, dvpe)
+    if sparse is None:
+        sparse = e.shape[0] > 2000
+    if sparse:
+        parts = [diatom_G_triplets(jmax, l) for l in range(L)]
+        G = (np.concatenate([np.full(p[0].shape[0], l, np.int32) for l, p in enumerate(parts)]),
+             np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+             np.concatenate([p[2] for p in parts]))
+    else:
+        G = np.stack([diatom_G(jmax, l) for l in range(L)])
+    v, ends, dvp, dvpe = diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params, grid_log)
+    return System(e, lev, jq, mq, G, v, ends, mu, r_min, r_max, dvp, dvpe, grid_log=grid_log, trunc=trunc,
+                  n_terms=L)
 
 
 def asym_levels(J: int, A: float, B: float, Cc: float):

@@ -33,7 +33,11 @@
  *     P_R = -sqrt(2 mu (E - M_s0s0(R0)) - P_Phi^2 / R0^2).
  *   - Spline: clamped cubic on a uniform grid with given end slopes; outside the
  *     grid the first / last cubic is extrapolated.  Interval k = floor((R-r_min)/h)
- *     clamped to [0, n_grid-2], x = R - (r_min + k h).
+ *     clamped to [0, n_grid-2], x = R - (r_min + k h).  On the logarithmic grid of
+ *     Sec. III the spline is the clamped cubic in ln R on its uniform grid (end slopes
+ *     R dv/dR), R-derivatives by the chain rule.
+ *   - Truncation (Sec. III): an element M_rc is dropped for the whole propagation when
+ *     |M_rc(R)| <= threshold at both reference distances, M from the splines.
  *   - Time stepping: classical 4-stage RK4 with fixed dt, stage times
  *     n dt, n dt + dt/2, n dt + dt/2, (n+1) dt.  A trajectory stops after the
  *     first step that ends with R >= r_end and P_R > 0, or after max_steps.
@@ -141,13 +145,20 @@ void ora_diatom_G(int jmax, int lam, double *G)
  * Outputs v[L][n_grid], dv_ends[L][2] (analytic dv/dR at both ends) and, if
  * dvp != NULL, the derivatives with respect to theta = (A_0..A_{L-1}, beta_0..beta_{L-1}):
  * dvp[2L][L][n_grid], dvp_ends[2L][L][2]. */
-void ora_diatom_pes(int L, const double *A, const double *beta, double c6, double rd, int n_grid,
-                    double r_min, double r_max, double *v, double *dv_ends, double *dvp, double *dvp_ends)
+/* grid point k: uniform in R, or (grid_log) uniform in ln R (Sec. III: logarithmic spacing) */
+static double grid_r(int grid_log, int n_grid, double r_min, double r_max, int k)
 {
-    double h = (r_max - r_min) / (n_grid - 1);
+    if (grid_log) return r_min * exp(k * (log(r_max) - log(r_min)) / (n_grid - 1));
+    return r_min + k * (r_max - r_min) / (n_grid - 1);
+}
+
+void ora_diatom_pes_grid(int L, const double *A, const double *beta, double c6, double rd, int n_grid,
+                         double r_min, double r_max, int grid_log, double *v, double *dv_ends, double *dvp,
+                         double *dvp_ends)
+{
     for (int l = 0; l < L; ++l) {
         for (int k = 0; k < n_grid; ++k) {
-            double R = r_min + k * h;
+            double R = grid_r(grid_log, n_grid, r_min, r_max, k);
             double val = A[l] * exp(-beta[l] * R);
             if (l == 0) val -= c6 * pow(R, -6.0) * (1.0 - exp(-pow(R / rd, 6.0)));
             v[l * n_grid + k] = val;
@@ -169,7 +180,7 @@ void ora_diatom_pes(int L, const double *A, const double *beta, double c6, doubl
         double *pa = dvp + ((size_t)l * L + l) * n_grid;        /* d v_l / d A_l    */
         double *pb = dvp + ((size_t)(L + l) * L + l) * n_grid;  /* d v_l / d beta_l */
         for (int k = 0; k < n_grid; ++k) {
-            double R = r_min + k * h;
+            double R = grid_r(grid_log, n_grid, r_min, r_max, k);
             pa[k] = exp(-beta[l] * R);
             pb[k] = -R * A[l] * exp(-beta[l] * R);
         }
@@ -180,6 +191,37 @@ void ora_diatom_pes(int L, const double *A, const double *beta, double c6, doubl
             dvp_ends[((size_t)(L + l) * L + l) * 2 + e] = -A[l] * ex + beta[l] * R * A[l] * ex;
         }
     }
+}
+
+void ora_diatom_pes(int L, const double *A, const double *beta, double c6, double rd, int n_grid,
+                    double r_min, double r_max, double *v, double *dv_ends, double *dvp, double *dvp_ends)
+{
+    ora_diatom_pes_grid(L, A, beta, c6, rd, n_grid, r_min, r_max, 0, v, dv_ends, dvp, dvp_ends);
+}
+
+/* G^lambda of the linear rotor (Eq. 15) as triplets (row, col, value) of the non-zero
+ * entries, for bases too large for a dense N x N array; returns the count written (at most
+ * cap) or -1 if cap is too small. */
+long long ora_diatom_G_triplets(int jmax, int lam, long long cap, int *row, int *col, double *val)
+{
+    long long k = 0;
+    for (int j2 = 0; j2 <= jmax; ++j2)
+        for (int j1 = 0; j1 <= jmax; ++j1) {
+            double c0 = ora_cg(j1, 0, lam, 0, j2, 0);
+            if (c0 == 0.0) continue;
+            double f = sqrt((2.0 * j1 + 1.0) / (2.0 * j2 + 1.0)) * c0;
+            int mm = j1 < j2 ? j1 : j2;
+            for (int m = -mm; m <= mm; ++m) {
+                double g = f * ora_cg(j1, m, lam, 0, j2, m);
+                if (g == 0.0) continue;
+                if (k >= cap) return -1;
+                row[k] = j2 * j2 + (m + j2);
+                col[k] = j1 * j1 + (m + j1);
+                val[k] = g;
+                ++k;
+            }
+        }
+    return k;
 }
 
 /* ------------------------------------------------------------------ */
@@ -259,6 +301,16 @@ typedef struct {
     int n_params;          /* derivative tables for ora_tangent (0 if unused) */
     const double *dvp;     /* [P][L][n_grid] */
     const double *dvp_ends;/* [P][L][2]      */
+    /* grid_log: grid uniform in ln R (R_k = r_min (r_max/r_min)^(k/(n_grid-1))), spline in ln R */
+    int grid_log;
+    /* truncation (Sec. III): M_rc is dropped when |M_rc(R)| <= trunc_thr at both trunc_r;
+       trunc_thr <= 0 keeps every element */
+    double trunc_thr;
+    double trunc_r[2];
+    /* G in triplet form when G == NULL: g_nnz entries (term, row, col, value), summed */
+    long long g_nnz;
+    const int *g_term, *g_row, *g_col;
+    const double *g_val;
 } ora_system_desc;
 
 typedef struct {
@@ -275,6 +327,8 @@ typedef struct {
 typedef struct {
     int n, L, n_int, P;
     double mu, r_min, h;
+    int grid_log;      /* spline variable x = ln R instead of R          */
+    double x0;         /* first knot in the spline variable             */
     const double *E;
     int n_blk;
     int *blk_start, *blk_size, *members; /* members grouped by block (same m) */
@@ -282,6 +336,7 @@ typedef struct {
     size_t *blk_goff;
     int *up, *dn;                        /* Coriolis partners (-1: none)      */
     double *aup, *adn;                   /* A+ and A- ladder factors          */
+    unsigned char *keep;                 /* per block: [nb][nb] truncation mask (NULL: keep all) */
     double *coef;                        /* [L][n_int][4]                     */
     double *dcoef;                       /* [P][L][n_int][4]                  */
 } ora_sys;
@@ -289,28 +344,49 @@ typedef struct {
 static void sys_free(ora_sys *S)
 {
     free(S->blk_start); free(S->blk_size); free(S->members); free(S->Gb); free(S->blk_goff);
-    free(S->up); free(S->dn); free(S->aup); free(S->adn); free(S->coef); free(S->dcoef);
+    free(S->up); free(S->dn); free(S->aup); free(S->adn); free(S->coef); free(S->dcoef); free(S->keep);
     memset(S, 0, sizeof(*S));
 }
+
+/* sort key of the Coriolis partner search: states of one level and one j, ordered by m */
+typedef struct { int level, j, m, s; } ora_key;
+
+static int key_cmp(const void *pa, const void *pb)
+{
+    const ora_key *a = pa, *b = pb;
+    if (a->level != b->level) return a->level < b->level ? -1 : 1;
+    if (a->j != b->j) return a->j < b->j ? -1 : 1;
+    if (a->m != b->m) return a->m < b->m ? -1 : 1;
+    return 0;
+}
+
+static void eval_terms(const ora_sys *S, const double *coef, double R, double *v, double *dv, double *d2v);
 
 static int sys_build(const ora_system_desc *d, ora_sys *S)
 {
     memset(S, 0, sizeof(*S));
     int n = d->n, L = d->n_terms;
     if (n < 1 || L < 1 || d->n_grid < 2 || !(d->mu > 0) || !(d->r_max > d->r_min)) return ORA_EINVAL;
+    if (d->grid_log && !(d->r_min > 0)) return ORA_EINVAL;
+    if (!d->G && d->g_nnz > 0 && (!d->g_term || !d->g_row || !d->g_col || !d->g_val)) return ORA_EINVAL;
     S->n = n; S->L = L; S->n_int = d->n_grid - 1; S->P = d->n_params;
-    S->mu = d->mu; S->r_min = d->r_min; S->h = (d->r_max - d->r_min) / (d->n_grid - 1);
+    S->mu = d->mu; S->r_min = d->r_min;
+    S->grid_log = d->grid_log != 0;
+    S->x0 = S->grid_log ? log(d->r_min) : d->r_min;
+    S->h = ((S->grid_log ? log(d->r_max) : d->r_max) - S->x0) / (d->n_grid - 1);
     S->E = d->energy;
     /* blocks of equal m (Eq. 5 couples states only within each m) */
-    int *blk_of = malloc(sizeof(int) * n);
+    int *blk_of = malloc(sizeof(int) * n), *pos_of = malloc(sizeof(int) * n);
     S->blk_start = malloc(sizeof(int) * (n + 1));
     S->blk_size = malloc(sizeof(int) * n);
     S->members = malloc(sizeof(int) * n);
     S->up = malloc(sizeof(int) * n); S->dn = malloc(sizeof(int) * n);
     S->aup = malloc(sizeof(double) * n); S->adn = malloc(sizeof(double) * n);
     int *mvals = malloc(sizeof(int) * n);
-    if (!blk_of || !S->blk_start || !S->blk_size || !S->members || !S->up || !S->dn || !S->aup || !S->adn || !mvals) {
-        free(blk_of); free(mvals); sys_free(S);
+    ora_key *keys = malloc(sizeof(ora_key) * n);
+    if (!blk_of || !pos_of || !S->blk_start || !S->blk_size || !S->members || !S->up || !S->dn || !S->aup ||
+        !S->adn || !mvals || !keys) {
+        free(blk_of); free(pos_of); free(mvals); free(keys); sys_free(S);
         return ORA_ENOMEM;
     }
     int nb = 0;
@@ -322,56 +398,80 @@ static int sys_build(const ora_system_desc *d, ora_sys *S)
         blk_of[s] = b;
     }
     S->n_blk = nb;
+    for (int b = 0; b < nb; ++b) S->blk_size[b] = 0;
+    for (int s = 0; s < n; ++s) S->blk_size[blk_of[s]]++;
     int pos = 0;
-    for (int b = 0; b < nb; ++b) {
-        S->blk_start[b] = pos;
-        for (int s = 0; s < n; ++s)
-            if (blk_of[s] == b) S->members[pos++] = s;
-        S->blk_size[b] = pos - S->blk_start[b];
-    }
+    for (int b = 0; b < nb; ++b) { S->blk_start[b] = pos; pos += S->blk_size[b]; S->blk_size[b] = 0; }
     S->blk_start[nb] = pos;
+    for (int s = 0; s < n; ++s) {   /* members in state order within each block */
+        int b = blk_of[s];
+        pos_of[s] = S->blk_size[b]++;
+        S->members[S->blk_start[b] + pos_of[s]] = s;
+    }
     /* coupling must vanish between different m (Eq. 6) */
-    for (int l = 0; l < L; ++l)
-        for (int r = 0; r < n; ++r)
-            for (int c = 0; c < n; ++c)
-                if (blk_of[r] != blk_of[c] && d->G[((size_t)l * n + r) * n + c] != 0.0) {
-                    free(blk_of); free(mvals); sys_free(S);
-                    return ORA_EINVAL;
-                }
+    int bad = 0;
+    if (d->G) {
+        for (int l = 0; l < L && !bad; ++l)
+            for (int r = 0; r < n && !bad; ++r)
+                for (int c = 0; c < n; ++c)
+                    if (blk_of[r] != blk_of[c] && d->G[((size_t)l * n + r) * n + c] != 0.0) { bad = 1; break; }
+    } else {
+        for (long long e = 0; e < d->g_nnz && !bad; ++e) {
+            int l = d->g_term[e], r = d->g_row[e], c = d->g_col[e];
+            if (l < 0 || l >= L || r < 0 || r >= n || c < 0 || c >= n) bad = 1;
+            else if (blk_of[r] != blk_of[c] && d->g_val[e] != 0.0) bad = 1;
+        }
+    }
+    if (bad) { free(blk_of); free(pos_of); free(mvals); free(keys); sys_free(S); return ORA_EINVAL; }
     S->blk_goff = malloc(sizeof(size_t) * (nb + 1));
     size_t tot = 0;
     for (int b = 0; b < nb; ++b) { S->blk_goff[b] = tot; tot += (size_t)L * S->blk_size[b] * S->blk_size[b]; }
     S->blk_goff[nb] = tot;
-    S->Gb = malloc(sizeof(double) * (tot ? tot : 1));
-    for (int b = 0; b < nb; ++b) {
-        int sz = S->blk_size[b];
-        const int *mem = S->members + S->blk_start[b];
-        for (int l = 0; l < L; ++l)
-            for (int r = 0; r < sz; ++r)
-                for (int c = 0; c < sz; ++c)
-                    S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + c] = d->G[((size_t)l * n + mem[r]) * n + mem[c]];
+    S->Gb = calloc(tot ? tot : 1, sizeof(double));
+    if (!S->Gb) { free(blk_of); free(pos_of); free(mvals); free(keys); sys_free(S); return ORA_ENOMEM; }
+    if (d->G) {
+        for (int b = 0; b < nb; ++b) {
+            int sz = S->blk_size[b];
+            const int *mem = S->members + S->blk_start[b];
+            for (int l = 0; l < L; ++l)
+                for (int r = 0; r < sz; ++r)
+                    for (int c = 0; c < sz; ++c)
+                        S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + c] = d->G[((size_t)l * n + mem[r]) * n + mem[c]];
+        }
+    } else {
+        for (long long e = 0; e < d->g_nnz; ++e) {
+            int l = d->g_term[e], r = d->g_row[e], c = d->g_col[e], b = blk_of[r], sz = S->blk_size[b];
+            S->Gb[S->blk_goff[b] + ((size_t)l * sz + pos_of[r]) * sz + pos_of[c]] += d->g_val[e];
+        }
     }
-    /* Coriolis partners: same level and j, m +- 1 */
+    /* Coriolis partners: same level and j, m +- 1 (neighbours after sorting by level, j, m) */
     for (int s = 0; s < n; ++s) {
         S->up[s] = S->dn[s] = -1;
         S->aup[s] = S->adn[s] = 0.0;
+        keys[s].level = d->level[s]; keys[s].j = d->jq[s]; keys[s].m = d->mq[s]; keys[s].s = s;
+    }
+    qsort(keys, n, sizeof(ora_key), key_cmp);
+    for (int i = 0; i + 1 < n; ++i) {
+        const ora_key *a = keys + i, *b = keys + i + 1;
+        if (a->j < 0 || a->level != b->level || a->j != b->j || b->m != a->m + 1) continue;
+        S->up[a->s] = b->s;
+        S->dn[b->s] = a->s;
+    }
+    for (int s = 0; s < n; ++s) {
         int j = d->jq[s], m = d->mq[s];
-        if (j < 0) continue;
-        for (int q = 0; q < n; ++q) {
-            if (d->jq[q] != j || d->level[q] != d->level[s]) continue;
-            if (d->mq[q] == m + 1) S->up[s] = q;
-            if (d->mq[q] == m - 1) S->dn[s] = q;
-        }
+        if (j < 0) { S->up[s] = S->dn[s] = -1; continue; }
         double jj = (double)j * (j + 1);
         if (S->up[s] >= 0) S->aup[s] = sqrt(jj - (double)m * (m + 1));
         if (S->dn[s] >= 0) S->adn[s] = sqrt(jj - (double)m * (m - 1));
     }
-    free(blk_of); free(mvals);
-    /* splines of the expansion coefficients (and of their parameter derivatives) */
+    free(blk_of); free(pos_of); free(mvals); free(keys);
+    /* splines of the expansion coefficients (and of their parameter derivatives); on the log
+       grid the spline variable is x = ln R and the end slopes are dv/dx = R dv/dR */
+    double e0 = S->grid_log ? d->r_min : 1.0, e1 = S->grid_log ? d->r_max : 1.0;
     S->coef = malloc(sizeof(double) * (size_t)L * S->n_int * 4);
     for (int l = 0; l < L; ++l) {
-        int e = ora_spline(d->n_grid, S->h, d->v + (size_t)l * d->n_grid, d->dv_ends[2 * l], d->dv_ends[2 * l + 1],
-                           S->coef + (size_t)l * S->n_int * 4);
+        int e = ora_spline(d->n_grid, S->h, d->v + (size_t)l * d->n_grid, e0 * d->dv_ends[2 * l],
+                           e1 * d->dv_ends[2 * l + 1], S->coef + (size_t)l * S->n_int * 4);
         if (e) { sys_free(S); return e; }
     }
     if (S->P > 0) {
@@ -379,19 +479,60 @@ static int sys_build(const ora_system_desc *d, ora_sys *S)
         for (int p = 0; p < S->P; ++p)
             for (int l = 0; l < L; ++l) {
                 size_t o = (size_t)p * L + l;
-                int e = ora_spline(d->n_grid, S->h, d->dvp + o * d->n_grid, d->dvp_ends[2 * o], d->dvp_ends[2 * o + 1],
-                                   S->dcoef + o * S->n_int * 4);
+                int e = ora_spline(d->n_grid, S->h, d->dvp + o * d->n_grid, e0 * d->dvp_ends[2 * o],
+                                   e1 * d->dvp_ends[2 * o + 1], S->dcoef + o * S->n_int * 4);
                 if (e) { sys_free(S); return e; }
             }
     }
+    /* truncation (Sec. III): keep M_rc where |M_rc| exceeds the threshold at either reference
+       distance, M evaluated from the splines above */
+    if (d->trunc_thr > 0.0) {
+        size_t ktot = tot / (size_t)L;
+        S->keep = malloc(ktot ? ktot : 1);
+        double *va = malloc(sizeof(double) * 6 * L);
+        if (!S->keep || !va) { free(va); sys_free(S); return ORA_ENOMEM; }
+        eval_terms(S, S->coef, d->trunc_r[0], va, va + L, va + 2 * L);
+        eval_terms(S, S->coef, d->trunc_r[1], va + 3 * L, va + 4 * L, va + 5 * L);
+        for (int b = 0; b < nb; ++b) {
+            int sz = S->blk_size[b];
+            const double *Gb = S->Gb + S->blk_goff[b];
+            unsigned char *kp = S->keep + S->blk_goff[b] / L;
+            for (int r = 0; r < sz; ++r)
+                for (int c = 0; c < sz; ++c) {
+                    double ma = 0.0, mb = 0.0;
+                    for (int l = 0; l < L; ++l) {
+                        double g = Gb[((size_t)l * sz + r) * sz + c];
+                        ma += va[l] * g;
+                        mb += va[3 * L + l] * g;
+                    }
+                    kp[(size_t)r * sz + c] = (fabs(ma) > d->trunc_thr || fabs(mb) > d->trunc_thr) ? 1 : 0;
+                }
+        }
+        free(va);
+    }
     return ORA_OK;
+}
+
+/* whether M_rc of block b is kept by the truncation */
+static int kept(const ora_sys *S, int b, int r, int c)
+{
+    if (!S->keep) return 1;
+    int sz = S->blk_size[b];
+    return S->keep[S->blk_goff[b] / S->L + (size_t)r * sz + c];
 }
 
 /* v_lambda and its first two R-derivatives; table_range set if R < r_min */
 static void eval_terms(const ora_sys *S, const double *coef, double R, double *v, double *dv, double *d2v)
 {
+    double x = S->grid_log ? log(R) : R;
     for (int l = 0; l < S->L; ++l)
-        spline_at(coef + (size_t)l * S->n_int * 4, S->n_int, S->r_min, S->h, R, v + l, dv + l, d2v + l);
+        spline_at(coef + (size_t)l * S->n_int * 4, S->n_int, S->x0, S->h, x, v + l, dv + l, d2v + l);
+    if (S->grid_log)  /* chain rule from x = ln R: f' = f_x / R, f'' = (f_xx - f_x) / R^2 */
+        for (int l = 0; l < S->L; ++l) {
+            double d1 = dv[l] / R;
+            d2v[l] = (d2v[l] - dv[l]) / (R * R);
+            dv[l] = d1;
+        }
 }
 
 /* y = sum over the m-blocks of (sum_lambda f_lambda G^lambda) x   (Eq. 5 / Eq. 12) */
@@ -404,6 +545,7 @@ static void couple(const ora_sys *S, const double *f, const double complex *x, d
         for (int r = 0; r < sz; ++r) {
             double complex acc = 0.0;
             for (int c = 0; c < sz; ++c) {
+                if (!kept(S, b, r, c)) continue;
                 double mrc = 0.0;
                 for (int l = 0; l < S->L; ++l) mrc += f[l] * Gb[((size_t)l * sz + r) * sz + c];
                 acc += mrc * x[mem[c]];
@@ -543,7 +685,8 @@ static void initial_state(const ora_sys *S, const ora_traj *tr, double complex *
             if (S->members[S->blk_start[q2] + i] == s0) { b = q2; r = i; }
     int sz = S->blk_size[b];
     double m00 = 0.0;
-    for (int l = 0; l < S->L; ++l) m00 += pv[l] * S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + r];
+    if (kept(S, b, r, r))
+        for (int l = 0; l < S->L; ++l) m00 += pv[l] * S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + r];
     free(pv);
     double lz = tr->b * sqrt(2.0 * S->mu * tr->e_coll);
     q[0] = tr->r0;
@@ -629,6 +772,38 @@ static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o
 /* Propagate n_traj trajectories (Sec. II / III).  final_amp: [n_traj][n] complex (interleaved re, im).
  * line_speed: prescribed-line speed per trajectory (only with ORA_F_PRESCRIBED; the line is
  * time-symmetric about max_steps*dt/2 with impact parameter b). */
+/* v_lambda(R) and its first two R-derivatives from the system's splines at npts distances
+ * (out: [npts][L] each) */
+int ora_sys_terms(const ora_system_desc *d, int npts, const double *R, double *v, double *dv, double *d2v)
+{
+    ora_sys S;
+    int e = sys_build(d, &S);
+    if (e) return e;
+    for (int i = 0; i < npts; ++i)
+        eval_terms(&S, S.coef, R[i], v + (size_t)i * S.L, dv + (size_t)i * S.L, d2v + (size_t)i * S.L);
+    sys_free(&S);
+    return ORA_OK;
+}
+
+/* the truncation's decision per element: keep[r * n + c] = 1 for a retained M_rc (0 for a
+ * dropped one and for every pair of different m); dense n x n output, small systems only */
+int ora_sys_kept(const ora_system_desc *d, unsigned char *keep)
+{
+    ora_sys S;
+    int e = sys_build(d, &S);
+    if (e) return e;
+    int n = S.n;
+    memset(keep, 0, (size_t)n * n);
+    for (int b = 0; b < S.n_blk; ++b) {
+        int sz = S.blk_size[b];
+        const int *mem = S.members + S.blk_start[b];
+        for (int r = 0; r < sz; ++r)
+            for (int c = 0; c < sz; ++c) keep[(size_t)mem[r] * n + mem[c]] = (unsigned char)kept(&S, b, r, c);
+    }
+    sys_free(&S);
+    return ORA_OK;
+}
+
 int ora_propagate(const ora_system_desc *d, const ora_traj *tr, int n_traj, int flags, const double *line_speed,
                   int n_threads, double *final_amp, ora_result *res)
 {
@@ -741,7 +916,8 @@ static int tangent_one(const ora_sys *S, const ora_traj *tr, double complex *a_o
         for (int p = 0; p < P; ++p) {
             eval_terms(S, S->dcoef + (size_t)p * S->L * S->n_int * 4, tr->r0, W.pv, W.pdv, W.pd2v);
             double dm00 = 0.0;
-            for (int l2 = 0; l2 < S->L; ++l2) dm00 += W.pv[l2] * S->Gb[S->blk_goff[b] + ((size_t)l2 * sz + r) * sz + r];
+            if (kept(S, b, r, r))
+                for (int l2 = 0; l2 < S->L; ++l2) dm00 += W.pv[l2] * S->Gb[S->blk_goff[b] + ((size_t)l2 * sz + r) * sz + r];
             tq[4 * p + 1] = -S->mu * dm00 / q[1];
         }
     }

@@ -735,7 +735,7 @@ __global__ void k_tc_continue(TcState T, cudaGraphConditionalHandle h)
     if (threadIdx.x == 0) {
         const int live = *((volatile int *)T.live), err = *((volatile int *)(T.live + 1));
         T.live[2] += 1;  // chunks run (launch accounting)
-        cudaGraphSetConditional(h, live > 0 && !err ? 1u : 0u);
+        if (h) cudaGraphSetConditional(h, live > 0 && !err ? 1u : 0u);
     }
 }
 
@@ -824,10 +824,28 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     cudaStream_t cap = nullptr;
     cudaGraphConditionalHandle cond;
     cudaGraphNode_t wnode;
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) {
+    int live[4] = {0, 0, 0, 0};
+    // MQCT_TC_HOST_LOOP=1: the same chunks launched directly from a host loop that reads the
+    // live-slot count after each chunk (for profilers that do not follow conditional graph nodes)
+    const char *hl = std::getenv("MQCT_TC_HOST_LOOP");
+    const bool host_loop = hl && hl[0] == '1';
+    for (long long it = 0; host_loop && e == cudaSuccess; ++it) {
+        k_tc_reset_live<<<1, 32, 0, st>>>(T);
+        for (int k = 0; k < chunk; ++k)
+            for (int s = 0; s < 4; ++s) {
+                const int cur = s & 1;
+                k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, st>>>(T, s, cur);
+                k_tc_slots<<<slot_blocks, 128, 0, st>>>(T, s, n_rowblocks);
+            }
+        k_tc_continue<<<1, 32, 0, st>>>(T, 0);
+        if ((e = cudaMemcpyAsync(live, T.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (live[0] == 0 || live[1]) break;
+    }
+    if (!host_loop && e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (!host_loop && e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+    if (!host_loop && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+    if (!host_loop && e == cudaSuccess) {
         alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)] = {};
         cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
         np.type = cudaGraphNodeTypeConditional;
@@ -837,8 +855,8 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         e = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &np);
         if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
+    if (!host_loop && e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (!host_loop && e == cudaSuccess) {
         k_tc_reset_live<<<1, 32, 0, cap>>>(T);
         for (int k = 0; k < chunk; ++k)
             for (int s = 0; s < 4; ++s) {
@@ -850,11 +868,10 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(cap, &captured);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
-    int live[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(live, T.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (!host_loop && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (!host_loop && e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (!host_loop && e == cudaSuccess) e = cudaMemcpyAsync(live, T.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!host_loop && e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);

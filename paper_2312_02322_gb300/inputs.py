@@ -295,3 +295,25 @@ def rate_set(n_levels=30, temps_k=(10.0, 50.0, 100.0, 300.0, 1000.0), emax_cm=80
         sig[:, a, a] = 50.0 / (1.0 + U / 1000.0)
     kT = np.asarray(temps_k, np.float64) * 3.1668115634556e-6
     return RateSet(u=cm(U), energy=cm(E), g=g, sigma=sig, kT=kT, mu=float(mu_amu * AMU_ME))
+
+
+def sparse_pes_params(jmax=200, lam_max=12, n_grid=63, mu_amu=1.8, bconst_cm=None):
+    """The paper-scale setup of Sec. III on an atom + rigid rotor: a 63-point logarithmic R grid on
+    3-30 bohr, Legendre terms lam <= lam_max, wall and anisotropy placed where the paper's
+    truncation distances (6.03, 7.11 bohr) sit on the repulsive wall:
+    v_0 = 1e4 cm^-1 exp(-1.8 (R - 5)) - damped C6 (3e5 cm^-1 bohr^6, Rd = 3), and for lam >= 1
+    v_lam = 3000 cm^-1 0.6^(lam-1) exp(-(1.8 + 0.05 lam)(R - 5)).  The rotational constant puts the
+    top of the basis near the paper's 8000 cm^-1 (B = 8000 / (jmax (jmax + 1)) cm^-1, at most
+    10 cm^-1); mu = 1.8 amu (H2O + H2)."""
+    L = lam_max + 1
+    beta = np.array([1.8] + [1.8 + 0.05 * l for l in range(1, L)])
+    a5 = np.array([1e4] + [3000.0 * 0.6 ** (l - 1) for l in range(1, L)])
+    A = cm(a5 * np.exp(beta * 5.0))
+    B = bconst_cm if bconst_cm is not None else min(10.0, 8000.0 / max(1, jmax * (jmax + 1)))
+    return DiatomParams(jmax=jmax, bconst=float(cm(B)), mu=mu_amu * AMU_ME, A=A, beta=beta, c6=float(cm(3e5)),
+                        rd=3.0, n_grid=n_grid, r_min=3.0, r_max=30.0)
+
+
+# the paper's truncation (Sec. III): |M| > 1 cm^-1 at R = 6.03 or 7.11 bohr
+PAPER_TRUNC_CM = 1.0
+PAPER_TRUNC_R = (6.03, 7.11)
