@@ -148,8 +148,12 @@ void ora_diatom_G(int jmax, int lam, double *G)
 /* grid point k: uniform in R, or (grid_log) uniform in ln R (Sec. III: logarithmic spacing) */
 static double grid_r(int grid_log, int n_grid, double r_min, double r_max, int k)
 {
-    if (grid_log) return r_min * exp(k * (log(r_max) - log(r_min)) / (n_grid - 1));
-    return r_min + k * (r_max - r_min) / (n_grid - 1);
+    if (grid_log) {
+        double hl = (log(r_max) - log(r_min)) / (n_grid - 1);
+        return r_min * exp(k * hl);
+    }
+    double h = (r_max - r_min) / (n_grid - 1);
+    return r_min + k * h;
 }
 
 void ora_diatom_pes_grid(int L, const double *A, const double *beta, double c6, double rd, int n_grid,
