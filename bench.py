@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--batch-shape", type=int, default=0,
                     help="FP32 batched kernel shape 1..7 for every system (see mqct_propagate_opts); implies "
                          "--no-autotune")
+    ap.add_argument("--no-sparse", dest="sparse", action="store_false",
+                    help="skip the paper-scale sparse-path (log grid, truncation, N = 40401) timing")
     ap.add_argument("--no-rates", dest="rates", action="store_false",
                     help="skip the post-processing (Eq. 20 and rate coefficients) timing")
     ap.add_argument("--no-n1600", dest="n1600", action="store_false",
@@ -441,6 +443,66 @@ def rates_block(api, n_levels=1032, reps=5):
             "ms": ms, "rate_coefficients_per_s": n_rates / (ms * 1e-3), "transitions": L * (L - 1) // 2}
 
 
+def sparse_block(api, n_traj=1024, max_steps=2000, jmax=200):
+    """The paper-scale setup of Sec. III on an atom + rotor (FP32 spline table, stage-synchronous
+    sparse kernel): N = (jmax+1)^2 = 40401 states, Legendre terms lambda <= 12, the 63-point log grid on
+    3-30 bohr, |M| > 1 cm^-1 at 6.03 / 7.11 bohr; n_traj seeded trajectories from 30 bohr (E log-uniform
+    on 100-5000 cm^-1, b uniform on 0-10 bohr, initial j uniform on 0-10), each capped at max_steps
+    RK4 steps; one warm-up call, then one timed call with the trajectories resident on the device."""
+    import torch
+
+    t0 = time.perf_counter()
+    p = W.sparse_pes_params(jmax=jmax, lam_max=12)
+    trunc = (float(W.cm(W.PAPER_TRUNC_CM)), *W.PAPER_TRUNC_R)
+    sys_ = api.System.diatom(p, path="plain", precision="fp32", grid="log", trunc=trunc)
+    build_s = time.perf_counter() - t0
+    inf = sys_.info
+    rng = np.random.default_rng(W.DEFAULT_SEED)
+    e = W.cm(np.exp(rng.uniform(np.log(100.0), np.log(5000.0), n_traj)))
+    b = rng.uniform(0.0, 10.0, n_traj)
+    j = rng.integers(0, 11, n_traj).astype(np.int32)
+    ts = W.TrajSet(e, b, j, np.zeros_like(j), np.zeros(n_traj, np.int32), 1, r0=30.0, r_end=30.0, dt=5.0,
+                   max_steps=max_steps, sampling="mc", b_max=10.0, n_b=0)
+    tr = api.make_trajs(ts, sys_)
+    trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+    few = torch.from_numpy(tr[:64].copy().view(np.uint8)).cuda()
+    api.propagate(sys_, few, want_pop=False, device=True)  # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    pop, _, dg = api.propagate(sys_, trd, want_pop=True, device=True, stream=stream.cuda_stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    launches = api.last_launch_count()
+    ms = ev[0].elapsed_time(ev[1])
+    d = api.diag_to_numpy(dg)
+    steps = float(d["steps"].sum())
+    stages = 4.0 * steps
+    # algorithmic bytes per trajectory-stage: the amplitudes streamed once (C read, A and ACC read and
+    # written, the next stage's C written: 6 x 8 B per state) plus one interval's FP32 table slab
+    # shared by the slots in that interval (counted once per stage launch: a lower bound)
+    amp_b = 6 * 8 * inf["n_states"]
+    table_b = inf["table_bytes"] / (p.n_grid - 1)
+    n_launch_stage = 4.0 * float(d["steps"].max() + 1)
+    algo = amp_b * stages + table_b * n_launch_stage
+    gbs = algo / (ms * 1e-3) / 1e9
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"workload": f"{n_traj} trajectories, N = {inf['n_states']} (jmax {jmax}, lambda <= 12), log grid 3-30 bohr "
+                        f"x {p.n_grid}, |M| > 1 cm^-1 at 6.03/7.11 bohr, each capped at {max_steps} steps",
+            "table_nnz": int(inf["table_nnz"]), "trunc_dropped": int(inf["trunc_dropped"]),
+            "table_bytes": int(inf["table_bytes"]), "build_s": build_s, "ms": ms,
+            "traj_steps": steps, "traj_steps_per_s": steps / (ms * 1e-3), "gpu_launches": launches,
+            "max_norm_dev": float(np.max(d["norm_dev"])),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_traj_stage": amp_b, "table_slab_bytes": table_b,
+                         "kernel": "k_sp_stage (timed with the whole propagate call)"}}
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def gpu_arm(args):
     import torch
@@ -620,6 +682,7 @@ def gpu_arm(args):
     if args.adjoint:
         adj = adjoint_block(api, args.adjoint)
     rates = rates_block(api) if args.rates else None
+    sparse = sparse_block(api) if args.sparse else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -657,7 +720,7 @@ def gpu_arm(args):
         "gpu_launches": n_launch[0], "latency": latency, "comparison": compare, "adjoint": adj,
         "sigma_sets_per_s": sigma_sets * ws / (ms * 1e-3 / args.steps),
         "sigma_set": "all cross sections out of one (collision energy, initial level) group",
-        "n1600": n1600, "rates": rates,
+        "n1600": n1600, "rates": rates, "sparse": sparse,
     }))
 
 

@@ -70,10 +70,15 @@ typedef enum { MQCT_PATH_PLAIN = 0, MQCT_PATH_FACTORISED = 1 } mqct_path;
 
 /* Precision of the amplitudes and of the coupling contraction.  Phase arguments E_n t,
  * the classical variables and the conserved-quantity bookkeeping are FP64 in every mode.
- * MQCT_BF16X3 runs the stage-synchronous tensor-core path: one CUDA graph with a conditional
- * loop runs every trajectory; with the environment variable MQCT_TC_HOST_LOOP=1 the same
- * kernels are launched from a host loop instead (for profilers that do not follow
- * conditional graph nodes; same arithmetic). */
+ * MQCT_FP32 on the FACTORISED path runs the persistent batched kernel (amplitudes of a few
+ * trajectories in each CTA's shared memory, bases up to ~3000 states); MQCT_FP32 on the PLAIN path
+ * runs the stage-synchronous sparse path for bases of any size (amplitudes of every trajectory in
+ * flight in device memory, an FP32 spline table of every retained M_nm evaluated per element and
+ * trajectory, the logarithmic grid and the truncation of Sec. III available).  MQCT_BF16X3 (FACTORISED
+ * only) runs the stage-synchronous tensor-core path.  Both stage-synchronous paths run every
+ * trajectory under one CUDA graph with a conditional loop; with the environment variable
+ * MQCT_TC_HOST_LOOP=1 the same kernels are launched from a host loop instead (for profilers that do
+ * not follow conditional graph nodes; same arithmetic). */
 typedef enum { MQCT_FP64 = 0, MQCT_FP32 = 1, MQCT_BF16X3 = 2 } mqct_precision;
 
 /* per-trajectory status bits (mqct_diag.status) */
@@ -112,7 +117,7 @@ typedef struct {
     const int32_t *g_row;    /*   (row,col) and (col,row); duplicates are summed              */
     const int32_t *g_col;
     const double *g_val;
-    int32_t n_grid;          /* >= 4 uniform grid points R_k = r_min + k (r_max-r_min)/(n_grid-1) */
+    int32_t n_grid;          /* >= 4 grid points (grid_kind below)                            */
     double r_min, r_max;
     const double *v;         /* [L][n_grid] v_lambda(R_k) (hartree)                          */
     const double *dv_ends;   /* [L][2] dv_lambda/dR at r_min and r_max (clamped spline)      */
@@ -122,7 +127,21 @@ typedef struct {
     int32_t path;            /* mqct_path                                                    */
     int32_t precision;       /* mqct_precision                                               */
     int32_t flags;           /* 0 or MQCT_PRESCRIBED_TRAJ                                     */
+    int32_t grid_kind;       /* MQCT_GRID_UNIFORM, or MQCT_GRID_LOG (below)                   */
+    double trunc_threshold;  /* PLAIN path: M_nm dropped when |M_nm(R)| <= threshold at both  */
+    double trunc_r[2];       /*   trunc_r (hartree, bohr; Sec. III); <= 0 keeps every element */
 } mqct_system_desc;
+
+/* R grids (Sec. III).  MQCT_GRID_UNIFORM: R_k = r_min + k (r_max - r_min)/(n_grid - 1), splines
+ * clamped cubics in R.  MQCT_GRID_LOG: R_k = r_min (r_max/r_min)^(k/(n_grid - 1)), r_min > 0 (the
+ * paper's logarithmic spacing); the splines are clamped cubics in ln R on its uniform grid (end
+ * slopes R dv/dR from dv_ends), R-derivatives by the chain rule.  The logarithmic grid runs on
+ * MQCT_FP64 systems (both paths) and on MQCT_FP32 systems of the PLAIN path.
+ * Truncation (PLAIN path only): M_nm(R) = sum_lambda v_lambda(R) G^lambda_nm is evaluated from the
+ * splines at trunc_r[0] and trunc_r[1]; an element whose magnitude is <= trunc_threshold at both is
+ * dropped for the whole propagation (the paper keeps |M| > 1 cm^-1 at 6.03 and 7.11 bohr). */
+#define MQCT_GRID_UNIFORM 0
+#define MQCT_GRID_LOG 1
 
 /* One trajectory (Sec. III: collision energy, impact parameter, initial state). */
 typedef struct {
@@ -160,6 +179,9 @@ typedef struct {
     int32_t n_coupling_terms; /* FACTORISED: terms stored as matrices (identity terms are not) */
     int32_t n_row_tiles;      /* BF16X3: 128-row tiles of whole m-blocks                   */
     int64_t tc_kchunks;       /* BF16X3: non-zero 16-column K chunks over terms and tiles  */
+    int64_t trunc_dropped;    /* PLAIN: elements M_nm dropped by the truncation           */
+    int32_t grid_kind;        /* MQCT_GRID_UNIFORM or MQCT_GRID_LOG                        */
+    int32_t reserved;
 } mqct_system_info_t;
 
 /* Parameters of the built-in atom + linear rotor system (helper for users and tests):
@@ -180,6 +202,9 @@ typedef struct {
     double r_min, r_max;
     int32_t with_params;
     int32_t path, precision;
+    int32_t grid_kind;        /* MQCT_GRID_UNIFORM or MQCT_GRID_LOG: tabulation grid of v_lambda */
+    double trunc_threshold;   /* copied into the description (PLAIN path truncation)            */
+    double trunc_r[2];
 } mqct_diatom_params;
 
 /* Build the description of the atom + linear rotor system above.  Allocates the host
@@ -275,9 +300,11 @@ typedef struct {
                              gets the widest slot count (32, 16, 8 or 4, at most the shape's) its
                              basis fits; a shape that some system does not fit
                              -> MQCT_ERR_UNSUPPORTED                                             */
-    const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: BF16X3 trajectories in flight per
-                             system (rounded up to a multiple of 64, at most 8192), 0 = automatic
-                             (one or two waves of the GPU)                                       */
+    const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: trajectories in flight per system
+                             on the stage-synchronous paths -- BF16X3: rounded up to a multiple
+                             of 64, at most 8192, 0 = automatic (one or two waves of the GPU);
+                             FP32 PLAIN: rounded up to a multiple of 8, at most 8192, 0 = every
+                             trajectory up to 4096                                              */
 } mqct_propagate_opts;
 
 /* mqct_propagate with options (opts may be NULL).  Uneven batches: the trajectories of several

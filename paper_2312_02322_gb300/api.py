@@ -43,6 +43,7 @@ class Desc(C.Structure):
         ("g_val", C.c_void_p), ("n_grid", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double),
         ("v", C.c_void_p), ("dv_ends", C.c_void_p), ("n_params", C.c_int32), ("dv_dparam", C.c_void_p),
         ("ddv_ends", C.c_void_p), ("path", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
+        ("grid_kind", C.c_int32), ("trunc_threshold", C.c_double), ("trunc_r", C.c_double * 2),
     ]
 
 
@@ -51,14 +52,16 @@ class Info(C.Structure):
                 ("n_blocks", C.c_int32), ("max_block", C.c_int32), ("path", C.c_int32), ("precision", C.c_int32),
                 ("table_nnz", C.c_int64), ("table_bytes", C.c_int64), ("glambda_nnz", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_coupling_terms", C.c_int32), ("n_row_tiles", C.c_int32),
-                ("tc_kchunks", C.c_int64)]
+                ("tc_kchunks", C.c_int64), ("trunc_dropped", C.c_int64), ("grid_kind", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class DiatomParams(C.Structure):
     _fields_ = [("jmax", C.c_int32), ("bconst", C.c_double), ("mu", C.c_double), ("n_terms", C.c_int32),
                 ("A", C.c_double * 16), ("beta", C.c_double * 16), ("c6", C.c_double), ("rd", C.c_double),
                 ("n_grid", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double), ("with_params", C.c_int32),
-                ("path", C.c_int32), ("precision", C.c_int32)]
+                ("path", C.c_int32), ("precision", C.c_int32), ("grid_kind", C.c_int32),
+                ("trunc_threshold", C.c_double), ("trunc_r", C.c_double * 2)]
 
 
 class AsymParams(C.Structure):
@@ -73,6 +76,9 @@ class AsymParams(C.Structure):
 class PropagateOpts(C.Structure):
     _fields_ = [("t_start_ns", C.c_void_p), ("t_done_ns", C.c_void_p), ("batch_shape", C.c_void_p),
                 ("tc_slots", C.c_void_p)]
+
+
+GRID_UNIFORM, GRID_LOG = 0, 1
 
 
 class RateDesc(C.Structure):
@@ -188,9 +194,11 @@ class System:
 
     @classmethod
     def diatom(cls, p: "_inputs.DiatomParams", path="plain", precision="fp64", with_params=False,
-               prescribed=False) -> "System":
+               prescribed=False, grid="uniform", trunc=None) -> "System":
         """prescribed=True: MQCT_PRESCRIBED_TRAJ, each trajectory follows the time-symmetric straight
-        line of impact parameter b and speed sqrt(2 e_coll / mu) for exactly max_steps steps."""
+        line of impact parameter b and speed sqrt(2 e_coll / mu) for exactly max_steps steps.
+        grid="log": MQCT_GRID_LOG tabulation (splines in ln R); trunc=(threshold, R_a, R_b): PLAIN-path
+        truncation of |M| <= threshold at both distances (Sec. III)."""
         dp = DiatomParams()
         dp.jmax, dp.bconst, dp.mu, dp.n_terms = p.jmax, p.bconst, p.mu, p.n_terms
         for i in range(p.n_terms):
@@ -199,6 +207,9 @@ class System:
         dp.c6, dp.rd, dp.n_grid, dp.r_min, dp.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
         dp.with_params = int(bool(with_params))
         dp.path, dp.precision = _PATHS[path], _PRECS[precision]
+        dp.grid_kind = {"uniform": GRID_UNIFORM, "log": GRID_LOG}[grid]
+        if trunc is not None:
+            dp.trunc_threshold, dp.trunc_r[0], dp.trunc_r[1] = (float(x) for x in trunc)
         d = Desc()
         _check(lib().mqct_build_diatom(C.byref(dp), C.byref(d)))
         d.flags = PRESCRIBED_TRAJ if prescribed else 0

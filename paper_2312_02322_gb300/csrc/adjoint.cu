@@ -721,6 +721,7 @@ extern "C" mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int
                                     double *dL_dparam, void *cuda_stream)
 {
     reset_launches();
+    if (sys && sys->s.h.grid_log) return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: the logarithmic grid is not supported");
     if (!sys || n < 0 || n_groups < 0 || ckpt < 1 || !dL_dparam) return fail(MQCT_ERR_INVALID_ARG, "mqct_adjoint: bad argument");
     const DevSys &h = sys->s.h;
     if (h.P < 1 || !h.dvcoef) return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: the system has no parameter tables");

@@ -306,5 +306,5 @@ extern "C" mqct_status mqct_build_asym_top(const mqct_asym_params *p, mqct_syste
     std::vector<double> A(L), beta(L);
     for (int t = 0; t < L; ++t) { A[t] = p->coef[t]; beta[t] = p->beta[t]; }
     return finish_desc(out, "mqct_build_asym_top", energy, level, jq, mq, p->mu, L, gt, gr, gc, gv, A.data(),
-                       beta.data(), p->c6, p->rd, ng, p->r_min, p->r_max, p->with_params != 0, p->path, p->precision);
+                       beta.data(), p->c6, p->rd, ng, p->r_min, p->r_max, p->with_params != 0, p->path, p->precision, MQCT_GRID_UNIFORM);
 }

@@ -100,10 +100,13 @@ mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vecto
                         const std::vector<int32_t> &mq, double mu, int L, const std::vector<int32_t> &gt,
                         const std::vector<int32_t> &gr, const std::vector<int32_t> &gc, const std::vector<double> &gv,
                         const double *A, const double *beta, double c6, double rd, int ng, double r_min, double r_max,
-                        bool with_params, int path, int precision)
+                        bool with_params, int path, int precision, int grid_kind)
 {
     const int n = (int)energy.size();
+    // grid point k: uniform in R, or in ln R (MQCT_GRID_LOG)
     const double h = (r_max - r_min) / (ng - 1);
+    const double hl = grid_kind == MQCT_GRID_LOG ? (std::log(r_max) - std::log(r_min)) / (ng - 1) : 0.0;
+    auto grid_r = [&](int k) { return grid_kind == MQCT_GRID_LOG ? r_min * std::exp(k * hl) : r_min + k * h; };
     std::vector<double> v((size_t)L * ng), ends((size_t)L * 2);
     auto c6term = [&](double R) { return -c6 * std::pow(R, -6.0) * (1.0 - std::exp(-std::pow(R / rd, 6.0))); };
     auto c6slope = [&](double R) {
@@ -112,7 +115,7 @@ mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vecto
     };
     for (int l = 0; l < L; ++l) {
         for (int k = 0; k < ng; ++k) {
-            double R = r_min + k * h;
+            double R = grid_r(k);
             v[(size_t)l * ng + k] = A[l] * std::exp(-beta[l] * R) + (l == 0 ? c6term(R) : 0.0);
         }
         for (int e = 0; e < 2; ++e) {
@@ -128,7 +131,7 @@ mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vecto
         dvpe.assign((size_t)P * L * 2, 0.0);
         for (int l = 0; l < L; ++l) {
             for (int k = 0; k < ng; ++k) {
-                double R = r_min + k * h, ex = std::exp(-beta[l] * R);
+                double R = grid_r(k), ex = std::exp(-beta[l] * R);
                 dvp[((size_t)l * L + l) * ng + k] = ex;                      // d/dA_l
                 dvp[((size_t)(L + l) * L + l) * ng + k] = -R * A[l] * ex;    // d/dbeta_l
             }
@@ -164,6 +167,7 @@ mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vecto
     out->path = path;
     out->precision = precision;
     out->flags = 0;
+    out->grid_kind = grid_kind;
     if (!out->energy || !out->level || !out->j || !out->m || !out->g_term || !out->g_row || !out->g_col ||
         !out->g_val || !out->v || !out->dv_ends || (P && (!out->dv_dparam || !out->ddv_ends))) {
         mqct_free_desc(out);
@@ -186,6 +190,8 @@ extern "C" mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_syste
     if (!(p->r_max > p->r_min) || !(p->r_min > 0)) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: bad grid range");
     if (!(p->mu > 0)) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: mu <= 0");
     if (!(p->rd > 0)) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: rd <= 0");
+    if (p->grid_kind != MQCT_GRID_UNIFORM && p->grid_kind != MQCT_GRID_LOG)
+        return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: unknown grid_kind");
     const int n = (jmax + 1) * (jmax + 1);
 
     std::vector<double> energy(n);
@@ -227,8 +233,15 @@ extern "C" mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_syste
         }
     }
 
-    return mqct::finish_desc(out, "mqct_build_diatom", energy, level, jq, mq, p->mu, L, gt, gr, gc, gv, p->A, p->beta,
-                             p->c6, p->rd, ng, p->r_min, p->r_max, p->with_params != 0, p->path, p->precision);
+    const mqct_status st = mqct::finish_desc(out, "mqct_build_diatom", energy, level, jq, mq, p->mu, L, gt, gr, gc, gv,
+                                             p->A, p->beta, p->c6, p->rd, ng, p->r_min, p->r_max, p->with_params != 0,
+                                             p->path, p->precision, p->grid_kind);
+    if (st == MQCT_OK) {
+        out->trunc_threshold = p->trunc_threshold;
+        out->trunc_r[0] = p->trunc_r[0];
+        out->trunc_r[1] = p->trunc_r[1];
+    }
+    return st;
 }
 
 extern "C" void mqct_free_desc(mqct_system_desc *d)

@@ -30,6 +30,8 @@ struct DevSys {
     int n, n_levels, L, n_int, n_slices, P;
     int path, precision, flags;
     double mu, r_min, h, inv_h;
+    int grid_log;              // splines in x = ln R (MQCT_GRID_LOG) instead of x = R
+    double x0;                 // first knot in the spline variable (r_min or ln r_min)
     const double *lev_energy;  // [n_levels]
     const float *lev_energy_f; // [n_levels] FP32 copy (mixed-precision systems)
     const int *lev;            // [n]  level of each internal state
@@ -46,8 +48,7 @@ struct DevSys {
     const int *cols;           // [nnz_pad] internal column (padding: row itself, zero coefficients)
     const double2 *T01;        // [n_int][nnz_pad] (c0, c1)
     const double2 *T23;        // [n_int][nnz_pad] (c2, c3)
-    const float2 *T01f;        // FP32 copies (precision != FP64)
-    const float2 *T23f;
+    const float4 *T4f;         // PLAIN + FP32: [n_int][nnz_pad] (c0, c1, c2, c3) of each element
     long long nnz_pad;
     // FACTORISED path: per stored term f (a lambda whose G is not the identity) a sliced-ELL
     // matrix; identity terms are applied directly (id_mask bit lambda).
@@ -171,7 +172,7 @@ mqct_status finish_desc(mqct_system_desc *out, const char *who, const std::vecto
                         const std::vector<int32_t> &mq, double mu, int L, const std::vector<int32_t> &gt,
                         const std::vector<int32_t> &gr, const std::vector<int32_t> &gc, const std::vector<double> &gv,
                         const double *A, const double *beta, double c6, double rd, int ng, double r_min, double r_max,
-                        bool with_params, int path, int precision);
+                        bool with_params, int path, int precision, int grid_kind);
 
 }  // namespace mqct
 

@@ -28,7 +28,7 @@ namespace mqct {
 
 struct Ctl {
     double q[4], qs[4], lacc[4];
-    double phidot, x, dt, r_end;
+    double phidot, x, dinv, dt, r_end;  // dinv: dx/dR of the spline variable (1, or 1/R on the log grid)
     double line_b, line_v, line_t0;  // prescribed straight line (MQCT_PRESCRIBED_TRAJ)
     double e0, j0, ndev, edev, jdev;
     double v[kMaxTerms], dv[kMaxTerms];
@@ -51,12 +51,14 @@ __device__ __forceinline__ void term_at(const DevSys &S, int l, int k, double x,
     dv = c.y + x * (2.0 * c.z + 3.0 * x * c.w);
 }
 
+// interval and local coordinate of R; the spline variable is R, or ln R on the log grid (Sec. III)
 __device__ __forceinline__ void locate(const DevSys &S, double R, int &k, double &x)
 {
-    int kk = (int)floor((R - S.r_min) * S.inv_h);
+    const double X = S.grid_log ? log(R) : R;
+    int kk = (int)floor((X - S.x0) * S.inv_h);
     kk = kk < 0 ? 0 : (kk > S.n_int - 1 ? S.n_int - 1 : kk);
     k = kk;
-    x = R - (S.r_min + kk * S.h);
+    x = X - (S.x0 + kk * S.h);
 }
 
 // prescribed straight line at time t
@@ -71,6 +73,7 @@ __device__ void prepare_stage(const DevSys &S, Ctl &c)
 {
     double R = c.qs[0];
     locate(S, R, c.kint, c.x);
+    c.dinv = S.grid_log ? 1.0 / R : 1.0;
     c.phidot = (S.flags & MQCT_PRESCRIBED_TRAJ) ? c.line_b * c.line_v / (R * R) : c.qs[3] / (S.mu * R * R);
     if (R < S.r_min) c.status |= MQCT_TRAJ_TABLE_RANGE;
     if (S.path == MQCT_PATH_FACTORISED) {
@@ -78,6 +81,7 @@ __device__ void prepare_stage(const DevSys &S, Ctl &c)
         for (int l = 0; l < S.L; ++l) {
             double v, dv;
             term_at(S, l, c.kint, c.x, v, dv);
+            dv *= c.dinv;
             c.v[l] = v;
             c.dv[l] = dv;
             if ((S.id_mask >> l) & 1ull) { vid += v; dvid += dv; }
@@ -114,8 +118,8 @@ __device__ __forceinline__ void coupling_fp64(const DevSys &S, const Ctl &c, con
             }
             w.x = fma(x, fma(x, fma(x, u3.x, u2.x), u1.x), u0.x);
             w.y = fma(x, fma(x, fma(x, u3.y, u2.y), u1.y), u0.y);
-            u.x = fma(x, fma(3.0 * x, u3.x, 2.0 * u2.x), u1.x);
-            u.y = fma(x, fma(3.0 * x, u3.y, 2.0 * u2.y), u1.y);
+            u.x = fma(x, fma(3.0 * x, u3.x, 2.0 * u2.x), u1.x) * c.dinv;
+            u.y = fma(x, fma(3.0 * x, u3.y, 2.0 * u2.y), u1.y) * c.dinv;
         } else {
             const double2 z0 = r < S.n ? C[r] : make_double2(0.0, 0.0);
             w = make_double2(c.vid * z0.x, c.vid * z0.y);
@@ -504,7 +508,10 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
         if (h.path != path || h.precision != prec)
             return fail(MQCT_ERR_INVALID_ARG, "mqct_propagate: systems differ in path or precision");
     }
-    if (prec == MQCT_FP32)
+    // FP32 factorised systems run the persistent batched kernel; FP32 PLAIN systems (large bases
+    // with the FP32 spline table) and BF16X3 systems the stage-synchronous path
+    const bool stage_sync = prec == MQCT_BF16X3 || (prec == MQCT_FP32 && path == MQCT_PATH_PLAIN);
+    if (prec == MQCT_FP32 && !stage_sync)
         for (int i = 0; i < n_systems; ++i) {
             const DevSys &h = systems[i]->s.h;
             if (batched_width(h) == 0) return fail(MQCT_ERR_UNSUPPORTED, "mqct_propagate: basis too large for the batched kernel");
@@ -604,7 +611,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
                                                IsSystem{dtr, i}, st)) != cudaSuccess)
                     return cuda_fail(e, "cub::DeviceSelect");
         }
-        if (prec == MQCT_FP32) {
+        if (!stage_sync) {
             // one persistent launch over every system of the call (at most kBatchMaxSystems per
             // launch): CTAs bind to systems on the device
             BatchMultiArgs ma{};

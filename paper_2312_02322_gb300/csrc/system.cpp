@@ -169,8 +169,20 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     if (d->path != MQCT_PATH_PLAIN && d->path != MQCT_PATH_FACTORISED) return fail(MQCT_ERR_INVALID_ARG, "unknown path");
     if (d->precision != MQCT_FP64 && d->precision != MQCT_FP32 && d->precision != MQCT_BF16X3)
         return fail(MQCT_ERR_INVALID_ARG, "unknown precision");
-    if (d->precision != MQCT_FP64 && d->path != MQCT_PATH_FACTORISED)
-        return fail(MQCT_ERR_UNSUPPORTED, "mixed precision runs on the factorised (batched) path only");
+    if (d->precision == MQCT_BF16X3 && d->path != MQCT_PATH_FACTORISED)
+        return fail(MQCT_ERR_UNSUPPORTED, "MQCT_BF16X3 runs on the factorised path only");
+    if (d->grid_kind != MQCT_GRID_UNIFORM && d->grid_kind != MQCT_GRID_LOG)
+        return fail(MQCT_ERR_INVALID_ARG, "unknown grid_kind");
+    if (d->grid_kind == MQCT_GRID_LOG && !(d->r_min > 0))
+        return fail(MQCT_ERR_INVALID_ARG, "MQCT_GRID_LOG needs r_min > 0");
+    if (d->grid_kind == MQCT_GRID_LOG && d->precision != MQCT_FP64 && d->path == MQCT_PATH_FACTORISED)
+        return fail(MQCT_ERR_UNSUPPORTED, "MQCT_GRID_LOG runs on FP64 systems and on the PLAIN path");
+    if (!std::isfinite(d->trunc_threshold)) return fail(MQCT_ERR_INVALID_ARG, "non-finite trunc_threshold");
+    if (d->trunc_threshold > 0.0) {
+        if (d->path != MQCT_PATH_PLAIN) return fail(MQCT_ERR_UNSUPPORTED, "truncation needs the PLAIN path");
+        if (!(d->trunc_r[0] > 0) || !(d->trunc_r[1] > 0) || !std::isfinite(d->trunc_r[0]) || !std::isfinite(d->trunc_r[1]))
+            return fail(MQCT_ERR_INVALID_ARG, "trunc_r must be finite and > 0");
+    }
     if (d->flags & ~MQCT_PRESCRIBED_TRAJ) return fail(MQCT_ERR_INVALID_ARG, "unknown flags");
     if ((d->flags & MQCT_PRESCRIBED_TRAJ) && d->precision != MQCT_FP64)
         return fail(MQCT_ERR_UNSUPPORTED, "MQCT_PRESCRIBED_TRAJ needs precision MQCT_FP64");
@@ -269,12 +281,16 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     }
 
     // ---- splines of v_lambda and of the parameter derivatives
+    // on the logarithmic grid the spline variable is x = ln R (uniform knots), end slopes R dv/dR
     const int n_int = ng - 1;
-    const double h = (d->r_max - d->r_min) / (ng - 1);
+    const bool glog = d->grid_kind == MQCT_GRID_LOG;
+    const double x0 = glog ? std::log(d->r_min) : d->r_min;
+    const double h = glog ? (std::log(d->r_max) - std::log(d->r_min)) / (ng - 1) : (d->r_max - d->r_min) / (ng - 1);
+    const double e0 = glog ? d->r_min : 1.0, e1 = glog ? d->r_max : 1.0;
     std::vector<std::vector<dbl4>> vc(L);
     std::vector<dbl4> vcoef((size_t)L * n_int);
     for (int l = 0; l < L; ++l) {
-        clamped_spline(ng, h, d->v + (size_t)l * ng, d->dv_ends[2 * l], d->dv_ends[2 * l + 1], vc[l]);
+        clamped_spline(ng, h, d->v + (size_t)l * ng, e0 * d->dv_ends[2 * l], e1 * d->dv_ends[2 * l + 1], vc[l]);
         std::copy(vc[l].begin(), vc[l].end(), vcoef.begin() + (size_t)l * n_int);
     }
     std::vector<dbl4> dvcoef;
@@ -286,7 +302,7 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
                 size_t o = (size_t)p * L + l;
                 for (int k = 0; k < ng; ++k)
                     if (!std::isfinite(d->dv_dparam[o * ng + k])) { delete hs; return fail(MQCT_ERR_INVALID_ARG, "non-finite dv_dparam"); }
-                clamped_spline(ng, h, d->dv_dparam + o * ng, d->ddv_ends[2 * o], d->ddv_ends[2 * o + 1], tmp);
+                clamped_spline(ng, h, d->dv_dparam + o * ng, e0 * d->ddv_ends[2 * o], e1 * d->ddv_ends[2 * o + 1], tmp);
                 std::copy(tmp.begin(), tmp.end(), dvcoef.begin() + o * n_int);
             }
     }
@@ -304,12 +320,51 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     for (int l = 0; l < L; ++l)
         for (auto &row : grows[l]) std::sort(row.begin(), row.end(), [](const Entry &a, const Entry &b) { return a.c < b.c; });
 
+    // ---- truncation (Sec. III): M_rc = sum_l G^l_rc v_l(R) from the splines at the two
+    // reference distances; an element at or below the threshold at both is dropped from every term
+    int64_t n_dropped = 0;
+    if (d->trunc_threshold > 0.0) {
+        double va[2][kMaxTerms];
+        for (int q = 0; q < 2; ++q) {
+            const double R = d->trunc_r[q], X = glog ? std::log(R) : R;
+            int k = (int)std::floor((X - x0) / h);
+            k = std::max(0, std::min(n_int - 1, k));
+            const double x = X - (x0 + k * h);
+            for (int l = 0; l < L; ++l) {
+                const dbl4 &c = vc[l][k];
+                va[q][l] = c.x + x * (c.y + x * (c.z + x * c.w));
+            }
+        }
+        const double thr = d->trunc_threshold;
+        for (int r = 0; r < n; ++r) {
+            std::map<int, std::pair<double, double>> mrow;  // column -> (M(R_a), M(R_b)), terms in order
+            for (int l = 0; l < L; ++l)
+                for (auto &e : grows[l][r]) {
+                    auto &m = mrow[e.c];
+                    m.first += va[0][l] * e.v;
+                    m.second += va[1][l] * e.v;
+                }
+            for (auto &kv : mrow) {
+                if (std::fabs(kv.second.first) > thr || std::fabs(kv.second.second) > thr) continue;
+                ++n_dropped;
+                const int c = kv.first;
+                for (int l = 0; l < L; ++l) {
+                    auto &row = grows[l][r];
+                    row.erase(std::remove_if(row.begin(), row.end(), [c](const Entry &e) { return e.c == c; }), row.end());
+                }
+                if (c == r)
+                    for (int l = 0; l < L; ++l) diag_g[(size_t)l * n + r] = 0.0;
+            }
+        }
+    }
+
     const int n_slices = (n + kSlice - 1) / kSlice;
     DevSys &D = S.h;
     std::memset(&D, 0, sizeof(D));
     D.n = n; D.n_levels = n_levels; D.L = L; D.n_int = n_int; D.n_slices = n_slices; D.P = P;
     D.path = d->path; D.precision = d->precision; D.flags = d->flags;
     D.mu = d->mu; D.r_min = d->r_min; D.h = h; D.inv_h = 1.0 / h;
+    D.grid_log = glog ? 1 : 0; D.x0 = x0;
 
     mqct_status st = MQCT_OK;
     auto up_ = [&](auto &v, auto **dst) { if (st == MQCT_OK) st = upload(S, v, dst); };
@@ -343,6 +398,8 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     S.info.n_blocks = (int)bl.size();
     S.info.max_block = S.max_block;
     S.info.path = d->path;
+    S.info.trunc_dropped = n_dropped;
+    S.info.grid_kind = d->grid_kind;
     S.info.precision = d->precision;
 
     if (d->path == MQCT_PATH_PLAIN) {
@@ -366,7 +423,11 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
                     gv[r][it - rows[r].begin()][l] = e.v;
                 }
         }
-        std::vector<double2> T01(nnz_pad * n_int), T23(nnz_pad * n_int);
+        // FP64 systems: (c0, c1) and (c2, c3) planes; FP32 systems (stage-synchronous sparse path):
+        // one float4 per element and interval
+        const bool f32 = d->precision == MQCT_FP32;
+        std::vector<double2> T01(f32 ? 0 : nnz_pad * n_int), T23(f32 ? 0 : nnz_pad * n_int);
+        std::vector<float4> T4(f32 ? nnz_pad * n_int : 0);
         for (size_t e = 0; e < nnz_pad; ++e) {
             int r = sl.row_of[e], k0 = sl.src[e];
             for (int k = 0; k < n_int; ++k) {
@@ -378,8 +439,12 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
                         const dbl4 &q = vc[l][k];
                         c[0] += g * q.x; c[1] += g * q.y; c[2] += g * q.z; c[3] += g * q.w;
                     }
-                T01[(size_t)k * nnz_pad + e] = make_double2(c[0], c[1]);
-                T23[(size_t)k * nnz_pad + e] = make_double2(c[2], c[3]);
+                if (f32) {
+                    T4[(size_t)k * nnz_pad + e] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
+                } else {
+                    T01[(size_t)k * nnz_pad + e] = make_double2(c[0], c[1]);
+                    T23[(size_t)k * nnz_pad + e] = make_double2(c[2], c[3]);
+                }
             }
         }
         int64_t nnz = 0;
@@ -387,10 +452,17 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
         D.nnz_pad = (long long)nnz_pad;
         up_(sl.off, &D.sl_off);
         up_(sl.cols, &D.cols);
-        up_(T01, &D.T01);
-        up_(T23, &D.T23);
+        if (f32) {
+            up_(T4, &D.T4f);
+            std::vector<float> aupf(aup.begin(), aup.end()), adnf(adn.begin(), adn.end());
+            up_(aupf, &D.aupf);
+            up_(adnf, &D.adnf);
+        } else {
+            up_(T01, &D.T01);
+            up_(T23, &D.T23);
+        }
         S.info.table_nnz = nnz;
-        S.info.table_bytes = (int64_t)nnz_pad * n_int * 32;
+        S.info.table_bytes = (int64_t)nnz_pad * n_int * (f32 ? 16 : 32);
     }
     if (d->path == MQCT_PATH_FACTORISED || P > 0) {
         // identity terms are applied directly; others get one sliced-ELL matrix each (the

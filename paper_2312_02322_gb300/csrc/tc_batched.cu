@@ -70,6 +70,10 @@ struct TcState {
     float2 *part;             // [n_tiles][6][S] per-row-tile partial sums (hi, lo)
     double *Q, *QS, *LACC;    // [4][S] classical state, stage input, RK4 accumulator
     TSlot *slot;              // [S]
+    // PLAIN path (FP32 spline table): each slot's interval, local coordinate and dx/dR
+    int *kint;                // [S]
+    float *xs, *dinv;         // [S]
+    int plain;
 };
 
 __device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -103,27 +107,25 @@ __device__ __forceinline__ void tc_elem_gather(const TcState &T, const DevSys &S
     in.acc = T.ACC[e];
 }
 
-// the update of one element from w = M c and u = M' c (Eq. 5, RK4) and its gathered inputs;
-// adds its force, torque and (stage 0) diagnostic contributions to part[6] (FP32: a thread sums
-// a few rows; the sums across threads, row tiles and the classical update are FP64 -- the FP64
-// pipe of this GPU is far too narrow for per-element FP64 arithmetic)
-__device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S, int s, int cur, int r, int sl,
-                                              int st, const ElemIn &in, float2 w, float2 u, float *part)
+// the update of one element from w = M c and u = M' c (Eq. 5, RK4) and its inputs; adds its force,
+// torque and (stage 0) diagnostic contributions to part[6] (FP32: a thread sums a few rows; the
+// sums across threads, row tiles and the classical update are FP64 -- the FP64 pipe of this GPU is
+// far too narrow for per-element FP64 arithmetic).  Returns what the caller stores: 0 nothing,
+// 1 ACC and the next stage input C', 2 A, ACC and C', 3 the final amplitude a0 (a FINAL slot at
+// stage 0).  A slot waiting for its first step (WAIT, stage 3) gets e_s0 (is_s0), zero, e_s0.
+__device__ __forceinline__ int elem_core(int s, int st, bool is_s0, float2 c, float2 cu, float2 cd, float2 p,
+                                         float2 q, float2 a0, float2 acc, float au, float ad, float elev, float hp,
+                                         float dtj, float2 w, float2 u, float *part, float2 &a_out,
+                                         float2 &acc_out, float2 &c_out)
 {
-    const int nxt = cur ^ 1;
-    const size_t e = (size_t)r * T.S + sl;
     if (st == TS_WAIT && s == 3) {
-        const float2 v = make_float2(r == T.slot[sl].s0 ? 1.0f : 0.0f, 0.0f);
-        T.A[e] = v;
-        T.ACC[e] = make_float2(0.f, 0.f);
-        T.C[nxt][e] = v;
-        return;
+        a_out = c_out = make_float2(is_s0 ? 1.0f : 0.0f, 0.0f);
+        acc_out = make_float2(0.f, 0.f);
+        return 2;
     }
-    if (st != TS_ACTIVE && st != TS_FINAL) return;
-    const float2 c = in.c, p = in.p, a0 = in.a0;
-    const float2 dc = make_float2(in.ad * in.cd.x - in.au * in.cu.x, in.ad * in.cd.y - in.au * in.cu.y);
+    if (st != TS_ACTIVE && st != TS_FINAL) return 0;
+    const float2 dc = make_float2(ad * cd.x - au * cu.x, ad * cd.y - au * cu.y);
     const float2 da = make_float2(p.x * dc.x + p.y * dc.y, p.x * dc.y - p.y * dc.x);
-    const float hp = T.hp[sl];
     float2 kk;
     kk.x = fmaf(hp, da.x, p.x * w.y - p.y * w.x);
     kk.y = fmaf(hp, da.y, -(p.x * w.x + p.y * w.y));
@@ -133,19 +135,13 @@ __device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S,
         const float pp = a0.x * a0.x + a0.y * a0.y;
         part[2] += c.x * w.x + c.y * w.y;
         part[3] += pp;
-        part[4] += S.lev_energy_f[in.lev] * pp;
+        part[4] += elev * pp;
         part[5] += a0.x * da.y - a0.y * da.x;
     }
     if (st == TS_FINAL) {
-        if (s == 0) {
-            const size_t oo = (size_t)T.slot[sl].traj * T.nmax + S.perm[r];
-            if (T.pop) T.pop[oo] = (double)(a0.x * a0.x + a0.y * a0.y);
-            if (T.amp) { T.amp[2 * oo] = a0.x; T.amp[2 * oo + 1] = a0.y; }
-        }
-        return;
+        a_out = a0;
+        return s == 0 ? 3 : 0;
     }
-    const float dtj = T.dtf[sl];
-    float2 acc = in.acc;
     if (s == 0) {
         acc = make_float2(kk.x + acc.x, kk.y + acc.y);  // acc holds the last rounding error
     } else {
@@ -153,7 +149,6 @@ __device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S,
         acc.x = fmaf(wg, kk.x, acc.x);
         acc.y = fmaf(wg, kk.y, acc.y);
     }
-    const float2 q = in.q;
     if (s == 3) {
         // compensated a + (dt/6) acc (two-sum); the rounding error goes to the accumulator
         const float h6 = dtj * (1.0f / 6.0f), ih6 = 6.0f / dtj;
@@ -162,15 +157,48 @@ __device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S,
         const float bx = __fsub_rn(sx, a0.x), by = __fsub_rn(sy, a0.y);
         const float ex = __fadd_rn(__fsub_rn(a0.x, __fsub_rn(sx, bx)), __fsub_rn(ix, bx));
         const float ey = __fadd_rn(__fsub_rn(a0.y, __fsub_rn(sy, by)), __fsub_rn(iy, by));
-        T.A[e] = make_float2(sx, sy);
-        T.ACC[e] = make_float2(ex * ih6, ey * ih6);
-        T.C[nxt][e] = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
-    } else {
-        T.ACC[e] = acc;
-        const float bn = s == 2 ? dtj : 0.5f * dtj;
-        const float2 yn = make_float2(fmaf(bn, kk.x, a0.x), fmaf(bn, kk.y, a0.y));
-        T.C[nxt][e] = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
+        a_out = make_float2(sx, sy);
+        acc_out = make_float2(ex * ih6, ey * ih6);
+        c_out = make_float2(q.x * sx - q.y * sy, q.x * sy + q.y * sx);
+        return 2;
     }
+    acc_out = acc;
+    const float bn = s == 2 ? dtj : 0.5f * dtj;
+    const float2 yn = make_float2(fmaf(bn, kk.x, a0.x), fmaf(bn, kk.y, a0.y));
+    c_out = make_float2(q.x * yn.x - q.y * yn.y, q.x * yn.y + q.y * yn.x);
+    return 1;
+}
+
+// stores of one element's update (elem_core's return value); a FINAL slot's populations and
+// amplitudes go to the caller's arrays in the caller's state order
+__device__ __forceinline__ void elem_store(const TcState &T, const DevSys &S, int cur, int r, int sl, int mode,
+                                           float2 a, float2 acc, float2 c)
+{
+    const size_t e = (size_t)r * T.S + sl;
+    if (mode == 1) {
+        T.ACC[e] = acc;
+        T.C[cur ^ 1][e] = c;
+    } else if (mode == 2) {
+        T.A[e] = a;
+        T.ACC[e] = acc;
+        T.C[cur ^ 1][e] = c;
+    } else if (mode == 3) {
+        const size_t oo = (size_t)T.slot[sl].traj * T.nmax + S.perm[r];
+        if (T.pop) T.pop[oo] = (double)(a.x * a.x + a.y * a.y);
+        if (T.amp) { T.amp[2 * oo] = a.x; T.amp[2 * oo + 1] = a.y; }
+    }
+}
+
+__device__ __forceinline__ void tc_elem_apply(const TcState &T, const DevSys &S, int s, int cur, int r, int sl,
+                                              int st, const ElemIn &in, float2 w, float2 u, float *part)
+{
+    if (st == TS_IDLE) return;
+    const bool is_s0 = st == TS_WAIT && s == 3 && r == T.slot[sl].s0;
+    const float elev = (st == TS_ACTIVE || st == TS_FINAL) && s == 0 ? S.lev_energy_f[in.lev] : 0.f;
+    float2 a, acc, c;
+    const int mode = elem_core(s, st, is_s0, in.c, in.cu, in.cd, in.p, in.q, in.a0, in.acc, in.au, in.ad, elev,
+                               T.hp[sl], T.dtf[sl], w, u, part, a, acc, c);
+    elem_store(T, S, cur, r, sl, mode, a, acc, c);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -414,6 +442,112 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
 }
 
 // ---------------------------------------------------------------------------------------------
+// one RK4 stage of every element on the PLAIN path with FP32 spline tables (bases too large for
+// shared memory, Sec. III): one CTA per (block of 256 rows, tile of 32 consecutive slots); lane =
+// slot, each warp takes one 32-row slice row by row.  Per element of a row's sliced-ELL list the
+// column index is one broadcast load, the amplitudes of the 32 slots one 256-byte load, and the
+// float4 (c0..c3) of each lane's interval a gather that lanes in the same interval share:
+//   w = sum_c M_rc(x) C_c,   u = (dx/dR) sum_c M'_rc(x) C_c,
+// then the element update of Eq. 5 and RK4 (every load coalesced over the slots) and the per-slot
+// partial sums of force, torque and diagnostics over the 256 rows (compensated FP32 across warps).
+constexpr int kSpWarps = 8, kSpTile = 32;
+
+__global__ void __launch_bounds__(32 * kSpWarps, 4) k_sp_stage(TcState T, int s, int cur)
+{
+    const DevSys &S = *T.sys;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sl = blockIdx.x * kSpTile + lane, rb = blockIdx.y;
+    const int slice = rb * kSpWarps + warp;
+    __shared__ float red[kSpWarps][6][kSpTile];
+    __shared__ int any_;
+    const int st = T.state[sl];
+    if (threadIdx.x == 0) any_ = 0;
+    __syncthreads();
+    if (warp == 0 && __any_sync(0xffffffffu, st != TS_IDLE) && lane == 0) any_ = 1;
+    __syncthreads();
+    float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (any_ && slice < S.n_slices) {
+        const bool need = st == TS_ACTIVE || (st == TS_FINAL && s == 0);
+        const int kint = need ? T.kint[sl] : 0;
+        const float x = T.xs[sl], dv = T.dinv[sl], hp = T.hp[sl], dtj = T.dtf[sl];
+        const int row0 = st == TS_WAIT ? T.slot[sl].s0 : -1;
+        const float4 *tab = S.T4f + (size_t)kint * S.nnz_pad;
+        const float2 *Cc = T.C[cur];
+        const float2 *PHc = (s == 0 || s == 3) ? T.PHa : T.PHb;
+        const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
+        const int off = S.sl_off[slice], width = (S.sl_off[slice + 1] - off) / kSlice;
+        const int r_end = min(S.n, (slice + 1) * kSlice);
+        for (int r = slice * kSlice; r < r_end; ++r) {
+            const int rl = r - slice * kSlice;
+            float2 w = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
+            if (need) {
+                int e = 0;
+                for (; e + 4 <= width; e += 4) {
+                    int col[4];
+                    float4 c[4];
+                    float2 z[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const size_t ei = (size_t)off + (size_t)(e + i) * kSlice + rl;
+                        col[i] = __ldg(S.cols + ei);
+                        c[i] = __ldg(tab + ei);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) z[i] = __ldg(Cc + (size_t)col[i] * T.S + sl);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float m = fmaf(fmaf(fmaf(c[i].w, x, c[i].z), x, c[i].y), x, c[i].x);
+                        const float md = fmaf(fmaf(3.0f * c[i].w, x, 2.0f * c[i].z), x, c[i].y);
+                        w.x = fmaf(m, z[i].x, w.x);
+                        w.y = fmaf(m, z[i].y, w.y);
+                        u.x = fmaf(md, z[i].x, u.x);
+                        u.y = fmaf(md, z[i].y, u.y);
+                    }
+                }
+                for (; e < width; ++e) {
+                    const size_t ei = (size_t)off + (size_t)e * kSlice + rl;
+                    const float4 c = __ldg(tab + ei);
+                    const float2 z = __ldg(Cc + (size_t)__ldg(S.cols + ei) * T.S + sl);
+                    const float m = fmaf(fmaf(fmaf(c.w, x, c.z), x, c.y), x, c.x);
+                    const float md = fmaf(fmaf(3.0f * c.w, x, 2.0f * c.z), x, c.y);
+                    w.x = fmaf(m, z.x, w.x);
+                    w.y = fmaf(m, z.y, w.y);
+                    u.x = fmaf(md, z.x, u.x);
+                    u.y = fmaf(md, z.y, u.y);
+                }
+            }
+            if (st == TS_IDLE) continue;
+            const int lev = __ldg(S.lev + r);
+            const size_t e0 = (size_t)r * T.S + sl;
+            const float2 c = __ldg(Cc + e0);
+            const float2 cu = __ldg(Cc + (size_t)__ldg(S.up + r) * T.S + sl);
+            const float2 cd = __ldg(Cc + (size_t)__ldg(S.dn + r) * T.S + sl);
+            const float2 p = __ldg(PHc + (size_t)lev * T.S + sl), q = __ldg(PHn + (size_t)lev * T.S + sl);
+            const float2 a0 = T.A[e0], acc = T.ACC[e0];
+            const float au = __ldg(S.aupf + r), ad = __ldg(S.adnf + r), elev = S.lev_energy_f[lev];
+            const float2 uu = make_float2(u.x * dv, u.y * dv);
+            float2 ao, acco, co;
+            const int mode = elem_core(s, st, r == row0, c, cu, cd, p, q, a0, acc, au, ad, elev, hp, dtj, w, uu, part,
+                                       ao, acco, co);
+            elem_store(T, S, cur, r, sl, mode, ao, acco, co);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) red[warp][k][lane] = part[k];
+    __syncthreads();
+    if (threadIdx.x < 6 * kSpTile) {
+        const int k = threadIdx.x / kSpTile, j = threadIdx.x % kSpTile;
+        float hi = 0.f, lo = 0.f;
+        for (int g = 0; g < kSpWarps; ++g) {
+            float e2;
+            two_sum(hi, red[g][k][j], hi, e2);
+            lo += e2;
+        }
+        T.part[((size_t)rb * 6 + k) * T.S + blockIdx.x * kSpTile + j] = make_float2(hi, lo);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // per-slot work: one warp per eight slots, lane 8 c + j carries component c of (R, P_R, Phi, P_Phi)
 // of slot j, so one FP64 instruction advances four components of eight trajectories; every lane
 // of the warp runs the same instructions (lanes of slots >= S compute on copies and store nothing)
@@ -499,6 +633,17 @@ __device__ int tc_next_stage(const TcState &T, const DevSys &S, const SlotLane &
     ir = 1.0 / R;
     i2m = T.inv_mu * ir * ir;
     phid = PP * i2m;
+    if (T.plain) {
+        // the element tables are evaluated by the stage kernel at (interval, x); derivatives carry
+        // dx/dR (1/R on the logarithmic grid)
+        if (publish && L.sc == 0) {
+            T.kint[L.sl] = k;
+            T.xs[L.sl] = (float)x;
+            T.dinv[L.sl] = S.grid_log ? (float)ir : 1.0f;
+            T.hp[L.sl] = (float)phid * 0.5f;
+        }
+        return below ? MQCT_TRAJ_TABLE_RANGE : 0;
+    }
     const float xf = (float)x;
     float v0 = 0.f, d0 = 0.f;
     for (int l = L.sc; l < S.L; l += 4) {
@@ -526,6 +671,16 @@ __device__ int tc_next_stage(const TcState &T, const DevSys &S, const SlotLane &
 // an idle slot's published views
 __device__ void tc_publish_idle(const TcState &T, const DevSys &S, const SlotLane &L)
 {
+    if (T.plain) {
+        if (L.sc == 0) {
+            T.kint[L.sl] = 0;
+            T.xs[L.sl] = 0.f;
+            T.dinv[L.sl] = 0.f;
+            T.hp[L.sl] = 0.f;
+            T.dtf[L.sl] = 1.f;
+        }
+        return;
+    }
     for (int l = L.sc; l < S.L; l += 4) T.coef[(size_t)l * T.S + L.sl] = T.coef[((size_t)S.L + l) * T.S + L.sl] = 0.f;
     if (L.sc == 0) {
         T.vid[L.sl] = T.vid[T.S + L.sl] = 0.f;
@@ -768,8 +923,16 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     }
     if (a.tc_slots > 0) n_slot_tiles = (a.tc_slots + kTcSlotsPerTile - 1) / kTcSlotsPerTile;
     n_slot_tiles = std::max(1, std::min(n_slot_tiles, 8192 / kTcSlotsPerTile));
-    const int S = n_slot_tiles * kTcSlotsPerTile;
-    const int n_rowblocks = std::max(1, h.n_tiles);
+    int S = n_slot_tiles * kTcSlotsPerTile;
+    int n_rowblocks = std::max(1, h.n_tiles);
+    const bool plain = h.path == MQCT_PATH_PLAIN;
+    if (plain) {
+        // PLAIN path: every trajectory in a slot at once up to 4096 slots (tiles of 32 slots; the
+        // stage kernel's CTAs are (256-row block, 32-slot tile)); a.tc_slots overrides (rounded to 32)
+        S = a.tc_slots > 0 ? a.tc_slots : std::min(a.n, 4096);
+        S = std::max(kSpTile, std::min(8192, (S + kSpTile - 1) / kSpTile * kSpTile));
+        n_rowblocks = (h.n_slices + kSpWarps - 1) / kSpWarps;
+    }
     std::vector<void *> tmp;
     cudaError_t e = cudaSuccess;
     auto get = [&](void **p, size_t b) {
@@ -784,6 +947,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     T.pop = a.pop; T.amp = a.amp; T.diag = a.diag; T.nmax = a.nmax; T.sys_idx = a.sys_idx;
     T.t_start = a.t_start; T.t_done = a.t_done;
     T.inv_mu = 1.0 / h.mu;
+    T.plain = plain ? 1 : 0;
     const size_t ns = (size_t)n * S;
     get((void **)&T.live, 4 * sizeof(int));
     get((void **)&T.C[0], sizeof(float2) * ns);
@@ -803,12 +967,18 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     get((void **)&T.QS, sizeof(double) * 4 * (size_t)S);
     get((void **)&T.LACC, sizeof(double) * 4 * (size_t)S);
     get((void **)&T.slot, sizeof(TSlot) * (size_t)S);
+    if (plain) {
+        get((void **)&T.kint, sizeof(int) * (size_t)S);
+        get((void **)&T.xs, sizeof(float) * (size_t)S);
+        get((void **)&T.dinv, sizeof(float) * (size_t)S);
+    }
     if (e != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "cudaMallocAsync (tensor-core path scratch)");
     }
     const size_t smem = kTcSmemFixed + sizeof(float) * 2 * kTcSlotsPerTile * (size_t)h.n_f;
-    if ((e = cudaFuncSetAttribute(k_tc_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+    if (!plain &&
+        (e = cudaFuncSetAttribute(k_tc_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "cudaFuncSetAttribute");
     }
@@ -816,6 +986,11 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     const int slot_blocks = (S / 8 + 3) / 4;  // four warps of eight slots per block
     k_tc_init<<<slot_blocks, 128, 0, st>>>(T);
     const int n_ct = S / kTcSlotsPerTile;
+    // the stage kernel: tcgen05 contraction (factorised BF16X3) or the sparse FP32 table (PLAIN)
+    auto stage = [&](cudaStream_t q, int s, int cur) {
+        if (plain) k_sp_stage<<<dim3(S / kSpTile, n_rowblocks), 32 * kSpWarps, 0, q>>>(T, s, cur);
+        else k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, q>>>(T, s, cur);
+    };
     // chunks of steps inside a WHILE node: the body (one chunk) ends with k_tc_continue, which
     // sets the condition from the live-slot count; one launch of the graph runs every trajectory
     const int chunk = 4;
@@ -834,7 +1009,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         for (int k = 0; k < chunk; ++k)
             for (int s = 0; s < 4; ++s) {
                 const int cur = s & 1;
-                k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, st>>>(T, s, cur);
+                stage(st, s, cur);
                 k_tc_slots<<<slot_blocks, 128, 0, st>>>(T, s, n_rowblocks);
             }
         k_tc_continue<<<1, 32, 0, st>>>(T, 0);
@@ -861,7 +1036,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
         for (int k = 0; k < chunk; ++k)
             for (int s = 0; s < 4; ++s) {
                 const int cur = s & 1;
-                k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, cap>>>(T, s, cur);
+                stage(cap, s, cur);
                 k_tc_slots<<<slot_blocks, 128, 0, cap>>>(T, s, n_rowblocks);
             }
         k_tc_continue<<<1, 32, 0, cap>>>(T, cond);

@@ -36,14 +36,16 @@ __device__ __forceinline__ float2 phase_factor(unsigned long long inc, unsigned 
     return make_float2(c, -s);
 }
 
-// ---- spline interval of R on the uniform grid (Sec. III): k = floor((R - r_min)/h) clamped,
-// x = R - R_k; *below is set when R < r_min (the end cubic is extrapolated)
+// ---- spline interval of R (Sec. III): the spline variable X is R, or ln R on the logarithmic
+// grid; k = floor((X - X_0)/h) clamped, x = X - X_k; *below is set when R < r_min (the end cubic
+// is extrapolated)
 __device__ __forceinline__ void locate_interval(const DevSys &S, double R, int &k, double &x, bool &below)
 {
-    const int kr = __double2int_rd((R - S.r_min) * S.inv_h);
+    const double X = S.grid_log ? log(R) : R;
+    const int kr = __double2int_rd((X - S.x0) * S.inv_h);
     below = kr < 0;
     k = kr < 0 ? 0 : (kr > S.n_int - 1 ? S.n_int - 1 : kr);
-    x = R - (S.r_min + k * S.h);
+    x = X - (S.x0 + k * S.h);
 }
 
 // a trajectory that lives in device memory was not seen by the host: validate it here

@@ -250,3 +250,24 @@ def test_struct_layouts_match_header(L, tmp_path):
     assert int(out["mqct_diag"]) == api.DIAG_DTYPE.itemsize
     for f in api.DIAG_DTYPE.names:
         assert int(out[f"mqct_diag.{f}"]) == api.DIAG_DTYPE.fields[f][1], f
+
+
+@pytest.mark.parametrize("path,prec,grid,thr,status,needle", [
+    ("plain", api.FP64, 2, 0.0, api.ERR_INVALID_ARG, b"grid_kind"),
+    ("factorised", api.FP32, api.GRID_LOG, 0.0, api.ERR_UNSUPPORTED, b"GRID_LOG"),
+    ("factorised", api.BF16X3, api.GRID_LOG, 0.0, api.ERR_UNSUPPORTED, b"GRID_LOG"),
+    ("factorised", api.FP64, api.GRID_UNIFORM, 1e-5, api.ERR_UNSUPPORTED, b"truncation"),
+    ("plain", api.FP64, api.GRID_UNIFORM, float("nan"), api.ERR_INVALID_ARG, b"trunc_threshold"),
+])
+def test_grid_and_truncation_validation(L, path, prec, grid, thr, status, needle):
+    """The logarithmic grid and the truncation (Sec. III) are rejected where no kernel runs them."""
+    d, _ = build_desc(2, path=path)
+    d.precision = prec
+    d.grid_kind = grid
+    d.trunc_threshold = thr
+    d.trunc_r[0], d.trunc_r[1] = 6.03, 7.11
+    h = C.c_void_p()
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == status
+    assert needle in L.mqct_last_error()
+    assert not h.value
+    api.lib().mqct_free_desc(C.byref(d))
