@@ -36,6 +36,7 @@ F_PRESCRIBED = 2
 F_FLIP_JY = 4
 F_PLANT_TORQUE = 8      # planted mistake: torque sign reversed alone
 F_PLANT_CORIOLIS = 16   # planted mistake: Coriolis factor 1/2 dropped
+F_DECOUPLED = 32        # classical motion in the isotropic potential alone (AT-MQCT decoupling)
 
 
 def build(force: bool = False) -> str:

@@ -69,6 +69,10 @@
 /* planted mistakes, used only by the tests that show the conservation pins catch them */
 #define ORA_F_PLANT_TORQUE 8     /* reverse the sign of the torque alone          */
 #define ORA_F_PLANT_CORIOLIS 16  /* drop the factor 1/2 of the Coriolis term      */
+/* decoupled classical motion (the AT-MQCT decoupling of Sec. III, in the reading of the design
+ * notes): R, Phi move in the isotropic potential v_0(R) alone (term 0, whose G must be the
+ * identity) with no torque; the amplitudes follow Eq. 5 along that trajectory */
+#define ORA_F_DECOUPLED 32
 
 /* ------------------------------------------------------------------ */
 /* Clebsch-Gordan coefficients: Racah's closed formula, long double.  */
@@ -605,6 +609,7 @@ typedef struct {
     double jy;   /* <J_y> = Im(a^dag D a)/2 */
     double norm; /* sum |a|^2 */
     double erot; /* sum E |a|^2 */
+    double viso; /* v_0(R) (decoupled mode) */
     int below;   /* R < r_min */
 } ora_eval;
 
@@ -629,6 +634,11 @@ static void rhs(const ora_sys *S, const ora_opts *o, double t, const double comp
     for (int s = 0; s < n; ++s) {
         force -= creal(conj(W->c[s]) * W->u[s]);
         torque += creal(conj(W->c[s]) * ladder(S, W->w, s));
+    }
+    if (o->flags & ORA_F_DECOUPLED) {
+        /* no back-reaction of the amplitudes: the isotropic potential alone, no torque */
+        force = -W->dv[0];
+        torque = 0.0;
     }
     force += PPhi * PPhi / (S->mu * R * R * R);
     torque *= o->jy_sign;
@@ -657,14 +667,23 @@ static void rhs(const ora_sys *S, const ora_opts *o, double t, const double comp
         ev->jy = 0.5 * o->jy_sign * jy;
         ev->norm = nrm;
         ev->erot = er;
+        ev->viso = W->v[0];
         ev->below = R < S->r_min;
     }
 }
 
-static double total_energy(const ora_sys *S, const double *q, const ora_eval *ev)
+static double total_energy(const ora_sys *S, const ora_opts *o, const double *q, const ora_eval *ev)
 {
     double R = q[0];
+    if (o->flags & ORA_F_DECOUPLED)  /* the classical energy, conserved on its own */
+        return q[1] * q[1] / (2.0 * S->mu) + q[3] * q[3] / (2.0 * S->mu * R * R) + ev->viso;
     return q[1] * q[1] / (2.0 * S->mu) + q[3] * q[3] / (2.0 * S->mu * R * R) + ev->erot + ev->vc;
+}
+
+/* the conserved angular momentum: P_Phi + <J_y>, or P_Phi alone with decoupled motion */
+static double total_angmom(const ora_opts *o, const double *q, const ora_eval *ev)
+{
+    return (o->flags & ORA_F_DECOUPLED) ? q[3] : q[3] + ev->jy;
 }
 
 static int finite_state(int n, const double complex *a, const double *q)
@@ -676,7 +695,8 @@ static int finite_state(int n, const double complex *a, const double *q)
     return 1;
 }
 
-static void initial_state(const ora_sys *S, const ora_traj *tr, double complex *a, double *q, double *m00_out)
+static void initial_state(const ora_sys *S, const ora_traj *tr, int decoupled, double complex *a, double *q,
+                          double *m00_out)
 {
     for (int s = 0; s < S->n; ++s) a[s] = 0.0;
     a[tr->init_state] = 1.0;
@@ -689,7 +709,9 @@ static void initial_state(const ora_sys *S, const ora_traj *tr, double complex *
             if (S->members[S->blk_start[q2] + i] == s0) { b = q2; r = i; }
     int sz = S->blk_size[b];
     double m00 = 0.0;
-    if (kept(S, b, r, r))
+    if (decoupled)
+        m00 = pv[0];  /* the isotropic potential: the classical motion does not see the state */
+    else if (kept(S, b, r, r))
         for (int l = 0; l < S->L; ++l) m00 += pv[l] * S->Gb[S->blk_goff[b] + ((size_t)l * sz + r) * sz + r];
     free(pv);
     double lz = tr->b * sqrt(2.0 * S->mu * tr->e_coll);
@@ -708,7 +730,7 @@ static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o
     if (!a || work_alloc(&W, n, S->L)) { free(a); work_free(&W); return ORA_ENOMEM; }
     double complex *k1 = a + n, *k2 = a + 2 * n, *k3 = a + 3 * n, *k4 = a + 4 * n, *ys = a + 5 * n;
     double q[4], qs[4], l1[4], l2[4], l3[4], l4[4];
-    initial_state(S, tr, a, q, NULL);
+    initial_state(S, tr, (o->flags & ORA_F_DECOUPLED) != 0, a, q, NULL);
     if (o->flags & ORA_F_PRESCRIBED) {
         double s = o->line_v * (0.0 - o->line_t0);
         q[0] = sqrt(o->line_b * o->line_b + s * s);
@@ -722,7 +744,7 @@ static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o
         rhs(S, o, t, a, q, k1, l1, &W, &ev);
         if (ev.below) status |= ORA_ST_TABLE_RANGE;
         {
-            double et = total_energy(S, q, &ev), jt = q[3] + ev.jy;
+            double et = total_energy(S, o, q, &ev), jt = total_angmom(o, q, &ev);
             if (step == 0) { e0 = et; j0 = jt; }
             if (fabs(ev.norm - 1.0) > ndev) ndev = fabs(ev.norm - 1.0);
             if (fabs(et - e0) > edev) edev = fabs(et - e0);
@@ -754,7 +776,7 @@ static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o
     if (!(status & ORA_ST_NONFINITE)) {
         /* diagnostics of the final state */
         rhs(S, o, steps * dt, a, q, k1, l1, &W, &ev);
-        double et = total_energy(S, q, &ev), jt = q[3] + ev.jy;
+        double et = total_energy(S, o, q, &ev), jt = total_angmom(o, q, &ev);
         if (steps == 0) { e0 = et; j0 = jt; }
         if (fabs(ev.norm - 1.0) > ndev) ndev = fabs(ev.norm - 1.0);
         if (fabs(et - e0) > edev) edev = fabs(et - e0);
@@ -819,6 +841,18 @@ int ora_propagate(const ora_system_desc *d, const ora_traj *tr, int n_traj, int 
             sys_free(&S);
             return ORA_EINVAL;
         }
+    if ((flags & ORA_F_DECOUPLED) && (flags & ORA_F_PRESCRIBED)) { sys_free(&S); return ORA_EINVAL; }
+    if (flags & ORA_F_DECOUPLED) {
+        /* term 0 must be the isotropic term: G^0 = identity (to the rounding of its construction) */
+        for (int b = 0; b < S.n_blk; ++b) {
+            int sz = S.blk_size[b];
+            for (int r = 0; r < sz; ++r)
+                for (int c = 0; c < sz; ++c) {
+                    double g = S.Gb[S.blk_goff[b] + (size_t)r * sz + c];
+                    if (fabs(g - (r == c ? 1.0 : 0.0)) > 1e-13) { sys_free(&S); return ORA_EINVAL; }
+                }
+        }
+    }
     int err = 0;
 #ifdef _OPENMP
     if (n_threads < 1) n_threads = omp_get_max_threads();
@@ -907,7 +941,7 @@ static int tangent_one(const ora_sys *S, const ora_traj *tr, double complex *a_o
     double *tq = tqbuf, *tl = tqbuf + 4 * P, *tqs = tqbuf + 20 * P; /* tq[P][4], tl[4][P][4], tqs[P][4] */
     double q[4], qs[4], l[4][4];
     double m00;
-    initial_state(S, tr, a, q, &m00);
+    initial_state(S, tr, 0, a, q, &m00);
     /* tangent of the initial state: only P_R depends on theta through M_s0s0(R0) */
     memset(ta, 0, sizeof(double complex) * (size_t)P * na);
     memset(tq, 0, sizeof(double) * 4 * P);
