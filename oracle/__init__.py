@@ -58,7 +58,7 @@ class _Desc(C.Structure):
         ("n_params", C.c_int), ("dvp", C.c_void_p), ("dvp_ends", C.c_void_p),
         ("grid_log", C.c_int), ("trunc_thr", C.c_double), ("trunc_r", C.c_double * 2),
         ("g_nnz", C.c_longlong), ("g_term", C.c_void_p), ("g_row", C.c_void_p), ("g_col", C.c_void_p),
-        ("g_val", C.c_void_p),
+        ("g_val", C.c_void_p), ("adapt_tol", C.c_double), ("adapt_hmax_factor", C.c_int),
     ]
 
 
@@ -116,11 +116,12 @@ class System:
     large bases, a tuple of triplet arrays (term, row, col, value) with n_terms L;
     v[L][n_grid] and dv_ends[L][2] (dv/dR) define the clamped splines of v_lambda(R) --
     in ln R on a logarithmic grid when grid_log (Sec. III).  trunc = (threshold, R_a, R_b)
-    drops every M_rc with |M_rc| <= threshold at both R_a and R_b (Sec. III).
+    drops every M_rc with |M_rc| <= threshold at both R_a and R_b (Sec. III).  adapt = (tol,
+    hmax_factor) switches on the step-doubling step control (steps between dt and hmax_factor dt).
     """
 
     def __init__(self, energy, level, jq, mq, G, v, dv_ends, mu, r_min, r_max, dvp=None, dvp_ends=None,
-                 grid_log=False, trunc=None, n_terms=None):
+                 grid_log=False, trunc=None, n_terms=None, adapt=None):
         self.energy = np.ascontiguousarray(energy, np.float64)
         self.level = np.ascontiguousarray(level, np.int32)
         self.jq = np.ascontiguousarray(jq, np.int32)
@@ -137,6 +138,7 @@ class System:
         self.n = self.energy.shape[0]
         self.L = self.G.shape[0] if self.G is not None else int(n_terms if n_terms is not None else self.v.shape[0])
         self.grid_log = bool(grid_log)
+        self.adapt = None if adapt is None else (float(adapt[0]), int(adapt[1]))
         self.trunc = None if trunc is None else tuple(float(x) for x in trunc)
         self.n_grid = self.v.shape[1]
         self.n_levels = int(self.level.max()) + 1
@@ -156,6 +158,8 @@ class System:
             d.g_nnz = self.trip[0].shape[0]
             d.g_term, d.g_row, d.g_col, d.g_val = (_p(a) for a in self.trip)
         d.grid_log = 1 if self.grid_log else 0
+        if self.adapt is not None:
+            d.adapt_tol, d.adapt_hmax_factor = self.adapt
         if self.trunc is not None:
             d.trunc_thr = self.trunc[0]
             d.trunc_r[0], d.trunc_r[1] = self.trunc[1], self.trunc[2]
@@ -229,7 +233,7 @@ def diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params=False, grid_lo
 
 
 def diatom_system(jmax, bconst, mu, A, beta, c6, rd, n_grid, r_min, r_max, with_params=False, grid_log=False,
-                  trunc=None, sparse=None) -> System:
+                  trunc=None, sparse=None, adapt=None) -> System:
     """Atom + linear rotor (Eq. 2 basis, Eq. 15 coupling, PES of the form used in the tests);
     sparse (default: N > 2000) passes G as triplets."""
     e, lev, jq, mq = diatom_basis(jmax, bconst)
@@ -245,7 +249,7 @@ def diatom_system(jmax, bconst, mu, A, beta, c6, rd, n_grid, r_min, r_max, with_
         G = np.stack([diatom_G(jmax, l) for l in range(L)])
     v, ends, dvp, dvpe = diatom_pes(A, beta, c6, rd, n_grid, r_min, r_max, with_params, grid_log)
     return System(e, lev, jq, mq, G, v, ends, mu, r_min, r_max, dvp, dvpe, grid_log=grid_log, trunc=trunc,
-                  n_terms=L)
+                  n_terms=L, adapt=adapt)
 
 
 def asym_levels(J: int, A: float, B: float, Cc: float):

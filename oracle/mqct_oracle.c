@@ -319,6 +319,10 @@ typedef struct {
     long long g_nnz;
     const int *g_term, *g_row, *g_col;
     const double *g_val;
+    /* adaptive step control: adapt_tol > 0 switches it on; the largest step is adapt_hmax_factor x
+       the trajectory's dt (16 when 0) and the smallest is dt */
+    double adapt_tol;
+    int adapt_hmax_factor;
 } ora_system_desc;
 
 typedef struct {
@@ -601,6 +605,8 @@ typedef struct {
     int flags;
     double jy_sign; /* +1, or -1 with ORA_F_FLIP_JY */
     double line_b, line_v, line_t0; /* prescribed straight line (ORA_F_PRESCRIBED) */
+    double tol;                     /* > 0: adaptive step control (step doubling), else fixed dt */
+    double hmax_factor;             /* largest adaptive step / dt                                */
 } ora_opts;
 
 /* quantities of a right-hand-side evaluation, for the diagnostics */
@@ -722,60 +728,106 @@ static void initial_state(const ora_sys *S, const ora_traj *tr, int decoupled, d
     if (m00_out) *m00_out = m00;
 }
 
+/* one RK4 step of length h from (t, a, q); ev receives the evaluation at the start of the step;
+ * returns the TABLE_RANGE bit of its four evaluations */
+static int rk4_step(const ora_sys *S, const ora_opts *o, double t, double h, double complex *a, double *q,
+                    ora_work *W, double complex *k1, double complex *k2, double complex *k3, double complex *k4,
+                    double complex *ys, ora_eval *ev)
+{
+    int n = S->n, status = 0;
+    double qs[4], l1[4], l2[4], l3[4], l4[4];
+    ora_eval e2;
+    rhs(S, o, t, a, q, k1, l1, W, ev);
+    if (ev->below) status |= ORA_ST_TABLE_RANGE;
+    for (int s = 0; s < n; ++s) ys[s] = a[s] + 0.5 * h * k1[s];
+    for (int i = 0; i < 4; ++i) qs[i] = q[i] + 0.5 * h * l1[i];
+    rhs(S, o, t + 0.5 * h, ys, qs, k2, l2, W, &e2);
+    if (e2.below) status |= ORA_ST_TABLE_RANGE;
+    for (int s = 0; s < n; ++s) ys[s] = a[s] + 0.5 * h * k2[s];
+    for (int i = 0; i < 4; ++i) qs[i] = q[i] + 0.5 * h * l2[i];
+    rhs(S, o, t + 0.5 * h, ys, qs, k3, l3, W, &e2);
+    if (e2.below) status |= ORA_ST_TABLE_RANGE;
+    for (int s = 0; s < n; ++s) ys[s] = a[s] + h * k3[s];
+    for (int i = 0; i < 4; ++i) qs[i] = q[i] + h * l3[i];
+    rhs(S, o, t + h, ys, qs, k4, l4, W, &e2);
+    if (e2.below) status |= ORA_ST_TABLE_RANGE;
+    for (int s = 0; s < n; ++s) a[s] += h / 6.0 * (k1[s] + 2.0 * k2[s] + 2.0 * k3[s] + k4[s]);
+    for (int i = 0; i < 4; ++i) q[i] += h / 6.0 * (l1[i] + 2.0 * l2[i] + 2.0 * l3[i] + l4[i]);
+    return status;
+}
+
 static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o, double complex *a_out, ora_result *res)
 {
     int n = S->n, status = 0;
     ora_work W;
-    double complex *a = malloc(sizeof(double complex) * n * 6);
+    double complex *a = malloc(sizeof(double complex) * n * 8);
     if (!a || work_alloc(&W, n, S->L)) { free(a); work_free(&W); return ORA_ENOMEM; }
     double complex *k1 = a + n, *k2 = a + 2 * n, *k3 = a + 3 * n, *k4 = a + 4 * n, *ys = a + 5 * n;
-    double q[4], qs[4], l1[4], l2[4], l3[4], l4[4];
+    double complex *a0 = a + 6 * n, *a1 = a + 7 * n;
+    double q[4];
     initial_state(S, tr, (o->flags & ORA_F_DECOUPLED) != 0, a, q, NULL);
     if (o->flags & ORA_F_PRESCRIBED) {
         double s = o->line_v * (0.0 - o->line_t0);
         q[0] = sqrt(o->line_b * o->line_b + s * s);
         q[1] = q[2] = q[3] = 0.0;
     }
-    double dt = tr->dt, e0 = 0.0, j0 = 0.0, ndev = 0.0, edev = 0.0, jdev = 0.0;
+    double dt = tr->dt, t = 0.0, e0 = 0.0, j0 = 0.0, ndev = 0.0, edev = 0.0, jdev = 0.0;
     ora_eval ev;
     int steps = 0, stopped = 0;
-    for (int step = 0; step < tr->max_steps; ++step) {
-        double t = step * dt;
-        rhs(S, o, t, a, q, k1, l1, &W, &ev);
-        if (ev.below) status |= ORA_ST_TABLE_RANGE;
+    /* Step control.  Fixed: every step dt.  Adaptive (o->tol > 0; ADAPTOL of Sec. III is not given,
+       this is the reading in the design notes): step doubling -- one RK4 step of h against two of
+       h/2 from the same state, error = max_n |a_n(two halves) - a_n(one step)|.  The two-half result
+       is kept when the error is at most tol or h is already dt (the smallest step); otherwise h is
+       halved and the step retried from the same state.  After an accepted step h doubles, up to
+       hmax_factor dt, when the error was at most tol / 64.  h starts at hmax_factor dt. */
+    const int adaptive = o->tol > 0.0;
+    const double hmax = dt * o->hmax_factor;
+    double h = adaptive ? hmax : dt;
+    while (steps < tr->max_steps) {
+        double qstart[4], q1[4], err = 0.0, tn;
+        for (int i = 0; i < 4; ++i) qstart[i] = q[i];
+        if (!adaptive) {
+            status |= rk4_step(S, o, steps * dt, dt, a, q, &W, k1, k2, k3, k4, ys, &ev);
+            tn = (steps + 1) * dt;
+        } else {
+            ora_eval eh;
+            for (int s = 0; s < n; ++s) { a0[s] = a[s]; a1[s] = a[s]; }
+            for (int i = 0; i < 4; ++i) q1[i] = q[i];
+            status |= rk4_step(S, o, t, h, a1, q1, &W, k1, k2, k3, k4, ys, &ev);
+            status |= rk4_step(S, o, t, 0.5 * h, a, q, &W, k1, k2, k3, k4, ys, &eh);
+            status |= rk4_step(S, o, t + 0.5 * h, 0.5 * h, a, q, &W, k1, k2, k3, k4, ys, &eh);
+            for (int s = 0; s < n; ++s) err = fmax(err, cabs(a[s] - a1[s]));
+            if (!(err <= o->tol) && h > dt) {
+                for (int s = 0; s < n; ++s) a[s] = a0[s];
+                for (int i = 0; i < 4; ++i) q[i] = qstart[i];
+                h *= 0.5;
+                continue;
+            }
+            tn = t + h;
+        }
+        /* diagnostics of the state the step started from */
         {
-            double et = total_energy(S, o, q, &ev), jt = total_angmom(o, q, &ev);
-            if (step == 0) { e0 = et; j0 = jt; }
+            double et = total_energy(S, o, qstart, &ev), jt = total_angmom(o, qstart, &ev);
+            if (steps == 0) { e0 = et; j0 = jt; }
             if (fabs(ev.norm - 1.0) > ndev) ndev = fabs(ev.norm - 1.0);
             if (fabs(et - e0) > edev) edev = fabs(et - e0);
             if (fabs(jt - j0) > jdev) jdev = fabs(jt - j0);
         }
-        for (int s = 0; s < n; ++s) ys[s] = a[s] + 0.5 * dt * k1[s];
-        for (int i = 0; i < 4; ++i) qs[i] = q[i] + 0.5 * dt * l1[i];
-        rhs(S, o, t + 0.5 * dt, ys, qs, k2, l2, &W, &ev);
-        if (ev.below) status |= ORA_ST_TABLE_RANGE;
-        for (int s = 0; s < n; ++s) ys[s] = a[s] + 0.5 * dt * k2[s];
-        for (int i = 0; i < 4; ++i) qs[i] = q[i] + 0.5 * dt * l2[i];
-        rhs(S, o, t + 0.5 * dt, ys, qs, k3, l3, &W, &ev);
-        if (ev.below) status |= ORA_ST_TABLE_RANGE;
-        for (int s = 0; s < n; ++s) ys[s] = a[s] + dt * k3[s];
-        for (int i = 0; i < 4; ++i) qs[i] = q[i] + dt * l3[i];
-        rhs(S, o, t + dt, ys, qs, k4, l4, &W, &ev);
-        if (ev.below) status |= ORA_ST_TABLE_RANGE;
-        for (int s = 0; s < n; ++s) a[s] += dt / 6.0 * (k1[s] + 2.0 * k2[s] + 2.0 * k3[s] + k4[s]);
-        for (int i = 0; i < 4; ++i) q[i] += dt / 6.0 * (l1[i] + 2.0 * l2[i] + 2.0 * l3[i] + l4[i]);
         if (o->flags & ORA_F_PRESCRIBED) {
-            double s = o->line_v * ((step + 1) * dt - o->line_t0);
+            double s = o->line_v * (tn - o->line_t0);
             q[0] = sqrt(o->line_b * o->line_b + s * s);
         }
-        steps = step + 1;
+        steps += 1;
+        t = tn;
+        if (adaptive && 64.0 * err <= o->tol && h < hmax) h *= 2.0;
         if (!finite_state(n, a, q)) { status |= ORA_ST_NONFINITE; stopped = 1; break; }
         if (!(o->flags & (ORA_F_NO_STOP | ORA_F_PRESCRIBED)) && q[0] >= tr->r_end && q[1] > 0.0) { stopped = 1; break; }
     }
     if (!stopped) status |= ORA_ST_MAX_STEPS;
     if (!(status & ORA_ST_NONFINITE)) {
         /* diagnostics of the final state */
-        rhs(S, o, steps * dt, a, q, k1, l1, &W, &ev);
+        double lf[4];
+        rhs(S, o, t, a, q, k1, lf, &W, &ev);
         double et = total_energy(S, o, q, &ev), jt = total_angmom(o, q, &ev);
         if (steps == 0) { e0 = et; j0 = jt; }
         if (fabs(ev.norm - 1.0) > ndev) ndev = fabs(ev.norm - 1.0);
@@ -788,7 +840,7 @@ static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o
     res->norm_dev = ndev;
     res->energy_dev = edev;
     res->angmom_dev = jdev;
-    res->t_final = steps * dt;
+    res->t_final = t;
     res->R = q[0]; res->PR = q[1]; res->Phi = q[2]; res->PPhi = q[3];
     free(a);
     work_free(&W);
@@ -865,6 +917,8 @@ int ora_propagate(const ora_system_desc *d, const ora_traj *tr, int n_traj, int 
         o.line_b = tr[i].b;
         o.line_v = line_speed ? line_speed[i] : 0.0;
         o.line_t0 = 0.5 * tr[i].max_steps * tr[i].dt;
+        o.tol = d->adapt_tol;
+        o.hmax_factor = d->adapt_hmax_factor > 0 ? (double)d->adapt_hmax_factor : 16.0;
         if (propagate_one(&S, tr + i, &o, (double complex *)(final_amp + 2 * (size_t)i * d->n), res + i))
 #ifdef _OPENMP
 #pragma omp atomic write

@@ -96,3 +96,46 @@ def test_decoupled_needs_isotropic_identity_term(ora):
                    r_min=2.0, r_max=30.0)
     with pytest.raises(RuntimeError):
         ora.propagate(s, [0.01], [0.0], [0], flags=ora.F_DECOUPLED)
+
+
+# ------------------------------------------------------------------ adaptive step control
+def _adapt_sys(ora, adapt, jmax=3):
+    p = W.diatom_pes_params(jmax=jmax, n_grid=200)
+    return ora.diatom_system(jmax, p.bconst, p.mu, p.A, p.beta, p.c6, p.rd, 200, p.r_min, p.r_max, adapt=adapt), p
+
+
+def test_adaptive_limits_are_fixed_half_steps(ora):
+    """Step doubling keeps the two-half-step result: with a tolerance no step can meet, every step is
+    the smallest (dt) and the run equals fixed steps of dt/2; with a tolerance every step meets, every
+    step is the largest (16 dt) and the run equals fixed steps of 8 dt -- bit for bit."""
+    e, b = W.cm([900.0]), [2.0]
+    s_tiny, _ = _adapt_sys(ora, (1e-300, 16))
+    s_huge, _ = _adapt_sys(ora, (1e300, 16))
+    s_fix, _ = _adapt_sys(ora, None)
+    a1, r1 = ora.propagate(s_tiny, e, b, [1], dt=4.0, max_steps=300, flags=ora.F_NO_STOP)
+    a2, r2 = ora.propagate(s_fix, e, b, [1], dt=2.0, max_steps=600, flags=ora.F_NO_STOP)
+    assert np.array_equal(a1, a2) and r1["R"][0] == r2["R"][0] and r1["t_final"][0] == r2["t_final"][0]
+    a3, r3 = ora.propagate(s_huge, e, b, [1], dt=4.0, max_steps=40, flags=ora.F_NO_STOP)
+    a4, r4 = ora.propagate(s_fix, e, b, [1], dt=32.0, max_steps=80, flags=ora.F_NO_STOP)
+    assert np.array_equal(a3, a4) and r3["R"][0] == r4["R"][0] and r3["t_final"][0] == 40 * 64.0
+
+
+def test_adaptive_error_follows_tolerance(ora):
+    """Against a fixed-step run at dt = 0.5 (converged): the level populations (summed over m, which
+    the frame rotation beyond r_end does not change) of adaptive runs stay within 1e-6 and get no
+    worse with a tighter tolerance, while the adaptive runs take over ten times fewer steps than fixed
+    dt = 5 -- large steps where the coupling is weak -- and more with a tighter tolerance."""
+    e, b, s0 = W.cm([300.0, 1500.0]), [1.0, 4.0], [0, 4]
+    ref_sys, _ = _adapt_sys(ora, None)
+    lev = lambda a: np.stack([np.bincount(ref_sys.level, weights=np.abs(x) ** 2) for x in a])
+    aref, _ = ora.propagate(ref_sys, e, b, s0, dt=0.5)
+    _, rfix = ora.propagate(ref_sys, e, b, s0, dt=5.0)
+    errs, steps = [], []
+    for tol in (1e-4, 1e-8):
+        s, _ = _adapt_sys(ora, (tol, 16))
+        a, r = ora.propagate(s, e, b, s0, dt=5.0)
+        assert np.all(r["status"] == 0)
+        errs.append(np.max(np.abs(lev(a) - lev(aref))))
+        steps.append(r["steps"].sum())
+    assert errs[0] < 1e-6 and errs[1] <= errs[0]
+    assert steps[0] < 0.1 * rfix["steps"].sum() and steps[1] >= steps[0]
