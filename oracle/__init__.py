@@ -386,3 +386,31 @@ def cross_sections(sys: System, pop, weight, group, n_groups) -> np.ndarray:
     lib().ora_cross_sections(C.c_int(sys.n), _p(sys.level), C.c_int(sys.n_levels), C.c_int(pop.shape[0]), _p(pop),
                              _p(weight), _p(group), C.c_int(n_groups), _p(sig))
     return sig
+
+
+def molmol_states(lev_J, j2s, lev_E1, bconst2):
+    """Composite states of Eq. 3 for an asymmetric top (levels l1 with J = lev_J[l1], energies lev_E1)
+    and a linear rotor (j2 in j2s, E = bconst2 j2 (j2+1)): for each level l1, each j2, each total j in
+    |J - j2| .. J + j2 and m = -j..j.  Level id = l1 * len(j2s) + index of j2.  Returns energy,
+    level, j (total), m, l1, j2."""
+    e, lev, jq, mq, l1s, j2o = [], [], [], [], [], []
+    for l1, (J, E1) in enumerate(zip(lev_J, lev_E1)):
+        for i2, a in enumerate(j2s):
+            for j in range(abs(int(J) - a), int(J) + a + 1):
+                for m in range(-j, j + 1):
+                    e.append(E1 + bconst2 * a * (a + 1)); lev.append(l1 * len(j2s) + i2)
+                    jq.append(j); mq.append(m); l1s.append(l1); j2o.append(a)
+    i32 = lambda x: np.array(x, np.int32)
+    return np.array(e), i32(lev), i32(jq), i32(mq), i32(l1s), i32(j2o)
+
+
+def molmol_G(lev_J, lev_b, jmax1, l1, j2, jt, mt, lam1, mu1, lam2, lam) -> np.ndarray:
+    """<n'' m | tau_{lam1 mu1 lam2 lam} | n' m> (Eqs. 13-17) over the composite states."""
+    n = len(l1)
+    G = np.zeros((n, n))
+    a = [np.ascontiguousarray(x, np.int32) for x in (l1, j2, jt, mt, lev_J)]
+    lib().ora_molmol_G(C.c_int(n), *(_p(x) for x in a[:4]), _p(a[4]),
+                       _p(np.ascontiguousarray(lev_b, np.float64)), C.c_int(jmax1), C.c_int(lam1), C.c_int(mu1),
+                       C.c_int(lam2), C.c_int(lam), _p(G))
+    return G
+

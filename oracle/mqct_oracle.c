@@ -1336,3 +1336,59 @@ void ora_asym_G(int n_lev, const int *lev_J, const double *lev_b, int jmax, int 
         }
     free(first);
 }
+
+/* ------------------------------------------------------------------ */
+/* Asymmetric top + linear rotor (Eqs. 3, 13-17)                      */
+/* ------------------------------------------------------------------ */
+/* Coupling matrix of one expansion term tau_{lam1 mu1 lam2 lam} (Eq. 13) between the composite states
+ * |n m> of Eq. 3.  State s is given by its molecule-1 level l1[s] (J = lev_J[l1], eigenvector
+ * lev_b[l1][K + jmax1] of Eq. 1), the rotor's j2[s], the total j[s] and the projection m[s].  With
+ * Eq. 16 for molecule 1 (normalisation sqrt((2j1+1)/(8 pi^2)) of Eq. 3):
+ *   <j1'' m1'' K''| D^{lam1*}_{eta nu} |j1' m1' K'> = sqrt((2j1'+1)/(2j1''+1)) C^{j1'' m1''}_{j1' m1' lam1 eta}
+ *                                                   C^{j1'' K''}_{j1' K' lam1 nu},
+ * Eq. 15 for molecule 2, and the couplings of Eq. 3 for both states (Eq. 17 before the CG
+ * selection rules are used).  G[n][n], row = final state, zero between different m. */
+void ora_molmol_G(int n, const int *l1, const int *j2, const int *jt, const int *mt, const int *lev_J,
+                  const double *lev_b, int jmax1, int lam1, int mu1, int lam2, int lam, double *G)
+{
+    const double pi = 3.14159265358979323846;
+    const int w = 2 * jmax1 + 1;
+    const double sgn = ((lam1 + mu1 + lam2 + lam) & 1) ? -1.0 : 1.0;
+    memset(G, 0, sizeof(double) * (size_t)n * n);
+#pragma omp parallel for schedule(dynamic)
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            if (mt[r] != mt[c]) continue;
+            const int m = mt[r];
+            const int J2 = lev_J[l1[r]], J1 = lev_J[l1[c]], a2 = j2[r], a1 = j2[c];
+            const double *b2 = lev_b + (size_t)l1[r] * w + jmax1, *b1 = lev_b + (size_t)l1[c] * w + jmax1;
+            /* molecule 1: the K sums of the two D functions of Eq. 13 (independent of m1) */
+            double Kp = 0.0, Km = 0.0;
+            for (int K1 = -J1; K1 <= J1; ++K1) {
+                if (K1 + mu1 >= -J2 && K1 + mu1 <= J2) Kp += b2[K1 + mu1] * b1[K1] * ora_cg(J1, K1, lam1, mu1, J2, K1 + mu1);
+                if (K1 - mu1 >= -J2 && K1 - mu1 <= J2) Km += b2[K1 - mu1] * b1[K1] * ora_cg(J1, K1, lam1, -mu1, J2, K1 - mu1);
+            }
+            const double Ksum = Kp + sgn * Km;
+            if (Ksum == 0.0) continue;
+            const double c2 = ora_cg(a1, 0, lam2, 0, a2, 0);
+            if (c2 == 0.0) continue;
+            const double pre1 = sqrt((2.0 * J1 + 1.0) / (2.0 * J2 + 1.0));
+            const double pre2 = sqrt((2.0 * a1 + 1.0) * (2.0 * lam2 + 1.0) / (4.0 * pi * (2.0 * a2 + 1.0))) * c2;
+            double acc = 0.0;
+            const int emax = lam1 < lam2 ? lam1 : lam2;
+            for (int eta = -emax; eta <= emax; ++eta) {
+                const double ce = ora_cg(lam1, eta, lam2, -eta, lam, 0);
+                if (ce == 0.0) continue;
+                for (int m1 = -J1; m1 <= J1; ++m1) {
+                    const int m2 = m - m1, n1 = m1 + eta, n2 = m2 - eta;   /* m1'' = m1' + eta, m2'' = m2' - eta */
+                    if (abs(m2) > a1 || abs(n1) > J2 || abs(n2) > a2) continue;
+                    const double cin = ora_cg(J1, m1, a1, m2, jt[c], m);
+                    const double cout = ora_cg(J2, n1, a2, n2, jt[r], m);
+                    if (cin == 0.0 || cout == 0.0) continue;
+                    acc += ce * cin * cout * pre1 * ora_cg(J1, m1, lam1, eta, J2, n1) * Ksum * pre2 *
+                           ora_cg(a1, m2, lam2, -eta, a2, n2);
+                }
+            }
+            G[(size_t)r * n + c] = sqrt((2.0 * lam1 + 1.0) / (4.0 * pi)) * acc;
+        }
+}
