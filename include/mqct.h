@@ -96,9 +96,15 @@ typedef enum { MQCT_FP64 = 0, MQCT_FP32 = 1, MQCT_BF16X3 = 2 } mqct_precision;
    t_0 = max_steps dt / 2 (time-symmetric about the middle of the run), for exactly max_steps RK4
    steps (r0 and r_end are not used; the mean field does not act back on the motion).  The
    quantum equation (Eqs. 4-6) is integrated along it.  This is the setting in which microscopic
-   reversibility (Eq. 19) holds exactly for the discrete propagator, and the classical-trajectory-
-   first decoupling the paper's production runs use (Sec. III).  P_R = P_Phi = 0 in the
+   reversibility (Eq. 19) holds exactly for the discrete propagator.  P_R = P_Phi = 0 in the
    diagnostics' energy. */
+#define MQCT_DECOUPLED_TRAJ 2   /* decoupled classical motion (FP64 systems only; the AT-MQCT
+   decoupling of Sec. III, whose equations the paper does not give, in this reading): R, Phi, P_R,
+   P_Phi follow Eqs. 7-10 with the mean field replaced by the isotropic potential alone -- the sum
+   v_iso(R) of the expansion terms whose G is the identity, which must exist -- and no torque, so the
+   path does not depend on the amplitudes; the amplitudes follow Eqs. 4-6 (Coriolis term included)
+   along it.  P_R starts from e_coll - v_iso(r0).  The diagnostics then track the classical energy
+   P_R^2/2mu + P_Phi^2/(2 mu R^2) + v_iso(R) and P_Phi, both conserved by this motion. */
 
 /* Description of one atom + rotor system.  All pointers are HOST pointers, read and
  * copied during mqct_create_system only. */
@@ -126,11 +132,22 @@ typedef struct {
     const double *ddv_ends;  /* [P][L][2] their R-derivatives at both ends                   */
     int32_t path;            /* mqct_path                                                    */
     int32_t precision;       /* mqct_precision                                               */
-    int32_t flags;           /* 0 or MQCT_PRESCRIBED_TRAJ                                     */
+    int32_t flags;           /* 0, MQCT_PRESCRIBED_TRAJ or MQCT_DECOUPLED_TRAJ                */
     int32_t grid_kind;       /* MQCT_GRID_UNIFORM, or MQCT_GRID_LOG (below)                   */
     double trunc_threshold;  /* PLAIN path: M_nm dropped when |M_nm(R)| <= threshold at both  */
     double trunc_r[2];       /*   trunc_r (hartree, bohr; Sec. III); <= 0 keeps every element */
+    double adapt_tol;        /* > 0: adaptive step control (FP64 systems; below), 0: fixed dt   */
+    int32_t adapt_hmax;      /* largest adaptive step in units of dt: a power of 2 in [1, 1024],
+                                0 = 16                                                        */
 } mqct_system_desc;
+
+/* Adaptive step control (FP64 systems; the paper's ADAPTOL predictor of Sec. III is not given, this
+ * is the reading used): step doubling -- one RK4 step of h against two of h/2 from the same state,
+ * error = max_n |a_n(two halves) - a_n(one step)|.  The two-half result is kept when the error is at
+ * most adapt_tol or h is already the trajectory's dt (the smallest step); otherwise h is halved and
+ * the step retried from the same state.  After an accepted step h doubles, up to adapt_hmax dt, when
+ * the error was at most adapt_tol / 64.  h starts at adapt_hmax dt.  max_steps and the diagnostics'
+ * steps count accepted steps; t_final is the time reached.  Not with MQCT_PRESCRIBED_TRAJ. */
 
 /* R grids (Sec. III).  MQCT_GRID_UNIFORM: R_k = r_min + k (r_max - r_min)/(n_grid - 1), splines
  * clamped cubics in R.  MQCT_GRID_LOG: R_k = r_min (r_max/r_min)^(k/(n_grid - 1)), r_min > 0 (the
@@ -250,6 +267,38 @@ typedef struct {
  * Errors: MQCT_ERR_INVALID_ARG (a bound above violated, or max_states below the first
  * level), MQCT_ERR_OOM. */
 mqct_status mqct_build_asym_top(const mqct_asym_params *p, mqct_system_desc *out);
+
+/* Parameters of the built-in asymmetric top + linear rotor system (the molecule-molecule coupling of
+ * Sec. II; helper for users and tests).  Composite states (Eq. 3)
+ *   |n m> = sum_{m1} C^{j m}_{j1 m1 j2 m-m1} psi_{j1 tau1 m1}(Lambda_1) Y^{j2}_{m-m1}(Lambda_2),
+ * n = {j, j1, tau1, j2}: molecule 1 levels (j1, tau1) of Eq. 1 for j1 <= j1max (ascending j1, then
+ * ascending energy), each combined with every j2 of the list, every total j in |j1 - j2| .. j1 + j2
+ * and m = -j..j (in that order); level id = (molecule-1 level) * n_j2 + index of j2, energy
+ * E_{j1 tau1} + bconst2 j2 (j2 + 1); the Coriolis ladder acts on the total j.  PES (Eq. 12) with the
+ * angular functions tau_{lam1 mu1 lam2 lam} of Eq. 13 and v_t(R) = coef_t exp(-beta_t R) (term 0 adds
+ * the damped dispersion -C6 R^-6 (1 - exp(-(R/Rd)^6))); G^t = <n'' m|tau_t|n' m> (Eq. 14 with the
+ * integrals of Eqs. 15-16; here evaluated by Gauss-Legendre quadrature over the polar angles). */
+typedef struct {
+    double A, B, C;          /* molecule 1 rotational constants (hartree), A >= B >= C > 0, A > C */
+    int32_t j1max;           /* 0..8                                                         */
+    double bconst2;          /* molecule 2 (linear rotor) constant (hartree)                  */
+    int32_t n_j2;            /* 1..8 values of j2                                            */
+    int32_t j2[8];           /* each 0..8                                                    */
+    double mu;               /* reduced mass (electron masses)                               */
+    int32_t n_terms;         /* 1..64                                                        */
+    int32_t lam1[64], mu1[64], lam2[64], lam[64];  /* 0 <= mu1 <= lam1 <= 8, lam2 <= 8, triangle */
+    double coef[64];         /* hartree */
+    double beta[64];         /* 1/bohr  */
+    double c6, rd;
+    int32_t n_grid;
+    double r_min, r_max;
+    int32_t path, precision;
+} mqct_molmol_params;
+
+/* Build the description of the asymmetric top + linear rotor system above (host arrays released by
+ * mqct_free_desc; G in triplet form).  Host-only.  Errors: MQCT_ERR_INVALID_ARG (ranges above, a term
+ * outside the triangle |lam1 - lam2| <= lam <= lam1 + lam2), MQCT_ERR_OOM. */
+mqct_status mqct_build_molmol(const mqct_molmol_params *p, mqct_system_desc *out);
 
 /* Free the arrays allocated by mqct_build_diatom / mqct_build_asym_top and zero *desc. */
 void mqct_free_desc(mqct_system_desc *desc);

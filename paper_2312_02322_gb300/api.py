@@ -23,6 +23,7 @@ PATH_PLAIN, PATH_FACTORISED = 0, 1
 FP64, FP32, BF16X3 = 0, 1, 2
 TRAJ_MAX_STEPS, TRAJ_TABLE_RANGE, TRAJ_NONFINITE, TRAJ_TIMEOUT, TRAJ_INVALID = 1, 2, 4, 8, 16
 PRESCRIBED_TRAJ = 1  # mqct_system_desc.flags
+DECOUPLED_TRAJ = 2
 
 _PATHS = {"plain": PATH_PLAIN, "factorised": PATH_FACTORISED}
 _PRECS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
@@ -44,6 +45,7 @@ class Desc(C.Structure):
         ("v", C.c_void_p), ("dv_ends", C.c_void_p), ("n_params", C.c_int32), ("dv_dparam", C.c_void_p),
         ("ddv_ends", C.c_void_p), ("path", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
         ("grid_kind", C.c_int32), ("trunc_threshold", C.c_double), ("trunc_r", C.c_double * 2),
+        ("adapt_tol", C.c_double), ("adapt_hmax", C.c_int32),
     ]
 
 
@@ -81,6 +83,15 @@ class PropagateOpts(C.Structure):
 GRID_UNIFORM, GRID_LOG = 0, 1
 
 
+class MolMolParams(C.Structure):
+    _fields_ = [("A", C.c_double), ("B", C.c_double), ("C", C.c_double), ("j1max", C.c_int32),
+                ("bconst2", C.c_double), ("n_j2", C.c_int32), ("j2", C.c_int32 * 8), ("mu", C.c_double),
+                ("n_terms", C.c_int32), ("lam1", C.c_int32 * 64), ("mu1", C.c_int32 * 64), ("lam2", C.c_int32 * 64),
+                ("lam", C.c_int32 * 64), ("coef", C.c_double * 64), ("beta", C.c_double * 64), ("c6", C.c_double),
+                ("rd", C.c_double), ("n_grid", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double),
+                ("path", C.c_int32), ("precision", C.c_int32)]
+
+
 class RateDesc(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("n_energies", C.c_int32), ("n_temps", C.c_int32), ("reserved", C.c_int32),
                 ("mu", C.c_double), ("u", C.c_void_p), ("kT", C.c_void_p), ("level_energy", C.c_void_p),
@@ -115,6 +126,7 @@ def lib():
             vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
             L.mqct_build_diatom.argtypes = [C.POINTER(DiatomParams), C.POINTER(Desc)]
             L.mqct_build_asym_top.argtypes = [C.POINTER(AsymParams), C.POINTER(Desc)]
+            L.mqct_build_molmol.argtypes = [C.POINTER(MolMolParams), C.POINTER(Desc)]
             L.mqct_free_desc.argtypes = [C.POINTER(Desc)]
             L.mqct_free_desc.restype = None
             L.mqct_create_system.argtypes = [C.POINTER(Desc), C.POINTER(vp)]
@@ -132,7 +144,7 @@ def lib():
             L.mqct_last_error.restype = C.c_char_p
             L.mqct_last_launch_count.restype = C.c_int64
             L.mqct_version.restype = C.c_char_p
-            for f in ("mqct_build_diatom", "mqct_build_asym_top", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
+            for f in ("mqct_build_diatom", "mqct_build_asym_top", "mqct_build_molmol", "mqct_create_system", "mqct_destroy_system", "mqct_system_info",
                       "mqct_propagate", "mqct_propagate_ex", "mqct_cross_sections", "mqct_adjoint",
                       "mqct_rate_coefficients"):
                 getattr(L, f).restype = C.c_int
@@ -194,11 +206,13 @@ class System:
 
     @classmethod
     def diatom(cls, p: "_inputs.DiatomParams", path="plain", precision="fp64", with_params=False,
-               prescribed=False, grid="uniform", trunc=None) -> "System":
+               prescribed=False, grid="uniform", trunc=None, decoupled=False, adapt=None) -> "System":
         """prescribed=True: MQCT_PRESCRIBED_TRAJ, each trajectory follows the time-symmetric straight
         line of impact parameter b and speed sqrt(2 e_coll / mu) for exactly max_steps steps.
         grid="log": MQCT_GRID_LOG tabulation (splines in ln R); trunc=(threshold, R_a, R_b): PLAIN-path
-        truncation of |M| <= threshold at both distances (Sec. III)."""
+        truncation of |M| <= threshold at both distances (Sec. III); decoupled=True: MQCT_DECOUPLED_TRAJ
+        (classical motion in the isotropic potential alone, the amplitudes along it); adapt=(tol, hmax):
+        step-doubling adaptive steps between dt and hmax dt (FP64 systems)."""
         dp = DiatomParams()
         dp.jmax, dp.bconst, dp.mu, dp.n_terms = p.jmax, p.bconst, p.mu, p.n_terms
         for i in range(p.n_terms):
@@ -212,7 +226,35 @@ class System:
             dp.trunc_threshold, dp.trunc_r[0], dp.trunc_r[1] = (float(x) for x in trunc)
         d = Desc()
         _check(lib().mqct_build_diatom(C.byref(dp), C.byref(d)))
-        d.flags = PRESCRIBED_TRAJ if prescribed else 0
+        d.flags = (PRESCRIBED_TRAJ if prescribed else 0) | (DECOUPLED_TRAJ if decoupled else 0)
+        if adapt is not None:
+            d.adapt_tol, d.adapt_hmax = float(adapt[0]), int(adapt[1])
+        try:
+            return cls(d)
+        finally:
+            lib().mqct_free_desc(C.byref(d))
+
+    @staticmethod
+    def molmol_params(p: "_inputs.MolMolParams", path="factorised", precision="fp64") -> MolMolParams:
+        mp = MolMolParams()
+        mp.A, mp.B, mp.C, mp.j1max, mp.bconst2 = p.A, p.B, p.C, p.j1max, p.bconst2
+        mp.n_j2 = len(p.j2)
+        for i, a in enumerate(p.j2):
+            mp.j2[i] = int(a)
+        mp.mu, mp.n_terms = p.mu, p.n_terms
+        for t, (a, m, b, c) in enumerate(p.terms):
+            mp.lam1[t], mp.mu1[t], mp.lam2[t], mp.lam[t] = a, m, b, c
+            mp.coef[t], mp.beta[t] = float(p.coef[t]), float(p.beta[t])
+        mp.c6, mp.rd, mp.n_grid, mp.r_min, mp.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
+        mp.path, mp.precision = _PATHS[path], _PRECS[precision]
+        return mp
+
+    @classmethod
+    def molmol(cls, p: "_inputs.MolMolParams", path="factorised", precision="fp64") -> "System":
+        """Asymmetric top + linear rotor (composite states of Eq. 3, coupling of Eqs. 13-17)."""
+        mp = cls.molmol_params(p, path, precision)
+        d = Desc()
+        _check(lib().mqct_build_molmol(C.byref(mp), C.byref(d)))
         try:
             return cls(d)
         finally:

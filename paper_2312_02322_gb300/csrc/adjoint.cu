@@ -729,8 +729,9 @@ extern "C" mqct_status mqct_adjoint(mqct_system sys, const mqct_traj *trajs, int
     if (h.L > kAdjMaxL) return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: more than 64 expansion terms");
     if (h.path != MQCT_PATH_FACTORISED)
         return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: the system must use the factorised path");
-    if (h.flags & MQCT_PRESCRIBED_TRAJ)
-        return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: not defined for prescribed trajectories");
+    if (h.adapt_tol > 0.0) return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: fixed steps only (adapt_tol > 0)");
+    if (h.flags & (MQCT_PRESCRIBED_TRAJ | MQCT_DECOUPLED_TRAJ))
+        return fail(MQCT_ERR_UNSUPPORTED, "mqct_adjoint: not defined for prescribed or decoupled trajectories");
     const bool fp32 = h.precision != MQCT_FP64;
     if (n > 0 && (!trajs || !weight || !group || !dL_dsigma)) return fail(MQCT_ERR_INVALID_ARG, "mqct_adjoint: NULL input");
     cudaStream_t st = (cudaStream_t)cuda_stream;

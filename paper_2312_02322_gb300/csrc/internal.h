@@ -31,6 +31,8 @@ struct DevSys {
     int path, precision, flags;
     double mu, r_min, h, inv_h;
     int grid_log;              // splines in x = ln R (MQCT_GRID_LOG) instead of x = R
+    double adapt_tol;          // > 0: adaptive step control (FP64 kernel)
+    double adapt_hmax;         // largest adaptive step / dt
     double x0;                 // first knot in the spline variable (r_min or ln r_min)
     const double *lev_energy;  // [n_levels]
     const float *lev_energy_f; // [n_levels] FP32 copy (mixed-precision systems)
@@ -99,6 +101,7 @@ struct PropArgs {
     int nmax;      // row stride of pop / amp
     int smem_n;    // shared-memory vector length (max n over systems)
     int smem_lev;  // max n_levels over systems
+    int adapt;     // some system uses adaptive steps: two more vectors of smem_n in shared memory
 };
 #ifdef __CUDACC__
 __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a);

@@ -157,7 +157,9 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
     const int per = (max_slices + maxw - 1) / maxw;
     const int nwarps = std::max(4, std::min(maxw, (max_slices + per - 1) / per));
     const int threads = nwarps * 32;
-    const size_t smem = sizeof(double2) * (6 * (size_t)nmax + 2 * (size_t)maxlev);
+    bool adapt = false;
+    for (int i = 0; i < n_systems; ++i) adapt |= systems[i]->s.h.adapt_tol > 0.0;
+    const size_t smem = sizeof(double2) * ((adapt ? 8 : 6) * (size_t)nmax + 2 * (size_t)maxlev);
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((e = cudaFuncSetAttribute(k_propagate_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -168,6 +170,7 @@ extern "C" mqct_status mqct_propagate_noalloc(const mqct_system *systems, int32_
     PropArgs pa{};
     pa.sys = dsys; pa.trajs = trajs; pa.order = nullptr; pa.n = n; pa.n_systems = n_systems; pa.queue = queue;
     pa.pop = final_pop; pa.amp = final_amp; pa.diag = diag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
+    pa.adapt = adapt ? 1 : 0;
     k_propagate_fp64<<<std::min(n, sms * per_sm), threads, smem, st>>>(pa);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");

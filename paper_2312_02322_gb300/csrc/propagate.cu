@@ -33,6 +33,7 @@ struct Ctl {
     double e0, j0, ndev, edev, jdev;
     double v[kMaxTerms], dv[kMaxTerms];
     double vid, dvid;
+    double q0[4], err, tcur;  // adaptive steps: classical state at the start, error, time
     int kint, status, steps, done, max_steps, t, item;
 };
 
@@ -85,6 +86,18 @@ __device__ void prepare_stage(const DevSys &S, Ctl &c)
             c.v[l] = v;
             c.dv[l] = dv;
             if ((S.id_mask >> l) & 1ull) { vid += v; dvid += dv; }
+        }
+        c.vid = vid;
+        c.dvid = dvid;
+    } else if (S.flags & MQCT_DECOUPLED_TRAJ) {
+        // the isotropic potential that drives the decoupled classical motion
+        double vid = 0.0, dvid = 0.0;
+        for (int l = 0; l < S.L; ++l) {
+            if (!((S.id_mask >> l) & 1ull)) continue;
+            double v, dv;
+            term_at(S, l, c.kint, c.x, v, dv);
+            vid += v;
+            dvid += dv * c.dinv;
         }
         c.vid = vid;
         c.dvid = dvid;
@@ -151,6 +164,162 @@ __device__ __forceinline__ void coupling_fp64(const DevSys &S, const Ctl &c, con
     }
 }
 
+// one RK4 step of length h from the state at t0 (A, C = exp(-iEt0) A, the classical stage input and
+// the stage quantities of prepare_stage): the amplitudes end in A and C (phases at t0 + h), the
+// classical state in c.q; t_next is the prescribed line's time at the end (t0 + h up to rounding);
+// with first set the diagnostics of the start state also reset e0 and j0.  Every thread calls it.
+__device__ void rk4_step(const DevSys &S, Ctl &c, double2 *A, double2 *Y0, double2 *Y1, double2 *ACC, double2 *C,
+                         double2 *W, double2 *PHa, double2 *PHb, double (*red)[6], double t0, double h, double t_next,
+                         bool first, int &ycur)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const int n = S.n;
+    for (int s = 0; s < 4; ++s) {
+        double2 *Yc = ycur ? Y1 : Y0, *Yn = ycur ? Y0 : Y1;
+        const double2 *PHc = (s == 0 || s == 3) ? PHa : PHb;
+        const double2 *PHn = (s == 0 || s == 1) ? PHb : PHa;
+        // P3 (+ phases of the next distinct stage time)
+        if (s == 0 || s == 2) {
+            const double tn = s == 0 ? t0 + 0.5 * h : t0 + h;
+            double2 *dst = s == 0 ? PHb : PHa;
+            for (int l = tid; l < S.n_levels; l += nt) {
+                double sn, cs;
+                sincos(S.lev_energy[l] * tn, &sn, &cs);
+                dst[l] = make_double2(cs, -sn);
+            }
+        }
+        double force = 0.0, vc = 0.0;
+        coupling_fp64(S, c, C, W, warp, nwarps, lane, force, vc);
+        __syncthreads();
+        // P4
+        const double hp = 0.5 * c.phidot;
+        const double wk = (s == 1 || s == 2) ? 2.0 : 1.0;
+        const double bn = s == 2 ? h : 0.5 * h;
+        double torque = 0.0, nrm = 0.0, erot = 0.0, jy = 0.0;
+        for (int r = tid; r < n; r += nt) {
+            const int ru = S.up[r], rd = S.dn[r];
+            const double au = S.aup[r], ad = S.adn[r];
+            const double2 y = Yc[r], yu = Yc[ru], yd = Yc[rd];
+            const double2 w = W[r], wu = W[ru], wd = W[rd];
+            const double2 z = C[r];
+            const double2 p = PHc[S.lev[r]];
+            const double2 Dy = make_double2(ad * yd.x - au * yu.x, ad * yd.y - au * yu.y);
+            const double2 Dw = make_double2(ad * wd.x - au * wu.x, ad * wd.y - au * wu.y);
+            torque += z.x * Dw.x + z.y * Dw.y;
+            // k = -i conj(p) w + (phidot/2) D y
+            double2 k;
+            k.x = fma(hp, Dy.x, p.x * w.y - p.y * w.x);
+            k.y = fma(hp, Dy.y, -(p.x * w.x + p.y * w.y));
+            if (s == 0) {
+                const double pp = y.x * y.x + y.y * y.y;
+                nrm += pp;
+                erot += S.lev_energy[S.lev[r]] * pp;
+                jy += y.x * Dy.y - y.y * Dy.x;
+                ACC[r] = k;
+            } else {
+                double2 acc = ACC[r];
+                acc.x = fma(wk, k.x, acc.x);
+                acc.y = fma(wk, k.y, acc.y);
+                ACC[r] = acc;
+                if (s == 3) {
+                    double2 an = A[r];
+                    an.x = fma(h / 6.0, acc.x, an.x);
+                    an.y = fma(h / 6.0, acc.y, an.y);
+                    A[r] = an;
+                    Yn[r] = an;
+                    const double2 pn = PHn[S.lev[r]];
+                    C[r] = make_double2(pn.x * an.x - pn.y * an.y, pn.x * an.y + pn.y * an.x);
+                }
+            }
+            if (s < 3) {
+                const double2 a0 = A[r];
+                const double2 yn = make_double2(fma(bn, k.x, a0.x), fma(bn, k.y, a0.y));
+                Yn[r] = yn;
+                const double2 pn = PHn[S.lev[r]];
+                C[r] = make_double2(pn.x * yn.x - pn.y * yn.y, pn.x * yn.y + pn.y * yn.x);
+            }
+        }
+        // block reduction
+        force = warp_sum(force);
+        torque = warp_sum(torque);
+        if (s == 0) {
+            vc = warp_sum(vc); nrm = warp_sum(nrm); erot = warp_sum(erot); jy = warp_sum(jy);
+        }
+        if (lane == 0) {
+            red[warp][0] = force; red[warp][1] = torque;
+            if (s == 0) { red[warp][2] = vc; red[warp][3] = nrm; red[warp][4] = erot; red[warp][5] = jy; }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double F = 0, T = 0, V = 0, NR = 0, ER = 0, JY = 0;
+            for (int w2 = 0; w2 < nwarps; ++w2) {
+                F += red[w2][0]; T += red[w2][1];
+                if (s == 0) { V += red[w2][2]; NR += red[w2][3]; ER += red[w2][4]; JY += red[w2][5]; }
+            }
+            const double R = c.qs[0], PR = c.qs[1], PP = c.qs[3], mu = S.mu;
+            const bool dec = S.flags & MQCT_DECOUPLED_TRAJ;
+            if (dec) { F = -c.dvid; T = 0.0; }  // isotropic potential alone, no torque
+            double l[4] = {PR / mu, F + PP * PP / (mu * R * R * R), c.phidot, T};
+            const bool presc = S.flags & MQCT_PRESCRIBED_TRAJ;
+            if (presc) l[0] = l[1] = l[2] = l[3] = 0.0;  // the motion is prescribed
+            if (s == 0) {
+                const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + (dec ? c.vid : ER + V);
+                const double jt = dec ? PP : PP + 0.5 * JY;
+                if (first) { c.e0 = et; c.j0 = jt; }
+                c.ndev = fmax(c.ndev, fabs(NR - 1.0));
+                c.edev = fmax(c.edev, fabs(et - c.e0));
+                c.jdev = fmax(c.jdev, fabs(jt - c.j0));
+                for (int i = 0; i < 4; ++i) c.lacc[i] = l[i];
+            } else {
+                for (int i = 0; i < 4; ++i) c.lacc[i] = fma(wk, l[i], c.lacc[i]);
+            }
+            if (s < 3) {
+                for (int i = 0; i < 4; ++i) c.qs[i] = fma(bn, l[i], c.q[i]);
+            } else {
+                for (int i = 0; i < 4; ++i) { c.q[i] = fma(h / 6.0, c.lacc[i], c.q[i]); c.qs[i] = c.q[i]; }
+                bool fin = isfinite(c.q[0]) && isfinite(c.q[1]) && isfinite(c.q[2]) && isfinite(c.q[3]);
+                if (!fin) { c.status |= MQCT_TRAJ_NONFINITE; c.done = 1; }
+            }
+            if (presc) {
+                // R of the next stage on the line (stage times as in the phase factors)
+                const double tn = s == 3 ? t_next : (s == 2 ? t0 + h : t0 + 0.5 * h);
+                c.qs[0] = line_r(c, tn);
+                if (s == 3) c.q[0] = c.qs[0];
+            }
+            if (!(c.status & MQCT_TRAJ_NONFINITE)) prepare_stage(S, c);
+        }
+        ycur ^= 1;
+        __syncthreads();
+    }
+}
+
+// back to the start of an adaptive step: amplitudes A0 at time t (also the next stage input Y and
+// C = exp(-iEt) A0 with fresh phase factors PHa), classical state c.q0, stage quantities
+__device__ void restore_start(const DevSys &S, Ctl &c, double2 *A, const double2 *A0, double2 *Y, double2 *C,
+                              double2 *PHa, double t)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int l = tid; l < S.n_levels; l += nt) {
+        double sn, cs;
+        sincos(S.lev_energy[l] * t, &sn, &cs);
+        PHa[l] = make_double2(cs, -sn);
+    }
+    __syncthreads();
+    for (int r = tid; r < S.n; r += nt) {
+        const double2 a0 = A0[r], p = PHa[S.lev[r]];
+        A[r] = a0;
+        Y[r] = a0;
+        C[r] = make_double2(p.x * a0.x - p.y * a0.y, p.x * a0.y + p.y * a0.x);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) c.q[i] = c.qs[i] = c.q0[i];
+        c.status &= ~MQCT_TRAJ_NONFINITE;
+        c.done = 0;
+        prepare_stage(S, c);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
 {
     extern __shared__ double2 smem[];
@@ -161,6 +330,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
     const int NN = a.smem_n;
     double2 *A = smem, *Y0 = A + NN, *Y1 = Y0 + NN, *ACC = Y1 + NN, *C = ACC + NN, *W = C + NN;
     double2 *PHa = W + NN, *PHb = PHa + a.smem_lev;
+    double2 *A0 = PHb + a.smem_lev, *A1 = A0 + NN;  // adaptive steps only (a.adapt)
 
     for (;;) {
         if (tid == 0) c.item = atomicAdd(a.queue, 1);
@@ -198,10 +368,12 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
             int k; double x;
             locate(S, tr.r0, k, x);
             double m00 = 0.0;
+            const bool dec = S.flags & MQCT_DECOUPLED_TRAJ;
             for (int l = 0; l < S.L; ++l) {
                 double v, dv;
                 term_at(S, l, k, x, v, dv);
-                m00 += v * S.diag_g[(size_t)l * n + s0];
+                // decoupled motion starts in the isotropic potential, not the state's mean field
+                m00 += dec ? (((S.id_mask >> l) & 1ull) ? v : 0.0) : v * S.diag_g[(size_t)l * n + s0];
             }
             const double lz = tr.b * sqrt(2.0 * S.mu * tr.e_coll);
             c.q[0] = tr.r0; c.q[2] = 0.0; c.q[3] = lz;
@@ -226,125 +398,72 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
         int ycur = 0;
         const double dt = tr.dt;
         // ---- RK4 steps
-        while (!c.done) {
-            const int step = c.steps;
-            const double t0 = step * dt;
-            for (int s = 0; s < 4; ++s) {
-                double2 *Yc = ycur ? Y1 : Y0, *Yn = ycur ? Y0 : Y1;
-                const double2 *PHc = (s == 0 || s == 3) ? PHa : PHb;
-                const double2 *PHn = (s == 0 || s == 1) ? PHb : PHa;
-                // P3 (+ phases of the next distinct stage time)
-                if (s == 0 || s == 2) {
-                    const double tn = s == 0 ? t0 + 0.5 * dt : t0 + dt;
-                    double2 *dst = s == 0 ? PHb : PHa;
-                    for (int l = tid; l < S.n_levels; l += nt) {
-                        double sn, cs;
-                        sincos(S.lev_energy[l] * tn, &sn, &cs);
-                        dst[l] = make_double2(cs, -sn);
-                    }
-                }
-                double force = 0.0, vc = 0.0;
-                coupling_fp64(S, c, C, W, warp, nwarps, lane, force, vc);
+        if (S.adapt_tol > 0.0) {
+            // step doubling (the adaptive step of Sec. III in the reading of the header): one step of
+            // h against two of h/2 from the same state; the two-half result is kept when
+            // max_n |a_n(halves) - a_n(one step)| <= tol or h = dt, else h halves and the step is
+            // retried; h doubles (up to hmax) after a step whose error was <= tol / 64
+            const double hmax = dt * S.adapt_hmax;
+            double h = hmax, tcur = 0.0;
+            while (!c.done) {
+                for (int r = tid; r < n; r += nt) A0[r] = A[r];
+                if (tid == 0)
+                    for (int i = 0; i < 4; ++i) c.q0[i] = c.q[i];
                 __syncthreads();
-                // P4
-                const double hp = 0.5 * c.phidot;
-                const double wk = (s == 1 || s == 2) ? 2.0 : 1.0;
-                const double bn = s == 2 ? dt : 0.5 * dt;
-                double torque = 0.0, nrm = 0.0, erot = 0.0, jy = 0.0;
+                rk4_step(S, c, A, Y0, Y1, ACC, C, W, PHa, PHb, red, tcur, h, tcur + h, c.steps == 0, ycur);
+                for (int r = tid; r < n; r += nt) A1[r] = A[r];
+                __syncthreads();
+                restore_start(S, c, A, A0, ycur ? Y1 : Y0, C, PHa, tcur);
+                rk4_step(S, c, A, Y0, Y1, ACC, C, W, PHa, PHb, red, tcur, 0.5 * h, tcur + 0.5 * h, false, ycur);
+                if (!(c.status & MQCT_TRAJ_NONFINITE))
+                    rk4_step(S, c, A, Y0, Y1, ACC, C, W, PHa, PHb, red, tcur + 0.5 * h, 0.5 * h, tcur + h, false, ycur);
+                // error: max over the states of |a(halves) - a(one step)| (independent of the order)
+                double err = 0.0;
                 for (int r = tid; r < n; r += nt) {
-                    const int ru = S.up[r], rd = S.dn[r];
-                    const double au = S.aup[r], ad = S.adn[r];
-                    const double2 y = Yc[r], yu = Yc[ru], yd = Yc[rd];
-                    const double2 w = W[r], wu = W[ru], wd = W[rd];
-                    const double2 z = C[r];
-                    const double2 p = PHc[S.lev[r]];
-                    const double2 Dy = make_double2(ad * yd.x - au * yu.x, ad * yd.y - au * yu.y);
-                    const double2 Dw = make_double2(ad * wd.x - au * wu.x, ad * wd.y - au * wu.y);
-                    torque += z.x * Dw.x + z.y * Dw.y;
-                    // k = -i conj(p) w + (phidot/2) D y
-                    double2 k;
-                    k.x = fma(hp, Dy.x, p.x * w.y - p.y * w.x);
-                    k.y = fma(hp, Dy.y, -(p.x * w.x + p.y * w.y));
-                    if (s == 0) {
-                        const double pp = y.x * y.x + y.y * y.y;
-                        nrm += pp;
-                        erot += S.lev_energy[S.lev[r]] * pp;
-                        jy += y.x * Dy.y - y.y * Dy.x;
-                        ACC[r] = k;
-                    } else {
-                        double2 acc = ACC[r];
-                        acc.x = fma(wk, k.x, acc.x);
-                        acc.y = fma(wk, k.y, acc.y);
-                        ACC[r] = acc;
-                        if (s == 3) {
-                            double2 an = A[r];
-                            an.x = fma(dt / 6.0, acc.x, an.x);
-                            an.y = fma(dt / 6.0, acc.y, an.y);
-                            A[r] = an;
-                            Yn[r] = an;
-                            const double2 pn = PHn[S.lev[r]];
-                            C[r] = make_double2(pn.x * an.x - pn.y * an.y, pn.x * an.y + pn.y * an.x);
-                        }
-                    }
-                    if (s < 3) {
-                        const double2 a0 = A[r];
-                        const double2 yn = make_double2(fma(bn, k.x, a0.x), fma(bn, k.y, a0.y));
-                        Yn[r] = yn;
-                        const double2 pn = PHn[S.lev[r]];
-                        C[r] = make_double2(pn.x * yn.x - pn.y * yn.y, pn.x * yn.y + pn.y * yn.x);
-                    }
+                    const double2 x = A[r], y = A1[r];
+                    err = fmax(err, hypot(x.x - y.x, x.y - y.y));
                 }
-                // block reduction
-                force = warp_sum(force);
-                torque = warp_sum(torque);
-                if (s == 0) {
-                    vc = warp_sum(vc); nrm = warp_sum(nrm); erot = warp_sum(erot); jy = warp_sum(jy);
-                }
-                if (lane == 0) {
-                    red[warp][0] = force; red[warp][1] = torque;
-                    if (s == 0) { red[warp][2] = vc; red[warp][3] = nrm; red[warp][4] = erot; red[warp][5] = jy; }
-                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+                if (lane == 0) red[warp][0] = err;
                 __syncthreads();
                 if (tid == 0) {
-                    double F = 0, T = 0, V = 0, NR = 0, ER = 0, JY = 0;
-                    for (int w2 = 0; w2 < nwarps; ++w2) {
-                        F += red[w2][0]; T += red[w2][1];
-                        if (s == 0) { V += red[w2][2]; NR += red[w2][3]; ER += red[w2][4]; JY += red[w2][5]; }
+                    double e2 = 0.0;
+                    for (int w2 = 0; w2 < nwarps; ++w2) e2 = fmax(e2, red[w2][0]);
+                    c.err = e2;
+                }
+                __syncthreads();
+                if (!(c.status & MQCT_TRAJ_NONFINITE) && !(c.err <= S.adapt_tol) && h > dt) {
+                    restore_start(S, c, A, A0, ycur ? Y1 : Y0, C, PHa, tcur);
+                    h *= 0.5;
+                    continue;
+                }
+                if (tid == 0) {
+                    c.steps += 1;
+                    if (!(c.status & MQCT_TRAJ_NONFINITE)) {
+                        if (c.q[0] >= c.r_end && c.q[1] > 0.0) c.done = 1;
+                        else if (c.steps >= c.max_steps) { c.status |= MQCT_TRAJ_MAX_STEPS; c.done = 1; }
                     }
-                    const double R = c.qs[0], PR = c.qs[1], PP = c.qs[3], mu = S.mu;
-                    double l[4] = {PR / mu, F + PP * PP / (mu * R * R * R), c.phidot, T};
+                    c.tcur = tcur + h;
+                }
+                __syncthreads();
+                tcur = c.tcur;
+                if (64.0 * c.err <= S.adapt_tol && h < hmax) h *= 2.0;
+            }
+        } else {
+            while (!c.done) {
+                const int step = c.steps;
+                const double t0 = step * dt;
+                rk4_step(S, c, A, Y0, Y1, ACC, C, W, PHa, PHb, red, t0, dt, (step + 1) * dt, step == 0, ycur);
+                if (tid == 0) {
                     const bool presc = S.flags & MQCT_PRESCRIBED_TRAJ;
-                    if (presc) l[0] = l[1] = l[2] = l[3] = 0.0;  // the motion is prescribed
-                    if (s == 0) {
-                        const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + ER + V;
-                        const double jt = PP + 0.5 * JY;
-                        if (step == 0) { c.e0 = et; c.j0 = jt; }
-                        c.ndev = fmax(c.ndev, fabs(NR - 1.0));
-                        c.edev = fmax(c.edev, fabs(et - c.e0));
-                        c.jdev = fmax(c.jdev, fabs(jt - c.j0));
-                        for (int i = 0; i < 4; ++i) c.lacc[i] = l[i];
-                    } else {
-                        for (int i = 0; i < 4; ++i) c.lacc[i] = fma(wk, l[i], c.lacc[i]);
-                    }
-                    if (s < 3) {
-                        for (int i = 0; i < 4; ++i) c.qs[i] = fma(bn, l[i], c.q[i]);
-                    } else {
-                        for (int i = 0; i < 4; ++i) { c.q[i] = fma(dt / 6.0, c.lacc[i], c.q[i]); c.qs[i] = c.q[i]; }
-                        c.steps = step + 1;
-                        bool fin = isfinite(c.q[0]) && isfinite(c.q[1]) && isfinite(c.q[2]) && isfinite(c.q[3]);
-                        if (!fin) { c.status |= MQCT_TRAJ_NONFINITE; c.done = 1; }
-                        else if (!presc && c.q[0] >= c.r_end && c.q[1] > 0.0) c.done = 1;
+                    c.steps = step + 1;
+                    if (!(c.status & MQCT_TRAJ_NONFINITE)) {
+                        if (!presc && c.q[0] >= c.r_end && c.q[1] > 0.0) c.done = 1;
                         else if (c.steps >= c.max_steps) { c.status |= presc ? 0 : MQCT_TRAJ_MAX_STEPS; c.done = 1; }
                     }
-                    if (presc) {
-                        // R of the next stage on the line (stage times as in the phase factors)
-                        const double tn = s == 3 ? c.steps * dt : (s == 2 ? t0 + dt : t0 + 0.5 * dt);
-                        c.qs[0] = line_r(c, tn);
-                        if (s == 3) c.q[0] = c.qs[0];
-                    }
-                    if (!(c.status & MQCT_TRAJ_NONFINITE)) prepare_stage(S, c);
+                    c.tcur = c.steps * dt;
                 }
-                ycur ^= 1;
                 __syncthreads();
             }
         }
@@ -369,8 +488,9 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
                 double V = 0, NR = 0, ER = 0, JY = 0;
                 for (int w2 = 0; w2 < nwarps; ++w2) { V += red[w2][2]; NR += red[w2][3]; ER += red[w2][4]; JY += red[w2][5]; }
                 const double R = c.q[0], PR = c.q[1], PP = c.q[3], mu = S.mu;
-                const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + ER + V;
-                const double jt = PP + 0.5 * JY;
+                const bool dec = S.flags & MQCT_DECOUPLED_TRAJ;
+                const double et = PR * PR / (2.0 * mu) + PP * PP / (2.0 * mu * R * R) + (dec ? c.vid : ER + V);
+                const double jt = dec ? PP : PP + 0.5 * JY;
                 if (c.steps == 0) { c.e0 = et; c.j0 = jt; }
                 c.ndev = fmax(c.ndev, fabs(NR - 1.0));
                 c.edev = fmax(c.edev, fabs(et - c.e0));
@@ -394,7 +514,7 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate_fp64(PropArgs a)
             mqct_diag d;
             d.steps = c.steps; d.status = c.status;
             d.norm_dev = c.ndev; d.energy_dev = c.edev; d.angmom_dev = c.jdev;
-            d.t_final = c.steps * dt;
+            d.t_final = c.tcur;
             a.diag[t] = d;
         }
         if (a.t_done && tid == 0) a.t_done[t] = mqct_clock_ns();
@@ -658,7 +778,9 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
     int per = (max_slices + maxw - 1) / maxw;
     int nwarps = std::max(4, std::min(maxw, (max_slices + per - 1) / per));
     int threads = nwarps * 32;
-    size_t smem = sizeof(double2) * (6 * (size_t)nmax + 2 * (size_t)maxlev);
+    bool adapt = false;
+    for (int i = 0; i < n_systems; ++i) adapt |= systems[i]->s.h.adapt_tol > 0.0;
+    size_t smem = sizeof(double2) * ((adapt ? 8 : 6) * (size_t)nmax + 2 * (size_t)maxlev);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -671,7 +793,7 @@ extern "C" mqct_status mqct_propagate_ex(const mqct_system *systems, int32_t n_s
     PropArgs pa{};
     pa.sys = dsys; pa.trajs = dtr; pa.order = order; pa.n = n; pa.n_systems = n_systems; pa.queue = queue;
     pa.pop = dpop; pa.amp = damp; pa.diag = ddiag; pa.nmax = nmax; pa.smem_n = nmax; pa.smem_lev = maxlev;
-    pa.t_start = dts; pa.t_done = dtd;
+    pa.t_start = dts; pa.t_done = dtd; pa.adapt = adapt ? 1 : 0;
     k_propagate_fp64<<<grid, threads, smem, st>>>(pa);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_propagate_fp64 launch");

@@ -178,14 +178,27 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     if (d->grid_kind == MQCT_GRID_LOG && d->precision != MQCT_FP64 && d->path == MQCT_PATH_FACTORISED)
         return fail(MQCT_ERR_UNSUPPORTED, "MQCT_GRID_LOG runs on FP64 systems and on the PLAIN path");
     if (!std::isfinite(d->trunc_threshold)) return fail(MQCT_ERR_INVALID_ARG, "non-finite trunc_threshold");
+    if (!std::isfinite(d->adapt_tol) || d->adapt_tol < 0.0) return fail(MQCT_ERR_INVALID_ARG, "adapt_tol must be finite and >= 0");
+    if (d->adapt_tol > 0.0) {
+        const int hm = d->adapt_hmax;
+        if (hm < 0 || hm > 1024 || (hm & (hm - 1)) != 0)
+            return fail(MQCT_ERR_INVALID_ARG, "adapt_hmax must be 0 or a power of 2 up to 1024");
+        if (d->precision != MQCT_FP64) return fail(MQCT_ERR_UNSUPPORTED, "adaptive steps need precision MQCT_FP64");
+        if (d->flags & MQCT_PRESCRIBED_TRAJ)
+            return fail(MQCT_ERR_UNSUPPORTED, "adaptive steps do not run with MQCT_PRESCRIBED_TRAJ");
+    }
     if (d->trunc_threshold > 0.0) {
         if (d->path != MQCT_PATH_PLAIN) return fail(MQCT_ERR_UNSUPPORTED, "truncation needs the PLAIN path");
         if (!(d->trunc_r[0] > 0) || !(d->trunc_r[1] > 0) || !std::isfinite(d->trunc_r[0]) || !std::isfinite(d->trunc_r[1]))
             return fail(MQCT_ERR_INVALID_ARG, "trunc_r must be finite and > 0");
     }
-    if (d->flags & ~MQCT_PRESCRIBED_TRAJ) return fail(MQCT_ERR_INVALID_ARG, "unknown flags");
+    if (d->flags & ~(MQCT_PRESCRIBED_TRAJ | MQCT_DECOUPLED_TRAJ)) return fail(MQCT_ERR_INVALID_ARG, "unknown flags");
+    if ((d->flags & MQCT_PRESCRIBED_TRAJ) && (d->flags & MQCT_DECOUPLED_TRAJ))
+        return fail(MQCT_ERR_INVALID_ARG, "MQCT_PRESCRIBED_TRAJ and MQCT_DECOUPLED_TRAJ exclude each other");
     if ((d->flags & MQCT_PRESCRIBED_TRAJ) && d->precision != MQCT_FP64)
         return fail(MQCT_ERR_UNSUPPORTED, "MQCT_PRESCRIBED_TRAJ needs precision MQCT_FP64");
+    if ((d->flags & MQCT_DECOUPLED_TRAJ) && d->precision != MQCT_FP64)
+        return fail(MQCT_ERR_UNSUPPORTED, "MQCT_DECOUPLED_TRAJ needs precision MQCT_FP64");
     if (P < 0 || (P > 0 && (!d->dv_dparam || !d->ddv_ends))) return fail(MQCT_ERR_INVALID_ARG, "bad parameter tables");
     if (!d->G && d->g_nnz > 0 && (!d->g_term || !d->g_row || !d->g_col || !d->g_val))
         return fail(MQCT_ERR_INVALID_ARG, "NULL triplet array");
@@ -320,6 +333,20 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     for (int l = 0; l < L; ++l)
         for (auto &row : grows[l]) std::sort(row.begin(), row.end(), [](const Entry &a, const Entry &b) { return a.c < b.c; });
 
+    // ---- terms whose G is the identity (the isotropic part of the potential, e.g. lambda = 0 of a
+    // Legendre expansion), up to the rounding of their construction
+    unsigned long long iso_mask = 0;
+    for (int l = 0; l < L; ++l) {
+        bool ident = true;
+        for (int r = 0; r < n && ident; ++r)
+            if (grows[l][r].size() != 1 || grows[l][r][0].c != r || std::fabs(grows[l][r][0].v - 1.0) > 1e-13) ident = false;
+        if (ident) iso_mask |= 1ull << l;
+    }
+    if ((d->flags & MQCT_DECOUPLED_TRAJ) && !iso_mask) {
+        delete hs;
+        return fail(MQCT_ERR_INVALID_ARG, "MQCT_DECOUPLED_TRAJ needs an expansion term whose G is the identity");
+    }
+
     // ---- truncation (Sec. III): M_rc = sum_l G^l_rc v_l(R) from the splines at the two
     // reference distances; an element at or below the threshold at both is dropped from every term
     int64_t n_dropped = 0;
@@ -365,6 +392,9 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     D.path = d->path; D.precision = d->precision; D.flags = d->flags;
     D.mu = d->mu; D.r_min = d->r_min; D.h = h; D.inv_h = 1.0 / h;
     D.grid_log = glog ? 1 : 0; D.x0 = x0;
+    D.id_mask = iso_mask;
+    D.adapt_tol = d->adapt_tol;
+    D.adapt_hmax = d->adapt_tol > 0.0 ? (d->adapt_hmax > 0 ? (double)d->adapt_hmax : 16.0) : 1.0;
 
     mqct_status st = MQCT_OK;
     auto up_ = [&](auto &v, auto **dst) { if (st == MQCT_OK) st = upload(S, v, dst); };

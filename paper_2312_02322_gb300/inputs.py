@@ -317,3 +317,44 @@ def sparse_pes_params(jmax=200, lam_max=12, n_grid=63, mu_amu=1.8, bconst_cm=Non
 # the paper's truncation (Sec. III): |M| > 1 cm^-1 at R = 6.03 or 7.11 bohr
 PAPER_TRUNC_CM = 1.0
 PAPER_TRUNC_R = (6.03, 7.11)
+
+
+@dataclass
+class MolMolParams:
+    """Asymmetric top + linear rotor (Sec. II, Eqs. 3 and 13): molecule-1 levels j1 <= j1max, rotor
+    j2 values, PES terms (lam1, mu1, lam2, lam) with v_t = coef_t exp(-beta_t R) (+ damped C6 on term 0)."""
+    A: float
+    B: float
+    C: float
+    j1max: int
+    bconst2: float
+    j2: list
+    mu: float
+    terms: list               # (lam1, mu1, lam2, lam)
+    coef: np.ndarray          # hartree
+    beta: np.ndarray          # 1/bohr
+    c6: float
+    rd: float = 3.0
+    n_grid: int = 200
+    r_min: float = 2.0
+    r_max: float = 30.0
+
+    @property
+    def n_terms(self) -> int:
+        return len(self.terms)
+
+
+def molmol_params(j1max=2, j2=(0, 2), n_grid=200):
+    """Water-like top (A, B, C = 27.88, 14.51, 9.28 cm^-1) + para-H2 (B = 60.85 cm^-1, j2 in {0, 2}),
+    mu = 1.8 amu; terms: the isotropic (0,0,0,0) -- whose tau is 1/(2 pi), so its coefficient is
+    2 pi x (2e5 cm^-1) exp(-1.8 R) with the damped C6 = 3e5 cm^-1 bohr^6 -- and eight anisotropic
+    (lam1, mu1, lam2, lam) terms with lam1, lam2 <= 2 and coefficients 2e4 / (1 + lam1 + lam2) cm^-1,
+    beta = 1.9 + 0.1 (lam1 + lam2) bohr^-1 (a stand-in for the H2O + H2 PES, which is not available)."""
+    terms = [(0, 0, 0, 0), (1, 0, 0, 1), (1, 1, 0, 1), (2, 0, 0, 2), (2, 2, 0, 2), (0, 0, 2, 2), (1, 0, 2, 1),
+             (2, 0, 2, 0), (2, 2, 2, 2)]
+    coef = [2 * np.pi * 2e5] + [2e4 / (1 + a + b) for (a, _, b, _) in terms[1:]]
+    beta = [1.8] + [1.9 + 0.1 * (a + b) for (a, _, b, _) in terms[1:]]
+    return MolMolParams(A=float(cm(27.88)), B=float(cm(14.51)), C=float(cm(9.28)), j1max=j1max,
+                        bconst2=float(cm(60.85)), j2=list(j2), mu=1.8 * AMU_ME, terms=terms, coef=cm(coef),
+                        beta=np.array(beta), c6=float(cm(3e5) * 2 * np.pi), n_grid=n_grid)
+

@@ -271,3 +271,55 @@ def test_grid_and_truncation_validation(L, path, prec, grid, thr, status, needle
     assert needle in L.mqct_last_error()
     assert not h.value
     api.lib().mqct_free_desc(C.byref(d))
+
+
+@pytest.mark.parametrize("flags,prec,status,needle", [
+    (api.PRESCRIBED_TRAJ | api.DECOUPLED_TRAJ, api.FP64, api.ERR_INVALID_ARG, b"exclude"),
+    (api.DECOUPLED_TRAJ, api.FP32, api.ERR_UNSUPPORTED, b"DECOUPLED"),
+])
+def test_decoupled_flag_validation(L, flags, prec, status, needle):
+    d, _ = build_desc(2, path="factorised")
+    d.flags = flags
+    d.precision = prec
+    h = C.c_void_p()
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == status
+    assert needle in L.mqct_last_error()
+    assert not h.value
+    api.lib().mqct_free_desc(C.byref(d))
+
+
+def _oracle_molmol(ora, p):
+    lev_J, lev_E, lev_b = [], [], []
+    for J in range(p.j1max + 1):
+        E, b = ora.asym_levels(J, p.A, p.B, p.C)
+        for e_, bb in zip(E, b):
+            row = np.zeros(2 * p.j1max + 1)
+            row[p.j1max - J:p.j1max + J + 1] = bb
+            lev_J.append(J); lev_E.append(e_); lev_b.append(row)
+    lev_J = np.array(lev_J, np.int32)
+    e, lev, jt, mt, l1, j2 = ora.molmol_states(lev_J, p.j2, lev_E, p.bconst2)
+    G = np.stack([ora.molmol_G(lev_J, np.array(lev_b), p.j1max, l1, j2, jt, mt, *t) for t in p.terms])
+    return e, lev, jt, mt, G
+
+
+@pytest.mark.parametrize("j1max,j2", [(2, (0, 2)), (3, (0, 1, 2))])
+def test_molmol_builder_matches_oracle(L, ora, j1max, j2):
+    """Asymmetric top + linear rotor: the library's composite states (Eq. 3) and coupling -- its own
+    Clebsch-Gordan coefficients by the lowering-operator construction and its one-molecule integrals
+    by quadrature -- agree with the oracle's Racah-formula algebra of Eqs. 15-17."""
+    p = inputs.molmol_params(j1max=j1max, j2=j2)
+    mp = api.System.molmol_params(p)
+    d = api.Desc()
+    assert L.mqct_build_molmol(C.byref(mp), C.byref(d)) == 0
+    n = d.n_states
+    arr = lambda ptr, t: np.ctypeslib.as_array(C.cast(ptr, C.POINTER(t)), (n,))
+    e, lev, jt, mt, Go = _oracle_molmol(ora, p)
+    assert n == len(e)
+    assert np.allclose(arr(d.energy, C.c_double), e, rtol=1e-13, atol=0)
+    assert np.array_equal(arr(d.level, C.c_int32), lev)
+    assert np.array_equal(arr(d.j, C.c_int32), jt)
+    assert np.array_equal(arr(d.m, C.c_int32), mt)
+    G = dense_G(d)
+    for t in range(p.n_terms):
+        assert np.max(np.abs(G[t] - Go[t])) < 1e-12, p.terms[t]
+    api.lib().mqct_free_desc(C.byref(d))
