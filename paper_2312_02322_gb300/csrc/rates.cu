@@ -16,7 +16,8 @@
 //
 // One thread per (unordered pair of levels, temperature).  The spline's second derivatives are
 // a fixed linear map of the knot values (set up on the host from the energy grid), the finite
-// pieces are integrated by 16-point Gauss-Legendre panels no wider than 4 kT, and the integrand
+// pieces are integrated by 16-point Gauss-Legendre panels no wider than 4 kT (the exponential at the
+// nodes as a panel factor times node factors shared by the panels of a piece), and the integrand
 // carries exp(-(U - u0)/kT) so that neither exponential factor of R2 overflows.
 #include <cuda_runtime.h>
 
@@ -127,9 +128,16 @@ __global__ void __launch_bounds__(128) k_rates(const __grid_constant__ RateArgs 
         const int np = (int)fmin(256.0, fmax(1.0, ceil((hi - lo) * 0.25 * ith)));
         const double hp = (hi - lo) / np;
         const double h = kind ? A.u[k + 1] - A.u[k] : 0.0;
+        // exp(-(U - u0)/kT) = exp(-(c - u0)/kT) exp(-(hp/2) x_j / kT): the node factors are the same
+        // for every panel of the piece
+        double ef[kGl];
+#pragma unroll
+        for (int j = 0; j < kGl; ++j) ef[j] = exp(-0.5 * hp * A.gx[j] * ith);
         for (int p = 0; p < np; ++p) {
             const double c = lo + hp * (p + 0.5);
+            const double ec = exp(-(c - u0) * ith);
             double s = 0.0;
+#pragma unroll
             for (int j = 0; j < kGl; ++j) {
                 const double U = fma(0.5 * hp, A.gx[j], c);
                 double v;
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(128) k_rates(const __grid_constant__ RateArgs 
                         h * h * (1.0 / 6.0) * ((st * st * st - st) * M[k] + (tt * tt * tt - tt) * M[k + 1]);
                     v = fmax(v, 0.0);
                 }
-                s = fma(A.gw[j], v * U * exp(-(U - u0) * ith), s);
+                s = fma(A.gw[j], v * U * (ec * ef[j]), s);
             }
             acc = fma(0.5 * hp, s, acc);
         }

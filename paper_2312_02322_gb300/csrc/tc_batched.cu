@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
 // partial sums of force, torque and diagnostics over the 256 rows (compensated FP32 across warps).
 constexpr int kSpWarps = 8, kSpTile = 32;
 
-__global__ void __launch_bounds__(32 * kSpWarps, 4) k_sp_stage(TcState T, int s, int cur)
+__global__ void __launch_bounds__(32 * kSpWarps, 3) k_sp_stage(TcState T, int s, int cur)
 {
     const DevSys &S = *T.sys;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -477,59 +477,89 @@ __global__ void __launch_bounds__(32 * kSpWarps, 4) k_sp_stage(TcState T, int s,
         const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
         const int off = S.sl_off[slice], width = (S.sl_off[slice + 1] - off) / kSlice;
         const int r_end = min(S.n, (slice + 1) * kSlice);
-        for (int r = slice * kSlice; r < r_end; ++r) {
-            const int rl = r - slice * kSlice;
-            float2 w = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
+        // two rows at a time (rows of one slice share the ELL width): twice the loads in flight
+        for (int r0 = slice * kSlice; r0 < r_end; r0 += 2) {
+            const int nr = r0 + 1 < r_end ? 2 : 1;
+            float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 u[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             if (need) {
+                const size_t base0 = (size_t)off + (size_t)(r0 - slice * kSlice);
                 int e = 0;
-                for (; e + 4 <= width; e += 4) {
-                    int col[4];
-                    float4 c[4];
-                    float2 z[4];
+                for (; e + 2 <= width; e += 2) {
+                    int col[2][2];
+                    float4 c[2][2];
+                    float2 z[2][2];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const size_t ei = (size_t)off + (size_t)(e + i) * kSlice + rl;
-                        col[i] = __ldg(S.cols + ei);
-                        c[i] = __ldg(tab + ei);
-                    }
+                    for (int q = 0; q < 2; ++q)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) z[i] = __ldg(Cc + (size_t)col[i] * T.S + sl);
+                        for (int i = 0; i < 2; ++i) {
+                            const size_t ei = base0 + q + (size_t)(e + i) * kSlice;
+                            const bool okq = q < nr;
+                            col[q][i] = okq ? __ldg(S.cols + ei) : 0;
+                            c[q][i] = okq ? __ldg(tab + ei) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float m = fmaf(fmaf(fmaf(c[i].w, x, c[i].z), x, c[i].y), x, c[i].x);
-                        const float md = fmaf(fmaf(3.0f * c[i].w, x, 2.0f * c[i].z), x, c[i].y);
-                        w.x = fmaf(m, z[i].x, w.x);
-                        w.y = fmaf(m, z[i].y, w.y);
-                        u.x = fmaf(md, z[i].x, u.x);
-                        u.y = fmaf(md, z[i].y, u.y);
-                    }
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) z[q][i] = __ldg(Cc + (size_t)col[q][i] * T.S + sl);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const float4 cc = c[q][i];
+                            const float m = fmaf(fmaf(fmaf(cc.w, x, cc.z), x, cc.y), x, cc.x);
+                            const float md = fmaf(fmaf(3.0f * cc.w, x, 2.0f * cc.z), x, cc.y);
+                            w[q].x = fmaf(m, z[q][i].x, w[q].x);
+                            w[q].y = fmaf(m, z[q][i].y, w[q].y);
+                            u[q].x = fmaf(md, z[q][i].x, u[q].x);
+                            u[q].y = fmaf(md, z[q][i].y, u[q].y);
+                        }
                 }
-                for (; e < width; ++e) {
-                    const size_t ei = (size_t)off + (size_t)e * kSlice + rl;
-                    const float4 c = __ldg(tab + ei);
-                    const float2 z = __ldg(Cc + (size_t)__ldg(S.cols + ei) * T.S + sl);
-                    const float m = fmaf(fmaf(fmaf(c.w, x, c.z), x, c.y), x, c.x);
-                    const float md = fmaf(fmaf(3.0f * c.w, x, 2.0f * c.z), x, c.y);
-                    w.x = fmaf(m, z.x, w.x);
-                    w.y = fmaf(m, z.y, w.y);
-                    u.x = fmaf(md, z.x, u.x);
-                    u.y = fmaf(md, z.y, u.y);
-                }
+                for (; e < width; ++e)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (q >= nr) break;
+                        const size_t ei = base0 + q + (size_t)e * kSlice;
+                        const float4 cc = __ldg(tab + ei);
+                        const float2 z = __ldg(Cc + (size_t)__ldg(S.cols + ei) * T.S + sl);
+                        const float m = fmaf(fmaf(fmaf(cc.w, x, cc.z), x, cc.y), x, cc.x);
+                        const float md = fmaf(fmaf(3.0f * cc.w, x, 2.0f * cc.z), x, cc.y);
+                        w[q].x = fmaf(m, z.x, w[q].x);
+                        w[q].y = fmaf(m, z.y, w[q].y);
+                        u[q].x = fmaf(md, z.x, u[q].x);
+                        u[q].y = fmaf(md, z.y, u[q].y);
+                    }
             }
             if (st == TS_IDLE) continue;
-            const int lev = __ldg(S.lev + r);
-            const size_t e0 = (size_t)r * T.S + sl;
-            const float2 c = __ldg(Cc + e0);
-            const float2 cu = __ldg(Cc + (size_t)__ldg(S.up + r) * T.S + sl);
-            const float2 cd = __ldg(Cc + (size_t)__ldg(S.dn + r) * T.S + sl);
-            const float2 p = __ldg(PHc + (size_t)lev * T.S + sl), q = __ldg(PHn + (size_t)lev * T.S + sl);
-            const float2 a0 = T.A[e0], acc = T.ACC[e0];
-            const float au = __ldg(S.aupf + r), ad = __ldg(S.adnf + r), elev = S.lev_energy_f[lev];
-            const float2 uu = make_float2(u.x * dv, u.y * dv);
-            float2 ao, acco, co;
-            const int mode = elem_core(s, st, r == row0, c, cu, cd, p, q, a0, acc, au, ad, elev, hp, dtj, w, uu, part,
-                                       ao, acco, co);
-            elem_store(T, S, cur, r, sl, mode, ao, acco, co);
+            // element update of both rows: every load first
+            float2 c[2], cu[2], cd[2], pp[2], qq[2], a0[2], acc[2];
+            float au[2], ad[2], elev[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int r = q < nr ? r0 + q : r0;
+                const int lev = __ldg(S.lev + r);
+                const size_t e0 = (size_t)r * T.S + sl;
+                c[q] = __ldg(Cc + e0);
+                cu[q] = __ldg(Cc + (size_t)__ldg(S.up + r) * T.S + sl);
+                cd[q] = __ldg(Cc + (size_t)__ldg(S.dn + r) * T.S + sl);
+                pp[q] = __ldg(PHc + (size_t)lev * T.S + sl);
+                qq[q] = __ldg(PHn + (size_t)lev * T.S + sl);
+                a0[q] = T.A[e0];
+                acc[q] = T.ACC[e0];
+                au[q] = __ldg(S.aupf + r);
+                ad[q] = __ldg(S.adnf + r);
+                elev[q] = S.lev_energy_f[lev];
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q >= nr) break;
+                const int r = r0 + q;
+                const float2 uu = make_float2(u[q].x * dv, u[q].y * dv);
+                float2 ao, acco, co;
+                const int mode = elem_core(s, st, r == row0, c[q], cu[q], cd[q], pp[q], qq[q], a0[q], acc[q], au[q],
+                                           ad[q], elev[q], hp, dtj, w[q], uu, part, ao, acco, co);
+                elem_store(T, S, cur, r, sl, mode, ao, acco, co);
+            }
         }
     }
 #pragma unroll
@@ -883,6 +913,95 @@ __global__ void __launch_bounds__(128) k_tc_slots(TcState T, int s, int n_rowblo
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// PLAIN path, at the end of a chunk of steps: the slots are reordered by spline interval so that the
+// 32 slots of a stage-kernel tile mostly read the same rows of the table (one transaction per element
+// instead of one per slot); idle slots go last.  perm[new] = old by a stable counting sort (one
+// thread: S <= 8192), then every per-slot and per-(row, slot) array is gathered into scratch and
+// copied back.
+struct SpSort {
+    int *perm, *cnt;            // [S], [n_int + 2]
+    TSlot *slot;                // scratch copies
+    double *Q, *QS, *LACC;      // [4][S]
+    int *state, *kint;
+    float *hp, *dtf, *xs, *dinv;
+    unsigned long long *inc;    // [n_levels][S]
+    float2 *PHa, *PHb;          // [n_levels][S]
+    float2 *A, *ACC;            // [n][S]; C[0] goes through C[1]
+};
+
+__global__ void k_sp_order(TcState T, SpSort P, int n_int)
+{
+    if (threadIdx.x != 0) return;
+    const int S = T.S, nb = n_int + 1;  // bucket n_int: idle slots
+    for (int b = 0; b <= nb; ++b) P.cnt[b] = 0;
+    for (int i = 0; i < S; ++i) {
+        const int k = T.state[i] == TS_IDLE ? n_int : min(max(T.kint[i], 0), n_int - 1);
+        P.cnt[k + 1] += 1;
+    }
+    for (int b = 1; b <= nb; ++b) P.cnt[b] += P.cnt[b - 1];
+    for (int i = 0; i < S; ++i) {
+        const int k = T.state[i] == TS_IDLE ? n_int : min(max(T.kint[i], 0), n_int - 1);
+        P.perm[P.cnt[k]++] = i;
+    }
+}
+
+// gather into scratch (dir 0) or copy back (dir 1): per-slot arrays, one thread per slot
+__global__ void k_sp_move_slots(TcState T, SpSort P, int n_levels, int dir)
+{
+    const int S = T.S;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+        const int o = dir == 0 ? P.perm[i] : i;
+        if (dir == 0) {
+            P.slot[i] = T.slot[o];
+            for (int c = 0; c < 4; ++c) {
+                P.Q[(size_t)c * S + i] = T.Q[(size_t)c * S + o];
+                P.QS[(size_t)c * S + i] = T.QS[(size_t)c * S + o];
+                P.LACC[(size_t)c * S + i] = T.LACC[(size_t)c * S + o];
+            }
+            P.state[i] = T.state[o]; P.kint[i] = T.kint[o];
+            P.hp[i] = T.hp[o]; P.dtf[i] = T.dtf[o]; P.xs[i] = T.xs[o]; P.dinv[i] = T.dinv[o];
+            for (int l = 0; l < n_levels; ++l) {
+                P.inc[(size_t)l * S + i] = T.inc[(size_t)l * S + o];
+                P.PHa[(size_t)l * S + i] = T.PHa[(size_t)l * S + o];
+                P.PHb[(size_t)l * S + i] = T.PHb[(size_t)l * S + o];
+            }
+        } else {
+            T.slot[i] = P.slot[i];
+            for (int c = 0; c < 4; ++c) {
+                T.Q[(size_t)c * S + i] = P.Q[(size_t)c * S + i];
+                T.QS[(size_t)c * S + i] = P.QS[(size_t)c * S + i];
+                T.LACC[(size_t)c * S + i] = P.LACC[(size_t)c * S + i];
+            }
+            T.state[i] = P.state[i]; T.kint[i] = P.kint[i];
+            T.hp[i] = P.hp[i]; T.dtf[i] = P.dtf[i]; T.xs[i] = P.xs[i]; T.dinv[i] = P.dinv[i];
+            for (int l = 0; l < n_levels; ++l) {
+                T.inc[(size_t)l * S + i] = P.inc[(size_t)l * S + i];
+                T.PHa[(size_t)l * S + i] = P.PHa[(size_t)l * S + i];
+                T.PHb[(size_t)l * S + i] = P.PHb[(size_t)l * S + i];
+            }
+        }
+    }
+}
+
+// gather (dir 0: A, ACC into scratch, C[0] into C[1]) or copy back (dir 1), one thread per element
+__global__ void k_sp_move_rows(TcState T, SpSort P, int n, int dir)
+{
+    const size_t S = T.S, total = (size_t)n * S;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        if (dir == 0) {
+            const size_t r = e / S, i = e % S, o = r * S + P.perm[i];
+            P.A[e] = T.A[o];
+            P.ACC[e] = T.ACC[o];
+            T.C[1][e] = T.C[0][o];
+        } else {
+            T.A[e] = P.A[e];
+            T.ACC[e] = P.ACC[e];
+            T.C[0][e] = T.C[1][e];
+        }
+    }
+}
+
 // the condition of the graph's WHILE node at the end of a chunk of steps: run another chunk while
 // trajectories are live and no bounded wait has run out
 __global__ void k_tc_continue(TcState T, cudaGraphConditionalHandle h)
@@ -967,10 +1086,29 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     get((void **)&T.QS, sizeof(double) * 4 * (size_t)S);
     get((void **)&T.LACC, sizeof(double) * 4 * (size_t)S);
     get((void **)&T.slot, sizeof(TSlot) * (size_t)S);
+    SpSort P;
+    std::memset(&P, 0, sizeof(P));
     if (plain) {
         get((void **)&T.kint, sizeof(int) * (size_t)S);
         get((void **)&T.xs, sizeof(float) * (size_t)S);
         get((void **)&T.dinv, sizeof(float) * (size_t)S);
+        get((void **)&P.perm, sizeof(int) * (size_t)S);
+        get((void **)&P.cnt, sizeof(int) * (size_t)(h.n_int + 2));
+        get((void **)&P.slot, sizeof(TSlot) * (size_t)S);
+        get((void **)&P.Q, sizeof(double) * 4 * (size_t)S);
+        get((void **)&P.QS, sizeof(double) * 4 * (size_t)S);
+        get((void **)&P.LACC, sizeof(double) * 4 * (size_t)S);
+        get((void **)&P.state, sizeof(int) * (size_t)S);
+        get((void **)&P.kint, sizeof(int) * (size_t)S);
+        get((void **)&P.hp, sizeof(float) * (size_t)S);
+        get((void **)&P.dtf, sizeof(float) * (size_t)S);
+        get((void **)&P.xs, sizeof(float) * (size_t)S);
+        get((void **)&P.dinv, sizeof(float) * (size_t)S);
+        get((void **)&P.inc, sizeof(unsigned long long) * (size_t)h.n_levels * S);
+        get((void **)&P.PHa, sizeof(float2) * (size_t)h.n_levels * S);
+        get((void **)&P.PHb, sizeof(float2) * (size_t)h.n_levels * S);
+        get((void **)&P.A, sizeof(float2) * ns);
+        get((void **)&P.ACC, sizeof(float2) * ns);
     }
     if (e != cudaSuccess) {
         cleanup();
@@ -990,6 +1128,16 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     auto stage = [&](cudaStream_t q, int s, int cur) {
         if (plain) k_sp_stage<<<dim3(S / kSpTile, n_rowblocks), 32 * kSpWarps, 0, q>>>(T, s, cur);
         else k_tc_stage<<<h.n_tiles * n_ct, kTcThreads, smem, q>>>(T, s, cur);
+    };
+    // PLAIN path: the slots sorted by interval at the end of each chunk
+    const int mv_blocks = (int)std::min<size_t>((ns + 255) / 256, (size_t)sms * 16);
+    auto sort_slots = [&](cudaStream_t q) {
+        if (!plain) return;
+        k_sp_order<<<1, 32, 0, q>>>(T, P, h.n_int);
+        k_sp_move_slots<<<(S + 127) / 128, 128, 0, q>>>(T, P, h.n_levels, 0);
+        k_sp_move_rows<<<mv_blocks, 256, 0, q>>>(T, P, n, 0);
+        k_sp_move_slots<<<(S + 127) / 128, 128, 0, q>>>(T, P, h.n_levels, 1);
+        k_sp_move_rows<<<mv_blocks, 256, 0, q>>>(T, P, n, 1);
     };
     // chunks of steps inside a WHILE node: the body (one chunk) ends with k_tc_continue, which
     // sets the condition from the live-slot count; one launch of the graph runs every trajectory
@@ -1012,6 +1160,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
                 stage(st, s, cur);
                 k_tc_slots<<<slot_blocks, 128, 0, st>>>(T, s, n_rowblocks);
             }
+        sort_slots(st);
         k_tc_continue<<<1, 32, 0, st>>>(T, 0);
         if ((e = cudaMemcpyAsync(live, T.live, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
             e = cudaStreamSynchronize(st);
@@ -1039,6 +1188,7 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
                 stage(cap, s, cur);
                 k_tc_slots<<<slot_blocks, 128, 0, cap>>>(T, s, n_rowblocks);
             }
+        sort_slots(cap);
         k_tc_continue<<<1, 32, 0, cap>>>(T, cond);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(cap, &captured);
@@ -1052,8 +1202,9 @@ mqct_status run_tc_batched(const BatchArgs &a, const DevSys &h, cudaStream_t st)
     if (cap) cudaStreamDestroy(cap);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core path");
-    // k_tc_init, then per chunk: reset, chunk x 4 x (stage, slots), continue
-    count_launches(1 + (long long)live[2] * (2 + 8 * chunk));
+    // k_tc_init, then per chunk: reset, chunk x 4 x (stage, slots), (PLAIN: the five sorting
+    // kernels), continue
+    count_launches(1 + (long long)live[2] * (2 + 8 * chunk + (plain ? 5 : 0)));
     if (live[1]) return fail(MQCT_ERR_TIMEOUT, "tensor-core path: a bounded MMA completion wait ran out");
     return MQCT_OK;
 }
