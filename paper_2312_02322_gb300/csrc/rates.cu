@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(128) k_rates(const __grid_constant__ RateArgs 
         const int np = (int)fmin(256.0, fmax(1.0, ceil((hi - lo) * 0.25 * ith)));
         const double hp = (hi - lo) / np;
         const double h = kind ? A.u[k + 1] - A.u[k] : 0.0;
+        // reciprocals once per piece (an FP64 division costs ~10 FMA slots on this GPU's FP64 pipe)
+        const double ih = kind ? 1.0 / h : 0.0, iramp = kind ? 0.0 : y[0] / (A.u[0] - u0);
+        const double h26 = h * h * (1.0 / 6.0);
         // exp(-(U - u0)/kT) = exp(-(c - u0)/kT) exp(-(hp/2) x_j / kT): the node factors are the same
         // for every panel of the piece
         double ef[kGl];
@@ -142,11 +145,10 @@ __global__ void __launch_bounds__(128) k_rates(const __grid_constant__ RateArgs 
                 const double U = fma(0.5 * hp, A.gx[j], c);
                 double v;
                 if (kind == 0) {
-                    v = y[0] * (U - u0) / (A.u[0] - u0);
+                    v = (U - u0) * iramp;
                 } else {
-                    const double tt = (U - A.u[k]) / h, st = 1.0 - tt;
-                    v = st * y[k] + tt * y[k + 1] +
-                        h * h * (1.0 / 6.0) * ((st * st * st - st) * M[k] + (tt * tt * tt - tt) * M[k + 1]);
+                    const double tt = (U - A.u[k]) * ih, st = 1.0 - tt;
+                    v = st * y[k] + tt * y[k + 1] + h26 * ((st * st * st - st) * M[k] + (tt * tt * tt - tt) * M[k + 1]);
                     v = fmax(v, 0.0);
                 }
                 s = fma(A.gw[j], v * U * (ec * ef[j]), s);

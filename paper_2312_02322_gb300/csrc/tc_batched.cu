@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stage(TcState T, int s, in
 // partial sums of force, torque and diagnostics over the 256 rows (compensated FP32 across warps).
 constexpr int kSpWarps = 8, kSpTile = 32;
 
-__global__ void __launch_bounds__(32 * kSpWarps, 3) k_sp_stage(TcState T, int s, int cur)
+__global__ void __launch_bounds__(32 * kSpWarps, 4) k_sp_stage(TcState T, int s, int cur)
 {
     const DevSys &S = *T.sys;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -477,89 +477,59 @@ __global__ void __launch_bounds__(32 * kSpWarps, 3) k_sp_stage(TcState T, int s,
         const float2 *PHn = (s == 0 || s == 1) ? T.PHb : T.PHa;
         const int off = S.sl_off[slice], width = (S.sl_off[slice + 1] - off) / kSlice;
         const int r_end = min(S.n, (slice + 1) * kSlice);
-        // two rows at a time (rows of one slice share the ELL width): twice the loads in flight
-        for (int r0 = slice * kSlice; r0 < r_end; r0 += 2) {
-            const int nr = r0 + 1 < r_end ? 2 : 1;
-            float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-            float2 u[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        for (int r = slice * kSlice; r < r_end; ++r) {
+            const int rl = r - slice * kSlice;
+            float2 w = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
             if (need) {
-                const size_t base0 = (size_t)off + (size_t)(r0 - slice * kSlice);
                 int e = 0;
-                for (; e + 2 <= width; e += 2) {
-                    int col[2][2];
-                    float4 c[2][2];
-                    float2 z[2][2];
+                for (; e + 4 <= width; e += 4) {
+                    int col[4];
+                    float4 c[4];
+                    float2 z[4];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q)
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) {
-                            const size_t ei = base0 + q + (size_t)(e + i) * kSlice;
-                            const bool okq = q < nr;
-                            col[q][i] = okq ? __ldg(S.cols + ei) : 0;
-                            c[q][i] = okq ? __ldg(tab + ei) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) z[q][i] = __ldg(Cc + (size_t)col[q][i] * T.S + sl);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) {
-                            const float4 cc = c[q][i];
-                            const float m = fmaf(fmaf(fmaf(cc.w, x, cc.z), x, cc.y), x, cc.x);
-                            const float md = fmaf(fmaf(3.0f * cc.w, x, 2.0f * cc.z), x, cc.y);
-                            w[q].x = fmaf(m, z[q][i].x, w[q].x);
-                            w[q].y = fmaf(m, z[q][i].y, w[q].y);
-                            u[q].x = fmaf(md, z[q][i].x, u[q].x);
-                            u[q].y = fmaf(md, z[q][i].y, u[q].y);
-                        }
-                }
-                for (; e < width; ++e)
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        if (q >= nr) break;
-                        const size_t ei = base0 + q + (size_t)e * kSlice;
-                        const float4 cc = __ldg(tab + ei);
-                        const float2 z = __ldg(Cc + (size_t)__ldg(S.cols + ei) * T.S + sl);
-                        const float m = fmaf(fmaf(fmaf(cc.w, x, cc.z), x, cc.y), x, cc.x);
-                        const float md = fmaf(fmaf(3.0f * cc.w, x, 2.0f * cc.z), x, cc.y);
-                        w[q].x = fmaf(m, z.x, w[q].x);
-                        w[q].y = fmaf(m, z.y, w[q].y);
-                        u[q].x = fmaf(md, z.x, u[q].x);
-                        u[q].y = fmaf(md, z.y, u[q].y);
+                    for (int i = 0; i < 4; ++i) {
+                        const size_t ei = (size_t)off + (size_t)(e + i) * kSlice + rl;
+                        col[i] = __ldg(S.cols + ei);
+                        c[i] = __ldg(tab + ei);
                     }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) z[i] = __ldg(Cc + (size_t)col[i] * T.S + sl);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float m = fmaf(fmaf(fmaf(c[i].w, x, c[i].z), x, c[i].y), x, c[i].x);
+                        const float md = fmaf(fmaf(3.0f * c[i].w, x, 2.0f * c[i].z), x, c[i].y);
+                        w.x = fmaf(m, z[i].x, w.x);
+                        w.y = fmaf(m, z[i].y, w.y);
+                        u.x = fmaf(md, z[i].x, u.x);
+                        u.y = fmaf(md, z[i].y, u.y);
+                    }
+                }
+                for (; e < width; ++e) {
+                    const size_t ei = (size_t)off + (size_t)e * kSlice + rl;
+                    const float4 c = __ldg(tab + ei);
+                    const float2 z = __ldg(Cc + (size_t)__ldg(S.cols + ei) * T.S + sl);
+                    const float m = fmaf(fmaf(fmaf(c.w, x, c.z), x, c.y), x, c.x);
+                    const float md = fmaf(fmaf(3.0f * c.w, x, 2.0f * c.z), x, c.y);
+                    w.x = fmaf(m, z.x, w.x);
+                    w.y = fmaf(m, z.y, w.y);
+                    u.x = fmaf(md, z.x, u.x);
+                    u.y = fmaf(md, z.y, u.y);
+                }
             }
             if (st == TS_IDLE) continue;
-            // element update of both rows: every load first
-            float2 c[2], cu[2], cd[2], pp[2], qq[2], a0[2], acc[2];
-            float au[2], ad[2], elev[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int r = q < nr ? r0 + q : r0;
-                const int lev = __ldg(S.lev + r);
-                const size_t e0 = (size_t)r * T.S + sl;
-                c[q] = __ldg(Cc + e0);
-                cu[q] = __ldg(Cc + (size_t)__ldg(S.up + r) * T.S + sl);
-                cd[q] = __ldg(Cc + (size_t)__ldg(S.dn + r) * T.S + sl);
-                pp[q] = __ldg(PHc + (size_t)lev * T.S + sl);
-                qq[q] = __ldg(PHn + (size_t)lev * T.S + sl);
-                a0[q] = T.A[e0];
-                acc[q] = T.ACC[e0];
-                au[q] = __ldg(S.aupf + r);
-                ad[q] = __ldg(S.adnf + r);
-                elev[q] = S.lev_energy_f[lev];
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q >= nr) break;
-                const int r = r0 + q;
-                const float2 uu = make_float2(u[q].x * dv, u[q].y * dv);
-                float2 ao, acco, co;
-                const int mode = elem_core(s, st, r == row0, c[q], cu[q], cd[q], pp[q], qq[q], a0[q], acc[q], au[q],
-                                           ad[q], elev[q], hp, dtj, w[q], uu, part, ao, acco, co);
-                elem_store(T, S, cur, r, sl, mode, ao, acco, co);
-            }
+            const int lev = __ldg(S.lev + r);
+            const size_t e0 = (size_t)r * T.S + sl;
+            const float2 c = __ldg(Cc + e0);
+            const float2 cu = __ldg(Cc + (size_t)__ldg(S.up + r) * T.S + sl);
+            const float2 cd = __ldg(Cc + (size_t)__ldg(S.dn + r) * T.S + sl);
+            const float2 p = __ldg(PHc + (size_t)lev * T.S + sl), q = __ldg(PHn + (size_t)lev * T.S + sl);
+            const float2 a0 = T.A[e0], acc = T.ACC[e0];
+            const float au = __ldg(S.aupf + r), ad = __ldg(S.adnf + r), elev = S.lev_energy_f[lev];
+            const float2 uu = make_float2(u.x * dv, u.y * dv);
+            float2 ao, acco, co;
+            const int mode = elem_core(s, st, r == row0, c, cu, cd, p, q, a0, acc, au, ad, elev, hp, dtj, w, uu, part,
+                                       ao, acco, co);
+            elem_store(T, S, cur, r, sl, mode, ao, acco, co);
         }
     }
 #pragma unroll
