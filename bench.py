@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--batch-shape", type=int, default=0,
                     help="FP32 batched kernel shape 1..7 for every system (see mqct_propagate_opts); implies "
                          "--no-autotune")
+    ap.add_argument("--no-molmol", dest="molmol", action="store_false",
+                    help="skip the asymmetric top + linear rotor timing")
     ap.add_argument("--no-sparse", dest="sparse", action="store_false",
                     help="skip the paper-scale sparse-path (log grid, truncation, N = 40401) timing")
     ap.add_argument("--no-rates", dest="rates", action="store_false",
@@ -503,6 +505,42 @@ def sparse_block(api, n_traj=1024, max_steps=2000, jmax=200):
                          "kernel": "k_sp_stage (timed with the whole propagate call)"}}
 
 
+def molmol_block(api, n_traj=1024):
+    """The molecule-molecule system of Sec. II (composite states of Eq. 3, coupling of Eqs. 13-17): a
+    water-like asymmetric top (j1 <= 2) + para-H2 (j2 in {0, 2}), N = 210 states, nine PES terms;
+    n_traj seeded trajectories (E log-uniform on 100-3000 cm^-1, b uniform on 0-10 bohr, from the ground
+    level), FP32 batched kernel and FP64 kernel, each timed once after a warm-up call."""
+    import torch
+
+    p = W.molmol_params(j1max=2, j2=(0, 2))
+    rng = np.random.default_rng(W.DEFAULT_SEED + 4)
+    out = {"workload": f"{n_traj} trajectories, asymmetric top (j1 <= 2) + linear rotor (j2 in 0, 2), N = 210, "
+                       f"{p.n_terms} terms"}
+    pops = {}
+    for prec, path in (("fp32", "factorised"), ("fp64", "factorised")):
+        sys_ = api.System.molmol(p, path=path, precision=prec)
+        tr = np.zeros(n_traj, api.TRAJ_DTYPE)
+        tr["e_coll"] = W.cm(np.exp(rng.uniform(np.log(100.0), np.log(3000.0), n_traj))) if prec == "fp32" else tr0["e_coll"]
+        tr["b"] = rng.uniform(0.0, 10.0, n_traj) if prec == "fp32" else tr0["b"]
+        tr["r0"], tr["r_end"], tr["dt"], tr["max_steps"] = 30.0, 30.0, 5.0, 1_000_000
+        if prec == "fp32":
+            tr0 = tr.copy()
+        trd = torch.from_numpy(tr.view(np.uint8).copy()).cuda()
+        api.propagate(sys_, trd[:64 * api.TRAJ_DTYPE.itemsize], want_pop=False, device=True)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pop, _, dg = api.propagate(sys_, trd, device=True)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        d = api.diag_to_numpy(dg)
+        pops[prec] = (pop.cpu().numpy(), d["steps"])
+        out[prec] = {"traj_steps_per_s": float(d["steps"].sum()) / sec, "seconds": sec}
+    same = pops["fp32"][1] == pops["fp64"][1]
+    out["max_abs_dP_fp32_vs_fp64"] = float(np.max(np.abs(pops["fp32"][0][same] - pops["fp64"][0][same])))
+    out["speedup"] = out["fp32"]["traj_steps_per_s"] / out["fp64"]["traj_steps_per_s"]
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def gpu_arm(args):
     import torch
@@ -683,6 +721,7 @@ def gpu_arm(args):
         adj = adjoint_block(api, args.adjoint)
     rates = rates_block(api) if args.rates else None
     sparse = sparse_block(api) if args.sparse else None
+    molmol = molmol_block(api) if args.molmol else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -720,7 +759,7 @@ def gpu_arm(args):
         "gpu_launches": n_launch[0], "latency": latency, "comparison": compare, "adjoint": adj,
         "sigma_sets_per_s": sigma_sets * ws / (ms * 1e-3 / args.steps),
         "sigma_set": "all cross sections out of one (collision energy, initial level) group",
-        "n1600": n1600, "rates": rates, "sparse": sparse,
+        "n1600": n1600, "rates": rates, "sparse": sparse, "molmol": molmol,
     }))
 
 
