@@ -536,7 +536,9 @@ def molmol_block(api, n_traj=1024):
         pops[prec] = (pop.cpu().numpy(), d["steps"])
         out[prec] = {"traj_steps_per_s": float(d["steps"].sum()) / sec, "seconds": sec}
     same = pops["fp32"][1] == pops["fp64"][1]
-    out["max_abs_dP_fp32_vs_fp64"] = float(np.max(np.abs(pops["fp32"][0][same] - pops["fp64"][0][same])))
+    out["same_steps"] = f"{int(same.sum())}/{n_traj}"
+    out["max_abs_dP_fp32_vs_fp64"] = (float(np.max(np.abs(pops["fp32"][0][same] - pops["fp64"][0][same])))
+                                      if same.any() else None)
     out["speedup"] = out["fp32"]["traj_steps_per_s"] / out["fp64"]["traj_steps_per_s"]
     return out
 
