@@ -343,8 +343,11 @@ typedef struct {
     int64_t *t_done_ns;   /* [n] GPU global-timer value (ns) when its results were written, or NULL */
     const int32_t *batch_shape; /* [n_systems] HOST array or NULL: shape of the FP32 batched kernel.
                              The call runs one launch for all its systems, whose shape is the first
-                             non-zero entry; 0 everywhere = automatic (the first of the first six
-                             that every system fits).  1..7 = (slots per CTA at most, threads) of
+                             non-zero entry; 0 everywhere = automatic (of the shapes every system
+                             fits, the one with the most slots on the GPU that leaves two
+                             trajectories per slot, else the one with the fewest slots; the
+                             (8,512) and (4,256) shapes first on ties).  1..7 = (slots per CTA at
+                             most, threads) of
                              (32,512) (16,512) (8,256) (8,512) (4,512) (16,256) (4,256); each system
                              gets the widest slot count (32, 16, 8 or 4, at most the shape's) its
                              basis fits; a shape that some system does not fit
@@ -352,7 +355,7 @@ typedef struct {
     const int32_t *tc_slots;    /* [n_systems] HOST array or NULL: trajectories in flight per system
                              on the stage-synchronous paths -- BF16X3: rounded up to a multiple
                              of 64, at most 8192, 0 = automatic (one or two waves of the GPU);
-                             FP32 PLAIN: rounded up to a multiple of 8, at most 8192, 0 = every
+                             FP32 PLAIN: rounded up to a multiple of 32, at most 8192, 0 = every
                              trajectory up to 4096                                              */
 } mqct_propagate_opts;
 

@@ -789,20 +789,31 @@ cudaError_t launch_batched(BatchMultiArgs a, const std::vector<const DevSys *> &
 // per SM (half the shared memory each).
 static size_t shape_cap(int i) { return (i == 2 || i == 6) ? 110 * 1024 : 220 * 1024; }
 
-bool batched_shape_fits(const DevSys &h, int i)
+// slot count of shape index i for the system (0: does not fit) and the shared memory it takes
+template <int BMAX, int T, int kUpt>
+static int shape_slots_of(const DevSys &h, size_t cap, size_t *smem)
+{
+    const int b = batched_slots<BMAX, T, kUpt>(h, cap);
+    if (smem) *smem = b ? batched_smem<BMAX, T>(h, b) + sizeof(BatchShared<BMAX>) : 0;
+    return b;
+}
+
+static int shape_slots(const DevSys &h, int i, size_t *smem = nullptr)
 {
     const size_t cap = shape_cap(i);
     switch (i) {
-        case 0: return batched_slots<32, 512, 4>(h, cap) > 0;
-        case 1: return batched_slots<16, 512, 4>(h, cap) > 0;
-        case 2: return batched_slots<8, 256, 4>(h, cap) > 0;
-        case 3: return batched_slots<8, 512, 2>(h, cap) > 0;
-        case 4: return batched_slots<4, 512, 4>(h, cap) > 0;
-        case 5: return batched_slots<16, 256, 4>(h, cap) > 0;
-        case 6: return batched_slots<4, 256, 2>(h, cap) > 0;
-        default: return false;
+        case 0: return shape_slots_of<32, 512, 4>(h, cap, smem);
+        case 1: return shape_slots_of<16, 512, 4>(h, cap, smem);
+        case 2: return shape_slots_of<8, 256, 4>(h, cap, smem);
+        case 3: return shape_slots_of<8, 512, 2>(h, cap, smem);
+        case 4: return shape_slots_of<4, 512, 4>(h, cap, smem);
+        case 5: return shape_slots_of<16, 256, 4>(h, cap, smem);
+        case 6: return shape_slots_of<4, 256, 2>(h, cap, smem);
+        default: return 0;
     }
 }
+
+bool batched_shape_fits(const DevSys &h, int i) { return shape_slots(h, i) > 0; }
 
 int batched_width(const DevSys &h)
 {
@@ -811,8 +822,46 @@ int batched_width(const DevSys &h)
     return 0;
 }
 
+// The automatic shape for n trajectories over the systems hs.  A CTA steps its slots in lockstep,
+// so its step time grows with its slot count while the throughput of an SM levels off from about
+// eight slots on: the longest trajectories, which start first from the longest-first work list,
+// then set the end of the launch when there are too many slots, and the refill order of the list
+// cannot balance the slots when there are too few.  The rule: the shape with the most slots on
+// the GPU (slots per CTA x CTAs per SM x SMs, the slot count of the narrowest system) that still
+// leaves two trajectories per slot, else the one with the fewest slots; ties go to the earlier
+// entry of kAutoOrder, which puts the eight-slots-per-SM shapes first.  -1: no shape fits.
+int batched_auto_shape(const std::vector<const DevSys *> &hs, int n, int sms)
+{
+    static const int kAutoOrder[7] = {3, 6, 4, 0, 1, 5, 2};
+    int best = -1, fewest = -1;
+    long long best_slots = -1, fewest_slots = 0;
+    for (int k = 0; k < 7; ++k) {
+        const int i = kAutoOrder[k];
+        int b = 1 << 30;
+        size_t smem = 0;
+        for (const DevSys *h : hs) {
+            size_t sm = 0;
+            b = std::min(b, shape_slots(*h, i, &sm));
+            smem = std::max(smem, sm);
+        }
+        if (hs.empty() || b <= 0) continue;
+        // two CTAs of 256 threads share an SM's registers when their shared memory allows
+        const int per_sm = (kBatchShapes[i][1] == 256 && smem <= 113 * 1024) ? 2 : 1;
+        const long long slots = (long long)b * per_sm * sms;
+        if (2 * slots <= n && slots > best_slots) {
+            best_slots = slots;
+            best = i;
+        }
+        if (fewest < 0 || slots < fewest_slots) {
+            fewest_slots = slots;
+            fewest = i;
+        }
+    }
+    return best >= 0 ? best : fewest;
+}
+
 // one persistent launch over every system of the call, with the requested shape (index + 1) or
-// the automatic one: the first of the first six that every system fits
+// the automatic one (batched_auto_shape)
 cudaError_t run_batched(BatchMultiArgs a, const std::vector<const DevSys *> &hs, int shape, cudaStream_t st)
 {
     int dev = 0, sms = 0;
@@ -829,8 +878,7 @@ cudaError_t run_batched(BatchMultiArgs a, const std::vector<const DevSys *> &hs,
         if (shape > 7 || !all_fit(shape - 1)) return cudaErrorInvalidConfiguration;
         idx = shape - 1;
     } else {
-        for (int i = 0; i < 6 && idx < 0; ++i)
-            if (all_fit(i)) idx = i;
+        idx = batched_auto_shape(hs, a.n, sms);
     }
     if (idx < 0) return cudaErrorInvalidConfiguration;
     const size_t cap = shape_cap(idx);

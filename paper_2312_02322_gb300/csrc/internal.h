@@ -148,10 +148,11 @@ struct BatchMultiArgs {
     long long *t_start, *t_done;  // optional device clock (ns) at start / end of each trajectory
     int nmax;
 };
-// the (slots per CTA at most, threads) instances of the FP32 batched kernel; the automatic choice
-// takes the first of the first six that fits (the last one is only ever chosen on request, e.g. by
-// the autotuner)
+// the (slots per CTA at most, threads) instances of the FP32 batched kernel; batched_auto_shape
+// picks one from the trajectory count and the slots each shape gives the systems
 constexpr int kBatchShapes[7][2] = {{32, 512}, {16, 512}, {8, 256}, {8, 512}, {4, 512}, {16, 256}, {4, 256}};
+// the automatic shape index (0-based) for n trajectories over the systems hs; -1 if none fits
+int batched_auto_shape(const std::vector<const DevSys *> &hs, int n, int sms);
 // true when shape index i (0-based) fits the system's basis with at least four slots
 bool batched_shape_fits(const DevSys &h, int i);
 int batched_width(const DevSys &h);

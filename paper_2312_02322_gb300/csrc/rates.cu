@@ -18,7 +18,9 @@
 // a fixed linear map of the knot values (set up on the host from the energy grid), the finite
 // pieces are integrated by 16-point Gauss-Legendre panels no wider than 4 kT (the exponential at the
 // nodes as a panel factor times node factors shared by the panels of a piece), and the integrand
-// carries exp(-(U - u0)/kT) so that neither exponential factor of R2 overflows.
+// carries exp(-(U - u0)/kT) so that neither exponential factor of R2 overflows.  The walk stops at
+// the first panel whose remainder bound (4 max|y| kT (U + kT) exp(-(U - u0)/kT) at its lower edge U)
+// is below 1e-17 of the integral so far; the tail is then dropped too.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,8 +97,9 @@ __global__ void __launch_bounds__(128) k_rates(const __grid_constant__ RateArgs 
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= A.n_pairs * A.n_T) return;
-    const int t = (int)(i % A.n_T);
-    const long long q = i / A.n_T;
+    // temperature is the slow index: the lanes of a warp share kT and so take similar panel counts
+    const int t = (int)(i / A.n_pairs);
+    const long long q = i % A.n_pairs;
     // q = b (b + 1) / 2 + a with a <= b
     long long b = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
     while (b * (b + 1) / 2 > q) --b;
@@ -136,9 +139,13 @@ __global__ void __launch_bounds__(128) k_rates(const __grid_constant__ RateArgs 
         double ef[kGl];
 #pragma unroll
         for (int j = 0; j < kGl; ++j) ef[j] = exp(-0.5 * hp * A.gx[j] * ith);
+        // the same remainder bound at each panel's lower edge c - hp/2, from the panel factor:
+        // exp(-(c - hp/2 - u0)/kT) = exp(-(c - u0)/kT) exp(hp/(2kT))
+        const double bnd = 4.0 * ymax * th * exp(0.5 * hp * ith);
         for (int p = 0; p < np; ++p) {
             const double c = lo + hp * (p + 0.5);
             const double ec = exp(-(c - u0) * ith);
+            if (p > 0 && bnd * (c - 0.5 * hp + th) * ec <= 1e-17 * acc) { done = true; return; }
             double s = 0.0;
 #pragma unroll
             for (int j = 0; j < kGl; ++j) {
