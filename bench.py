@@ -70,6 +70,10 @@ def parse():
                          "--no-autotune")
     ap.add_argument("--no-molmol", dest="molmol", action="store_false",
                     help="skip the asymmetric top + linear rotor timing")
+    ap.add_argument("--sparse-jmax", type=int, default=200,
+                    help="rotor jmax of the sparse paper-scale block (N = (jmax+1)^2)")
+    ap.add_argument("--sparse-traj", type=int, default=1024, help="trajectories of the sparse block")
+    ap.add_argument("--sparse-steps", type=int, default=2000, help="RK4 steps per trajectory of the sparse block")
     ap.add_argument("--no-sparse", dest="sparse", action="store_false",
                     help="skip the paper-scale sparse-path (log grid, truncation, N = 40401) timing")
     ap.add_argument("--no-rates", dest="rates", action="store_false",
@@ -447,7 +451,8 @@ def rates_block(api, n_levels=1032, reps=5):
 
 def sparse_block(api, n_traj=1024, max_steps=2000, jmax=200):
     """The paper-scale setup of Sec. III on an atom + rotor (FP32 spline table, stage-synchronous
-    sparse kernel): N = (jmax+1)^2 = 40401 states, Legendre terms lambda <= 12, the 63-point log grid on
+    sparse kernel): N = (jmax+1)^2 states (jmax 200: 40 401; jmax 446: 199 809, the paper's ~2e5),
+    Legendre terms lambda <= 12, the 63-point log grid on
     3-30 bohr, |M| > 1 cm^-1 at 6.03 / 7.11 bohr; n_traj seeded trajectories from 30 bohr (E log-uniform
     on 100-5000 cm^-1, b uniform on 0-10 bohr, initial j uniform on 0-10), each capped at max_steps
     RK4 steps; one warm-up call, then one timed call with the trajectories resident on the device."""
@@ -722,7 +727,8 @@ def gpu_arm(args):
     if args.adjoint:
         adj = adjoint_block(api, args.adjoint)
     rates = rates_block(api) if args.rates else None
-    sparse = sparse_block(api) if args.sparse else None
+    sparse = (sparse_block(api, n_traj=args.sparse_traj, max_steps=args.sparse_steps, jmax=args.sparse_jmax)
+              if args.sparse else None)
     molmol = molmol_block(api) if args.molmol else None
 
     cpu = None
