@@ -207,7 +207,7 @@ typedef struct {
  * G^lambda_{(j''m),(j'm)} = <j'' m|P_lambda|j' m> (Eq. 15).  With with_params != 0 the
  * derivative tables for theta = (A_0..A_{L-1}, beta_0..beta_{L-1}) are filled (P = 2L). */
 typedef struct {
-    int32_t jmax;
+    int32_t jmax;        /* 0..500 (N = (jmax+1)^2 <= 251 001) */
     double bconst;       /* hartree            */
     double mu;           /* electron masses    */
     int32_t n_terms;     /* L <= 16            */
@@ -226,7 +226,7 @@ typedef struct {
 
 /* Build the description of the atom + linear rotor system above.  Allocates the host
  * arrays of *out (released by mqct_free_desc); G is returned in triplet form.
- * Host-only: needs no GPU.  Errors: MQCT_ERR_INVALID_ARG (jmax < 0, n_terms outside
+ * Host-only: needs no GPU.  Errors: MQCT_ERR_INVALID_ARG (jmax outside [0, 500], n_terms outside
  * [1, 16], n_grid < 4, r_max <= r_min, mu <= 0), MQCT_ERR_OOM. */
 mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_system_desc *out);
 /* Parameters of the built-in atom + rigid asymmetric top system (helper for users and tests).

@@ -552,12 +552,15 @@ __device__ __forceinline__ void batched_system(const BatchMultiArgs &a, BatchSha
                     const int sl = r >> 5, rl = r & 31;
                     for (int f = 0; f < S.n_f; ++f) {
                         const int *so = S.f_sl_off + (size_t)f * (S.n_slices + 1);
-                        const int off = __ldg(so + sl) + rl, width = (__ldg(so + sl + 1) - __ldg(so + sl)) >> 5;
+                        const int o0 = __ldg(so + sl), o1 = __ldg(so + sl + 1);
+                        const int2 *pe = S.f_cvf + o0 + rl;
+                        const int width = (o1 - o0) >> 5;
                         float2 y[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 #pragma unroll 2
-                        for (int e = 0; e < width; ++e) {
-                            const int col = __ldg(S.f_cols + off + e * kSlice);
-                            const float gv = __ldg(S.f_valf + off + e * kSlice);
+                        for (int e = 0; e < width; ++e, pe += kSlice) {
+                            const int2 cv = __ldg(pe);
+                            const int col = cv.x;
+                            const float gv = __int_as_float(cv.y);
                             const F4x2 z = ld4(C, col * B + 4 * g);
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {

@@ -8,6 +8,7 @@
 // cos theta), with the selection rules of Eq. 15 (m'' = m', triangle rule,
 // j' + j'' + lambda even) applied to the structural zeros.
 // PES: V(R, theta) = sum_l A_l exp(-beta_l R) P_l(cos theta) - C6 R^-6 (1 - exp(-(R/Rd)^6)).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -184,7 +185,7 @@ extern "C" mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_syste
     if (!p || !out) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: NULL argument");
     std::memset(out, 0, sizeof(*out));
     const int jmax = p->jmax, L = p->n_terms, ng = p->n_grid;
-    if (jmax < 0 || jmax > 200) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: jmax outside [0, 200]");
+    if (jmax < 0 || jmax > 500) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: jmax outside [0, 500]");
     if (L < 1 || L > 16) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: n_terms outside [1, 16]");
     if (ng < 4) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: n_grid < 4");
     if (!(p->r_max > p->r_min) || !(p->r_min > 0)) return fail(MQCT_ERR_INVALID_ARG, "mqct_build_diatom: bad grid range");
@@ -210,18 +211,21 @@ extern "C" mqct_status mqct_build_diatom(const mqct_diatom_params *p, mqct_syste
     std::vector<double> xq, wq;
     gauss_legendre(nq, xq, wq);
     std::vector<std::vector<double>> th(nq);
-    std::vector<double> pl(nq);
+    std::vector<double> pl((size_t)L * nq);
+    for (int l = 0; l < L; ++l)
+        for (int q = 0; q < nq; ++q) pl[(size_t)l * nq + q] = legendre(l, xq[q]);
     std::vector<int32_t> gt, gr, gc;
     std::vector<double> gv;
-    for (int l = 0; l < L; ++l) {
-        for (int q = 0; q < nq; ++q) pl[q] = legendre(l, xq[q]);
-        for (int m = 0; m <= jmax; ++m) {
-            for (int q = 0; q < nq; ++q) norm_assoc_legendre(jmax, m, xq[q], th[q]);
+    for (int m = 0; m <= jmax; ++m) {
+        // the normalised associated Legendre functions of order m at the nodes, once per m
+        for (int q = 0; q < nq; ++q) norm_assoc_legendre(jmax, m, xq[q], th[q]);
+        for (int l = 0; l < L; ++l) {
+            const double *plq = pl.data() + (size_t)l * nq;
             for (int j2 = m; j2 <= jmax; ++j2)
-                for (int j1 = m; j1 <= jmax; ++j1) {
-                    if (std::abs(j1 - j2) > l || l > j1 + j2 || ((j1 + j2 + l) & 1)) continue;
+                for (int j1 = std::max(m, j2 - l); j1 <= std::min(jmax, j2 + l); ++j1) {
+                    if (l > j1 + j2 || ((j1 + j2 + l) & 1)) continue;
                     double acc = 0.0;
-                    for (int q = 0; q < nq; ++q) acc += wq[q] * th[q][j2] * pl[q] * th[q][j1];
+                    for (int q = 0; q < nq; ++q) acc += wq[q] * th[q][j2] * plq[q] * th[q][j1];
                     for (int sm = (m == 0 ? 1 : -1); sm <= 1; sm += 2) {
                         int mm = sm * m;
                         gt.push_back(l);

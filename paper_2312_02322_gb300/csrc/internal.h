@@ -61,6 +61,8 @@ struct DevSys {
     const int *f_cols;
     const double *f_val;
     const float *f_valf;       // FP32 copy of f_val (mixed-precision systems)
+    const int2 *f_cvf;         // f_cols and f_valf interleaved: (column, FP32 value bits) per entry,
+                               // one 8-byte load per entry (mixed-precision systems)
     // Batched mixed-precision paths: FP32 spline coefficients of v_lambda, ladder factors
     const float4 *vcoef_f;     // [L][n_int]
     const float *aupf, *adnf;  // [n] FP32 ladder factors

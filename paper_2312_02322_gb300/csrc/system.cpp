@@ -538,6 +538,13 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
                 vf[i] = make_float4((float)vcoef[i].x, (float)vcoef[i].y, (float)vcoef[i].z, (float)vcoef[i].w);
             std::vector<float> aupf(aup.begin(), aup.end()), adnf(adn.begin(), adn.end());
             up_(fvalf, &D.f_valf);
+            std::vector<int2> fcv(fcols.size());
+            for (size_t i = 0; i < fcols.size(); ++i) {
+                int bits;
+                std::memcpy(&bits, &fvalf[i], sizeof bits);
+                fcv[i] = make_int2(fcols[i], bits);
+            }
+            up_(fcv, &D.f_cvf);
             up_(aupf, &D.aupf);
             up_(adnf, &D.adnf);
             up_(vf, &D.vcoef_f);
