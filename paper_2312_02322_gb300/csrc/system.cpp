@@ -221,8 +221,13 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     for (auto &e : lev_e)
         if (std::isnan(e)) e = 0.0;  // unused level id
 
-    // ---- coupling entries per term (caller indices), duplicates summed
-    std::vector<std::map<std::pair<int, int>, double>> G(L);
+    // ---- coupling entries per term (caller indices): sorted by (row, column), duplicates summed
+    // in the order given
+    struct Trip {
+        int r, c;
+        double v;
+    };
+    std::vector<std::vector<Trip>> G(L);
     double gmax = 0.0;
     if (d->G) {
         for (int l = 0; l < L; ++l)
@@ -230,7 +235,7 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
                 for (int c = 0; c < n; ++c) {
                     double v = d->G[((size_t)l * n + r) * n + c];
                     if (!std::isfinite(v)) return fail(MQCT_ERR_INVALID_ARG, "non-finite G");
-                    if (v != 0.0) G[l][{r, c}] += v;
+                    if (v != 0.0) G[l].push_back({r, c, v});
                 }
     } else {
         for (int64_t i = 0; i < d->g_nnz; ++i) {
@@ -238,18 +243,28 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
             double v = d->g_val[i];
             if (l < 0 || l >= L || r < 0 || r >= n || c < 0 || c >= n) return fail(MQCT_ERR_INVALID_ARG, "G triplet out of range");
             if (!std::isfinite(v)) return fail(MQCT_ERR_INVALID_ARG, "non-finite G");
-            G[l][{r, c}] += v;
+            G[l].push_back({r, c, v});
         }
     }
+    auto trip_less = [](const Trip &a, const Trip &b) { return a.r != b.r ? a.r < b.r : a.c < b.c; };
+    for (auto &t : G) {
+        std::stable_sort(t.begin(), t.end(), trip_less);
+        size_t k = 0;
+        for (size_t i = 0; i < t.size(); ++i) {
+            if (k > 0 && t[k - 1].r == t[i].r && t[k - 1].c == t[i].c) t[k - 1].v += t[i].v;
+            else t[k++] = t[i];
+        }
+        t.resize(k);
+    }
     for (int l = 0; l < L; ++l)
-        for (auto &kv : G[l]) gmax = std::max(gmax, std::fabs(kv.second));
+        for (const Trip &e : G[l]) gmax = std::max(gmax, std::fabs(e.v));
     for (int l = 0; l < L; ++l)
-        for (auto &kv : G[l]) {
-            int r = kv.first.first, c = kv.first.second;
-            if (d->m[r] != d->m[c]) return fail(MQCT_ERR_INVALID_ARG, "G couples states of different m (Eq. 6)");
-            auto it = G[l].find({c, r});
-            double vt = it == G[l].end() ? 0.0 : it->second;
-            if (std::fabs(vt - kv.second) > 1e-12 * gmax) return fail(MQCT_ERR_INVALID_ARG, "G is not symmetric");
+        for (const Trip &e : G[l]) {
+            if (d->m[e.r] != d->m[e.c]) return fail(MQCT_ERR_INVALID_ARG, "G couples states of different m (Eq. 6)");
+            const Trip key{e.c, e.r, 0.0};
+            auto it = std::lower_bound(G[l].begin(), G[l].end(), key, trip_less);
+            double vt = (it != G[l].end() && it->r == e.c && it->c == e.r) ? it->v : 0.0;
+            if (std::fabs(vt - e.v) > 1e-12 * gmax) return fail(MQCT_ERR_INVALID_ARG, "G is not symmetric");
         }
 
     // ---- grid data
@@ -324,11 +339,11 @@ extern "C" mqct_status mqct_create_system(const mqct_system_desc *d, mqct_system
     std::vector<double> diag_g((size_t)L * n, 0.0);
     std::vector<std::vector<std::vector<Entry>>> grows(L, std::vector<std::vector<Entry>>(n));
     for (int l = 0; l < L; ++l)
-        for (auto &kv : G[l]) {
-            int r = S.inv[kv.first.first], c = S.inv[kv.first.second];
-            if (kv.second == 0.0) continue;
-            grows[l][r].push_back({r, c, kv.second});
-            if (r == c) diag_g[(size_t)l * n + r] = kv.second;
+        for (const Trip &e : G[l]) {
+            int r = S.inv[e.r], c = S.inv[e.c];
+            if (e.v == 0.0) continue;
+            grows[l][r].push_back({r, c, e.v});
+            if (r == c) diag_g[(size_t)l * n + r] = e.v;
         }
     for (int l = 0; l < L; ++l)
         for (auto &row : grows[l]) std::sort(row.begin(), row.end(), [](const Entry &a, const Entry &b) { return a.c < b.c; });

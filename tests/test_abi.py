@@ -207,6 +207,36 @@ def test_create_rejects_coupling_across_m(L):
     assert b"symmetric" in L.mqct_last_error()
 
 
+def test_create_sums_duplicate_triplets(L):
+    """Triplet G: repeated (term, row, column) entries are summed before the symmetry check, so
+    (0, 1) given as 0.25 + 0.25 against (1, 0) = 0.5 passes validation (on a machine without a GPU
+    the call then stops at the first device allocation), and 0.25 alone is rejected."""
+    n = 2
+    e = np.zeros(n)
+    lev = np.array([0, 1], np.int32)
+    j = np.array([1, 1], np.int32)
+    m = np.zeros(n, np.int32)
+    v = np.zeros((1, 8))
+    ends = np.zeros((1, 2))
+    term = np.zeros(3, np.int32)
+    row = np.array([0, 1, 0], np.int32)
+    col = np.array([1, 0, 1], np.int32)
+    val = np.array([0.25, 0.5, 0.25])
+    d = api.Desc()
+    d.n_states, d.energy, d.level, d.j, d.m = n, e.ctypes.data, lev.ctypes.data, j.ctypes.data, m.ctypes.data
+    d.mu, d.n_terms, d.G = 100.0, 1, None
+    d.g_nnz, d.g_term, d.g_row, d.g_col, d.g_val = 3, term.ctypes.data, row.ctypes.data, col.ctypes.data, val.ctypes.data
+    d.n_grid, d.r_min, d.r_max, d.v, d.dv_ends = 8, 2.0, 30.0, v.ctypes.data, ends.ctypes.data
+    h = C.c_void_p()
+    st = L.mqct_create_system(C.byref(d), C.byref(h))
+    assert st != api.ERR_INVALID_ARG, L.mqct_last_error()
+    if st == api.OK:
+        L.mqct_destroy_system(h)
+    d.g_nnz = 2  # (0, 1) = 0.25 only
+    assert L.mqct_create_system(C.byref(d), C.byref(h)) == api.ERR_INVALID_ARG
+    assert b"symmetric" in L.mqct_last_error()
+
+
 def test_struct_layouts_match_header(L, tmp_path):
     """Compile a probe against include/mqct.h with gcc and compare sizes and offsets with the binding."""
     import subprocess
