@@ -176,7 +176,7 @@ def test_fp32_plain_large_basis_sampled(mq, ora):
 
 def test_fp32_plain_paper_size_sampled(mq, ora):
     """jmax = 446 (N = 199 809, the paper's ~2e5 states), lambda <= 12, 63-point log grid on 3-30 bohr,
-    |M| > 1 cm^-1 at 6.03 and 7.11 bohr: 64 trajectories started on the wall (r0 = 8) for 8 steps keep
+    |M| > 1 cm^-1 at 6.03 and 7.11 bohr: 64 trajectories started on the wall (r0 = 8) for 4 steps keep
     their norms, and one of them matches the oracle (same cap on both sides)."""
     p = W.sparse_pes_params(jmax=446, lam_max=12)
     sys_ = mq.System.diatom(p, path="plain", precision="fp32", grid="log", trunc=TRUNC)
@@ -188,16 +188,16 @@ def test_fp32_plain_paper_size_sampled(mq, ora):
     b = rng.uniform(0.0, 6.0, n)
     j = rng.integers(0, 60, n).astype(np.int32)
     ts = W.TrajSet(e, b, j, np.zeros_like(j), np.zeros(n, np.int32), 1, r0=8.0, r_end=8.0, dt=5.0,
-                   max_steps=8, sampling="mc", b_max=6.0, n_b=0)
+                   max_steps=4, sampling="mc", b_max=6.0, n_b=0)
     tr = mq.make_trajs(ts, sys_)
     pop, _, dg = mq.propagate(sys_, tr, device=False)
-    assert np.all(dg["steps"] == 8) and np.all(dg["status"] & 1)
+    assert np.all(dg["steps"] == 4) and np.all(dg["status"] & 1)
     assert np.max(np.abs(pop.sum(axis=1) - 1.0)) < 1e-5
     sub = [0]
     s0 = [sys_.state(int(ts.init_j[0]), 0)]
     del sys_
     osys = ora.diatom_system(p.jmax, p.bconst, p.mu, p.A, p.beta, p.c6, p.rd, p.n_grid, p.r_min, p.r_max,
                              grid_log=True, trunc=TRUNC)
-    oamp, ores = ora.propagate(osys, ts.e_coll[sub], ts.b[sub], s0, r0=8.0, r_end=8.0, dt=5.0, max_steps=8)
-    assert np.all(ores["steps"] == 8)
+    oamp, ores = ora.propagate(osys, ts.e_coll[sub], ts.b[sub], s0, r0=8.0, r_end=8.0, dt=5.0, max_steps=4)
+    assert np.all(ores["steps"] == 4)
     assert np.max(np.abs(pop[sub] - np.abs(oamp) ** 2)) < 1e-4
