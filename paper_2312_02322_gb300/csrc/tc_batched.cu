@@ -621,7 +621,7 @@ __device__ int tc_claim(const TcState &T, const DevSys &S, const SlotLane &L, do
 // the quantities of the next stage at the slot's stage input qs: interval, spline values of every
 // term (FP32 views), 1/R, (1/mu)/R^2, dPhi/dt; returns the TABLE_RANGE bit.  Called by every lane
 // of the warp (publish: write the views of this slot).
-__device__ int tc_next_stage(const TcState &T, const DevSys &S, const SlotLane &L, double qs, bool publish,
+__device__ __forceinline__ int tc_next_stage(const TcState &T, const DevSys &S, const SlotLane &L, double qs, bool publish,
                              double &ir, double &i2m, double &phid)
 {
     const unsigned full = 0xffffffffu;
@@ -646,15 +646,27 @@ __device__ int tc_next_stage(const TcState &T, const DevSys &S, const SlotLane &
     }
     const float xf = (float)x;
     float v0 = 0.f, d0 = 0.f;
-    for (int l = L.sc; l < S.L; l += 4) {
-        const float4 c = S.vcoef_f[(size_t)l * S.n_int + k];
-        const float v = fmaf(xf, fmaf(xf, fmaf(xf, c.w, c.z), c.y), c.x);
-        const float dv = fmaf(xf, fmaf(3.0f * xf, c.w, 2.0f * c.z), c.y);
-        if (publish) {
-            T.coef[(size_t)l * T.S + L.sl] = v;
-            T.coef[((size_t)S.L + l) * T.S + L.sl] = dv;
+    // the spline coefficients (a read-only table) of four terms per lane are loaded ahead
+    for (int l0 = L.sc; l0 < S.L; l0 += 16) {
+        float4 cf[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int l = l0 + 4 * i;
+            cf[i] = l < S.L ? __ldg(S.vcoef_f + (size_t)l * S.n_int + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if ((S.id_mask >> l) & 1ull) { v0 += v; d0 += dv; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int l = l0 + 4 * i;
+            if (l >= S.L) continue;
+            const float4 c = cf[i];
+            const float v = fmaf(xf, fmaf(xf, fmaf(xf, c.w, c.z), c.y), c.x);
+            const float dv = fmaf(xf, fmaf(3.0f * xf, c.w, 2.0f * c.z), c.y);
+            if (publish) {
+                T.coef[(size_t)l * T.S + L.sl] = v;
+                T.coef[((size_t)S.L + l) * T.S + L.sl] = dv;
+            }
+            if ((S.id_mask >> l) & 1ull) { v0 += v; d0 += dv; }
+        }
     }
     v0 += __shfl_xor_sync(full, v0, 8);
     v0 += __shfl_xor_sync(full, v0, 16);
@@ -691,10 +703,24 @@ __device__ void tc_publish_idle(const TcState &T, const DevSys &S, const SlotLan
 
 // phase factors exp(-i E_l t) of the slot at stage time t = n_half dt / 2 into PH (the four lanes
 // split the levels)
-__device__ void tc_phases(const TcState &T, const DevSys &S, const SlotLane &L, float2 *PH, unsigned n_half)
+__device__ __forceinline__ void tc_phases(const TcState &T, const DevSys &S, const SlotLane &L, float2 *PH, unsigned n_half)
 {
-    for (int l = L.sc; l < S.n_levels; l += 4)
-        PH[(size_t)l * T.S + L.sl] = phase_factor(T.inc[(size_t)l * T.S + L.sl], n_half);
+    // the increments are loaded four at a time ahead of the stores, so that the independent global
+    // loads overlap instead of each waiting for the previous store
+    constexpr int kB = 4;
+    for (int l0 = L.sc; l0 < S.n_levels; l0 += 4 * kB) {
+        unsigned long long v[kB];
+#pragma unroll
+        for (int i = 0; i < kB; ++i) {
+            const int l = l0 + 4 * i;
+            v[i] = l < S.n_levels ? T.inc[(size_t)l * T.S + L.sl] : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < kB; ++i) {
+            const int l = l0 + 4 * i;
+            if (l < S.n_levels) PH[(size_t)l * T.S + L.sl] = phase_factor(v[i], n_half);
+        }
+    }
 }
 
 // claim the first trajectory of every slot, initialise its column and views
@@ -768,13 +794,23 @@ __global__ void __launch_bounds__(128) k_tc_slots(TcState T, int s, int n_rowblo
     double q = T.Q[ci], qs = T.QS[ci], lacc = T.LACC[ci];
     auto comp = [&](double v, int c2) { return __shfl_sync(full, v, 8 * c2 + L.sj); };
     // row-tile sums: lane c sums quantity c (F, T, V, |a|^2), lanes c < 2 also c + 4 (E|a|^2, <J_y>)
+    // (the partial sums of the previous launch are loaded four at a time ahead of the compensated
+    // additions; a zero beyond the last row block leaves both parts unchanged)
     auto tsum = [&](int qq) {
         float hi = 0.f, lo = 0.f;
-        for (int b = 0; b < n_rowblocks; ++b) {
-            const float2 p = T.part[((size_t)b * 6 + qq) * T.S + L.slc];
-            float e2;
-            two_sum(hi, p.x, hi, e2);
-            lo += e2 + p.y;
+        for (int b0 = 0; b0 < n_rowblocks; b0 += 4) {
+            float2 p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int b = b0 + i;
+                p[i] = b < n_rowblocks ? __ldg(T.part + ((size_t)b * 6 + qq) * T.S + L.slc) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float e2;
+                two_sum(hi, p[i].x, hi, e2);
+                lo += e2 + p[i].y;
+            }
         }
         return (double)hi + (double)lo;
     };
