@@ -22,8 +22,7 @@
  *   Sec. III    cubic-spline interpolation of the coupling along R
  *   Sec. II     final |a|^2 summed over final and averaged over initial degenerate states
  *
- * Readings where the printed text is garbled or silent (each is listed in the
- * design notes of the repository):
+ * Readings where the printed text is garbled or silent:
  *   - Eq. 5 Coriolis term: written as the anti-Hermitian generator
  *       (K a)_{j m} = (dPhi/dt / 2) [ A-_{jm} a_{j,m-1} - A+_{jm} a_{j,m+1} ],
  *     A+-_{jm} = sqrt(j(j+1) - m(m+-1)), i.e. H_q = H_rot + V - dPhi/dt J_y.
@@ -774,8 +773,8 @@ static int propagate_one(const ora_sys *S, const ora_traj *tr, const ora_opts *o
     double dt = tr->dt, t = 0.0, e0 = 0.0, j0 = 0.0, ndev = 0.0, edev = 0.0, jdev = 0.0;
     ora_eval ev;
     int steps = 0, stopped = 0;
-    /* Step control.  Fixed: every step dt.  Adaptive (o->tol > 0; ADAPTOL of Sec. III is not given,
-       this is the reading in the design notes): step doubling -- one RK4 step of h against two of
+    /* Step control.  Fixed: every step dt.  Adaptive (o->tol > 0; the algorithm of ADAPTOL in
+       Sec. III is not given, so this is a reading of it): step doubling -- one RK4 step of h against two of
        h/2 from the same state, error = max_n |a_n(two halves) - a_n(one step)|.  The two-half result
        is kept when the error is at most tol or h is already dt (the smallest step); otherwise h is
        halved and the step retried from the same state.  After an accepted step h doubles, up to

@@ -13,7 +13,7 @@ What the paper fixes (Sec. III):
     through the computed energies, extrapolated to zero at the excitation threshold and
     continued towards high energies.
 
-Readings where the paper defers to its ref. [44] (each stated again in the design doc):
+Readings where the paper defers to its ref. [44]:
   R1 (energy variable)  U, the energy at which both directions are compared in Eq. 19, is the
      mean of the incoming and outgoing translational energies, so the incoming energy of
      n'->n'' is U + dE/2 with dE = E'' - E'.

@@ -1,6 +1,6 @@
-"""Pins of the oracle's decoupled classical motion (the AT-MQCT decoupling of Sec. III, in the
-reading of the design notes: R and Phi move in the isotropic potential v_0 alone, with no torque,
-and the amplitudes follow Eq. 5 along that path).  CPU only."""
+"""Pins of the oracle's decoupled classical motion (the AT-MQCT decoupling of Sec. III, read as:
+R and Phi move in the isotropic potential v_0 alone, with no torque, and the amplitudes follow
+Eq. 5 along that path) and of its adaptive step control.  CPU only."""
 import numpy as np
 import pytest
 
