@@ -46,6 +46,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -68,15 +69,31 @@
 /* planted mistakes, used only by the tests that show the conservation pins catch them */
 #define ORA_F_PLANT_TORQUE 8     /* reverse the sign of the torque alone          */
 #define ORA_F_PLANT_CORIOLIS 16  /* drop the factor 1/2 of the Coriolis term      */
-/* decoupled classical motion (the AT-MQCT decoupling of Sec. III, in the reading of the design
- * notes): R, Phi move in the isotropic potential v_0(R) alone (term 0, whose G must be the
- * identity) with no torque; the amplitudes follow Eq. 5 along that trajectory */
+/* decoupled classical motion (the AT-MQCT decoupling of Sec. III, read as): R, Phi move in the
+ * isotropic potential v_0(R) alone (term 0, whose G must be the identity) with no torque; the
+ * amplitudes follow Eq. 5 along that trajectory */
 #define ORA_F_DECOUPLED 32
 
 /* ------------------------------------------------------------------ */
 /* Clebsch-Gordan coefficients: Racah's closed formula, long double.  */
 /* ------------------------------------------------------------------ */
-static long double lfac(int n) { return lgammal((long double)n + 1.0L); }
+/* ln n! = lgammal(n + 1); the values for n < ORA_LFAC_N are computed once (the same calls, so
+   the same numbers) because every coefficient of a large basis needs dozens of them */
+#define ORA_LFAC_N 4096
+static long double lfac_tab[ORA_LFAC_N];
+static pthread_once_t lfac_once = PTHREAD_ONCE_INIT;
+static void lfac_fill(void)
+{
+    for (int n = 0; n < ORA_LFAC_N; ++n) lfac_tab[n] = lgammal((long double)n + 1.0L);
+}
+static long double lfac(int n)
+{
+    if (n >= 0 && n < ORA_LFAC_N) {
+        pthread_once(&lfac_once, lfac_fill);
+        return lfac_tab[n];
+    }
+    return lgammal((long double)n + 1.0L);
+}
 
 double ora_cg(int j1, int m1, int j2, int m2, int J, int M)
 {
