@@ -167,6 +167,40 @@ def test_prescribed_flag_needs_fp64(L):
     api.lib().mqct_free_desc(C.byref(d))
 
 
+def test_builder_coupling_matches_oracle_at_paper_size(L, ora):
+    """jmax = 446 (N = 199 809, the largest basis the paper-scale tests run): the library's
+    Gauss-Legendre Gaunt integrals agree with the oracle's Racah-formula G^lambda to 1e-12 on every
+    entry of lambda = 0, 1, 6, 12; entries only the library lists are accidental zeros of the
+    Clebsch-Gordan coefficient (below 1e-15), which the oracle drops."""
+    p = inputs.sparse_pes_params(jmax=446, lam_max=12)
+    dp = api.DiatomParams()
+    dp.jmax, dp.bconst, dp.mu, dp.n_terms = p.jmax, p.bconst, p.mu, len(p.A)
+    for i in range(len(p.A)):
+        dp.A[i], dp.beta[i] = p.A[i], p.beta[i]
+    dp.c6, dp.rd, dp.n_grid, dp.r_min, dp.r_max = p.c6, p.rd, p.n_grid, p.r_min, p.r_max
+    dp.path, dp.grid_kind = api._PATHS["plain"], api.GRID_LOG
+    d = api.Desc()
+    assert L.mqct_build_diatom(C.byref(dp), C.byref(d)) == 0
+    nnz = d.g_nnz
+    get = lambda f, t: np.ctypeslib.as_array(C.cast(getattr(d, f), C.POINTER(t)), (nnz,)).copy()
+    t, r, c, v = get("g_term", C.c_int32), get("g_row", C.c_int32), get("g_col", C.c_int32), get("g_val", C.c_double)
+    assert d.n_states == 199809
+    api.lib().mqct_free_desc(C.byref(d))
+    for lam in (0, 1, 6, 12):
+        orow, ocol, oval = ora.diatom_G_triplets(446, lam)
+        m = t == lam
+        kl = r[m].astype(np.int64) * 1_000_000 + c[m]
+        ko = orow.astype(np.int64) * 1_000_000 + ocol
+        keys = np.union1d(kl, ko)
+        vl, vo = np.zeros(keys.size), np.zeros(keys.size)
+        vl[np.searchsorted(keys, kl)] = v[m]
+        vo[np.searchsorted(keys, ko)] = oval
+        assert np.max(np.abs(vl - vo)) < 1e-12, lam
+        only_lib = ~np.isin(keys, ko)
+        assert not np.any(~np.isin(keys, kl)), lam
+        assert np.all(np.abs(vl[only_lib]) < 1e-15), lam
+
+
 @pytest.mark.parametrize("field,value,needle", [
     ("n_grid", 3, b"n_grid"),
     ("mu", -1.0, b"mu"),
